@@ -1,0 +1,411 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+worked example (Tables 1-3, the sorting system of Sec. 6), the matrix
+formula C_{k+1} = C_k + S_k . M_Pi of Sec. 2 on delay-free systems, spike
+bookkeeping, hand-written delay traces, brute-force enumeration of every
+spiking vector on tiny systems, and NVIDIA's host-side Philox generator.
+"""
+import ctypes as ct
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_04343_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+
+def load_table1():
+    rows = []
+    for line in open(os.path.join(GOLD, "sort3_table1_dense.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        rows.append([int(x) for x in line.split()[1:]])
+    return np.array(rows, np.int64)
+
+
+def dense_matrix(desc):
+    """M_Pi by its definition (Sec. 2): row r has -c_r at its own neuron and
+    +p_r at every neuron its neuron has a synapse to."""
+    M = np.zeros((desc.m, desc.q), np.int64)
+    for i in range(desc.q):
+        for r in range(desc.rule_offsets[i], desc.rule_offsets[i + 1]):
+            M[r, i] -= desc.rule_c[r]
+            for e in range(desc.syn_offsets[i], desc.syn_offsets[i + 1]):
+                M[r, desc.syn_targets[e]] += desc.rule_p[r]
+    return M
+
+
+def regex_ok(n, k, j, c):
+    """a^k (a^j)*: n = k + t*j for some t >= 0 (j = 0: n = k); and n >= c."""
+    if j == 0:
+        return n == k and n >= c
+    return n >= k and (n - k) % j == 0 and n >= c
+
+
+def make_desc(q, rules, syn, init):
+    """rules: list per neuron of (k, j, c, p, d); syn: list of (i, j)."""
+    offs, ks, js, cs, ps, ds = [0], [], [], [], [], []
+    for rl in rules:
+        for (k, j, c, p, d) in rl:
+            ks.append(k); js.append(j); cs.append(c); ps.append(p); ds.append(d)
+        offs.append(len(ks))
+    out = [[] for _ in range(q)]
+    for (a, b) in syn:
+        out[a].append(b)
+    so, tg = [0], []
+    for i in range(q):
+        tg.extend(out[i]); so.append(len(tg))
+    a32 = lambda x: np.asarray(x, np.int32)
+    return synth.SystemDesc(q=q, init_spikes=a32(init), rule_offsets=np.asarray(offs, np.int64),
+                            rule_k=a32(ks), rule_j=a32(js), rule_c=a32(cs), rule_p=a32(ps),
+                            rule_d=a32(ds), syn_offsets=np.asarray(so, np.int64), syn_targets=a32(tg))
+
+
+def tiny_random(seed, q=5, delays=True):
+    rng = np.random.default_rng(seed)
+    rules = []
+    for i in range(q):
+        rl = []
+        for _ in range(int(rng.integers(0, 4))):
+            k = int(rng.integers(1, 4)); j = int(rng.integers(0, 3))
+            c = int(rng.integers(1, k + 1)); p = int(rng.integers(0, 3))
+            d = int(rng.integers(0, 3)) if (delays and p > 0) else 0
+            rl.append((k, j, c, p, d))
+        rules.append(rl)
+    syn = [(a, b) for a in range(q) for b in range(q) if a != b and rng.random() < 0.4]
+    init = rng.integers(0, 6, size=q)
+    return make_desc(q, rules, syn, init)
+
+
+# ---------------------------------------------------------------- Philox
+
+def _curand():
+    for name in ("libcurand.so", "libcurand.so.10"):
+        for d in ("", "/usr/local/cuda/lib64/", "/usr/local/cuda/lib/"):
+            try:
+                return ct.CDLL(d + name)
+            except OSError:
+                pass
+    return None
+
+
+def test_philox_matches_curand_host_generator():
+    """NVIDIA's host Philox4_32_10 generator (libcurand, run on the CPU) emits
+    block b of seed s as Philox4x32-10 at counter (b >> 16, 0, b & 0xffff, 0)
+    and key (s mod 2^32, s >> 32); the oracle's Philox must give the same words."""
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not available")
+    gen = ct.c_void_p()
+    CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+    assert lib.curandCreateGeneratorHost(ct.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) == 0
+    try:
+        nblk = 70000  # spans the 65,536-block wrap, so counter word 0 moves too
+        for seed in (0, 1, 0x9E3779B97F4A7C15, 0x0123456789ABCDEF, 2**64 - 1):
+            assert lib.curandSetPseudoRandomGeneratorSeed(gen, ct.c_ulonglong(seed)) == 0
+            assert lib.curandSetGeneratorOffset(gen, ct.c_ulonglong(0)) == 0
+            out = np.zeros(nblk * 4, np.uint32)
+            assert lib.curandGenerate(gen, out.ctypes.data_as(ct.c_void_p), ct.c_size_t(out.size)) == 0
+            out = out.reshape(-1, 4)
+            key = [seed & 0xFFFFFFFF, seed >> 32]
+            for b in [0, 1, 2, 3, 17, 255, 4096, 65535, 65536, 65537, 69999]:
+                got = oracle.philox4x32_10([b >> 16, 0, b & 0xFFFF, 0], key)
+                assert (got == out[b]).all(), (seed, b)
+    finally:
+        lib.curandDestroyGenerator(gen)
+
+
+def test_philox_choice_is_uniform():
+    """The Philox-keyed pick over |A| = 3 rules is uniform (chi-square, 2 dof)."""
+    # three always-applicable rules a*(k=1,j=1 with c=1 needs n>=1): give n large
+    d = make_desc(1, [[(1, 1, 1, 0, 0), (1, 1, 1, 0, 0), (1, 1, 1, 0, 0)]], [], [10**6])
+    counts = np.zeros(3)
+    st = oracle.initial_state(d)
+    for k in range(6000):
+        S, _, h = oracle.step(d, st, k, oracle.PHILOX, seed=12345)
+        counts[S[0]] += 1
+    exp = counts.sum() / 3
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 13.8  # p = 0.001 for 2 dof
+
+
+# ---------------------------------------------------------------- worked example
+
+def test_sort_system_reproduces_table1():
+    """The sorting system's rules and synapses give Table 1 entry for entry."""
+    d = synth.sort_system([3, 2, 1])
+    assert (dense_matrix(d) == load_table1()).all()
+
+
+def test_sort3_trace():
+    """Hand-derived computation of the sorting system on v = (3, 2, 1)."""
+    d = synth.sort_system([3, 2, 1])
+    tr = oracle.run_trace(d, 20)
+    assert len(tr) == 4                       # halts before step 4
+    C = [t[0].tolist() for t in tr]
+    S = [t[3].tolist() for t in tr]
+    #           i1 i2 i3 s1 s2 s3 o1 o2 o3
+    assert C[0] == [2, 1, 0, 3, 3, 3, 0, 0, 0]
+    assert C[1] == [1, 0, 0, 2, 2, 2, 1, 1, 1]
+    assert C[2] == [0, 0, 0, 1, 1, 1, 1, 2, 2]
+    assert C[3] == [0, 0, 0, 0, 0, 0, 1, 2, 3]
+    # rule ids: r1..r3 = 0..2, s1: r4 r5 r6 = 3 4 5, s2: r7 r8 r9 = 6 7 8, s3: 9 10 11
+    assert S[0] == [0, 1, 2, -1, -1, -1, -1, -1, -1]
+    assert S[1] == [0, 1, -1, 3, 7, 11, -1, -1, -1]
+    assert S[2] == [0, -1, -1, 4, 6, 10, -1, -1, -1]
+    assert S[3] == [-1, -1, -1, 5, 8, 9, -1, -1, -1]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_sort_closed_form(seed):
+    """o_k holds the k-th smallest input; the run takes max(v) + 1 steps."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 9))
+    v = rng.integers(1, 13, size=n).tolist()
+    d = synth.sort_system(v)
+    st = oracle.initial_state(d)
+    ex, _ = oracle.run(d, st, 1000)
+    assert ex == max(v) + 1
+    assert st[0][2 * n:].tolist() == sorted(v)
+
+
+def test_dense_formula_on_table1():
+    """Every step of the sorting system satisfies C_{k+1} = C_k + s_k . M_Pi
+    with M_Pi read from Table 1 and s_k the 0/1 vector of selected rules."""
+    M = load_table1()
+    for v in ([3, 2, 1], [1, 2, 3], [2, 2, 3]):
+        d = synth.sort_system(v)
+        st = oracle.initial_state(d)
+        for k in range(10):
+            c0 = st[0].astype(np.int64).copy()
+            S, _, halted = oracle.step(d, st, k)
+            if halted:
+                break
+            s = np.zeros(d.m, np.int64)
+            s[S[S >= 0]] = 1
+            assert (st[0] == c0 + s @ M).all()
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_dense_formula_random_delay_free(seed):
+    """Delay-free random systems: C_{k+1} = C_k + s_k . M_Pi every step,
+    for first-applicable and Philox selection."""
+    d = tiny_random(seed, q=6, delays=False)
+    M = dense_matrix(d)
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        st = oracle.initial_state(d)
+        for k in range(8):
+            c0 = st[0].astype(np.int64).copy()
+            S, _, halted = oracle.step(d, st, k, mode, seed=seed + 7)
+            if halted:
+                break
+            s = np.zeros(d.m, np.int64)
+            s[S[S >= 0]] = 1
+            assert (st[0] == c0 + s @ M).all()
+
+
+# ---------------------------------------------------------------- delays
+
+def test_delay_chain_traces():
+    """Hand traces: a rule fired at t with delay d consumes at t, keeps its
+    neuron closed for steps t..t+d-1 and emits at t+d."""
+    for dl in (1, 2, 3):
+        d = make_desc(2, [[(1, 0, 1, 1, dl)], []], [(0, 1)], [1, 0])
+        tr = oracle.run_trace(d, 20)
+        assert len(tr) == dl + 1
+        C, D, P, S = tr[0]
+        assert C.tolist() == [0, 0] and D.tolist() == [dl - 1, 0] and P.tolist() == [0, -1]
+        assert S.tolist() == [0, -1]
+        for t in range(1, dl):
+            C, D, P, S = tr[t]
+            assert C.tolist() == [0, 0] and D.tolist() == [dl - 1 - t, 0] and P.tolist() == [0, -1]
+            assert S.tolist() == [-1, -1]
+        C, D, P, S = tr[dl]
+        assert C.tolist() == [0, 1] and D.tolist() == [0, 0] and P.tolist() == [-1, -1]
+
+
+def test_spikes_to_closed_neuron_are_lost():
+    # n0: a -> a; 2   n2: a -> a; 0   synapses 2 -> 0, 0 -> 1
+    d = make_desc(3, [[(1, 0, 1, 1, 2)], [], [(1, 0, 1, 1, 0)]], [(2, 0), (0, 1)], [1, 0, 1])
+    tr = oracle.run_trace(d, 20)
+    assert len(tr) == 3
+    assert [t[0].tolist() for t in tr] == [[0, 0, 0], [0, 0, 0], [0, 1, 0]]
+    assert [t[1].tolist() for t in tr] == [[1, 0, 0], [0, 0, 0], [0, 0, 0]]
+    assert [t[2].tolist() for t in tr] == [[0, -1, -1], [0, -1, -1], [-1, -1, -1]]
+    assert [t[3].tolist() for t in tr] == [[0, -1, 1], [-1, -1, -1], [-1, -1, -1]]
+
+
+def test_reopened_neuron_receives_and_refires():
+    # n0: a -> a; 1   n1: sink   n2: a^2 -> a; 0   n3: a -> a; 0
+    # synapses 0 -> 1, 2 -> 0, 3 -> 2
+    d = make_desc(4, [[(1, 0, 1, 1, 1)], [], [(2, 0, 2, 1, 0)], [(1, 0, 1, 1, 0)]],
+                  [(0, 1), (2, 0), (3, 2)], [1, 0, 1, 1])
+    tr = oracle.run_trace(d, 20)
+    assert len(tr) == 4
+    assert [t[0].tolist() for t in tr] == [[0, 0, 2, 0], [1, 1, 0, 0], [0, 1, 0, 0], [0, 2, 0, 0]]
+    assert [t[1].tolist() for t in tr] == [[0] * 4] * 4
+    assert [t[2].tolist() for t in tr] == [[0, -1, -1, -1], [-1] * 4, [0, -1, -1, -1], [-1] * 4]
+    assert [t[3].tolist() for t in tr] == [[0, -1, -1, 2], [-1, -1, 1, -1], [0, -1, -1, -1],
+                                           [-1] * 4]
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_bookkeeping_with_delays(seed):
+    """Per step: the spike total changes by what open senders emit times their
+    out-degree, minus what is consumed, minus what lands on closed neurons;
+    a closed neuron's count does not change; every selection is applicable
+    and belongs to an idle open neuron; first-applicable picks the first."""
+    d = synth.random_system(300, 100 + seed, outdeg=(1, 8), rules=(2, 4), d_range=(0, 3), spikes=(0, 10))
+    outs = [d.syn_targets[d.syn_offsets[i]:d.syn_offsets[i + 1]] for i in range(d.q)]
+    mode = oracle.PHILOX if seed % 2 else oracle.FIRST
+    st = oracle.initial_state(d)
+    for k in range(30):
+        C0, D0, P0 = (x.copy() for x in st)
+        S, E, halted = oracle.step(d, st, k, mode, seed=seed)
+        if halted:
+            break
+        Ei = np.zeros(d.q, np.int64)
+        recv = np.ones(d.q, bool)
+        consumed = 0
+        for i in range(d.q):
+            if P0[i] != -1 and D0[i] == 0:
+                Ei[i] = d.rule_p[P0[i]]
+                assert S[i] == -1
+            elif P0[i] != -1:
+                recv[i] = False
+                assert S[i] == -1 and st[0][i] == C0[i]
+            elif S[i] != -1:
+                r = S[i]
+                assert d.rule_offsets[i] <= r < d.rule_offsets[i + 1]
+                assert regex_ok(C0[i], d.rule_k[r], d.rule_j[r], d.rule_c[r])
+                if mode == oracle.FIRST:
+                    for r2 in range(d.rule_offsets[i], r):
+                        assert not regex_ok(C0[i], d.rule_k[r2], d.rule_j[r2], d.rule_c[r2])
+                consumed += d.rule_c[r]
+                if d.rule_d[r] == 0:
+                    Ei[i] = d.rule_p[r]
+                else:
+                    recv[i] = False
+            else:
+                for r2 in range(d.rule_offsets[i], d.rule_offsets[i + 1]):
+                    assert not regex_ok(C0[i], d.rule_k[r2], d.rule_j[r2], d.rule_c[r2])
+        assert (E == Ei).all()
+        produced = sum(int(Ei[i]) * len(outs[i]) for i in range(d.q))
+        lost = sum(int(Ei[i]) * int((~recv[outs[i]]).sum()) for i in range(d.q))
+        assert int(st[0].astype(np.int64).sum() - C0.astype(np.int64).sum()) == produced - consumed - lost
+
+
+# ---------------------------------------------------------------- brute force
+
+def py_successors(d, C, D, P):
+    """Independent enumerator: every spiking vector of SV_k (one applicable
+    rule per idle open neuron, all combinations) and the state it leads to,
+    computed by pulling from in-neighbours.  Returns None at a fixed point."""
+    q = d.q
+    inn = [[] for _ in range(q)]
+    for i in range(q):
+        for e in range(d.syn_offsets[i], d.syn_offsets[i + 1]):
+            inn[d.syn_targets[e]].append(i)
+    choices = []
+    for i in range(q):
+        if P[i] == -1:
+            A = [r for r in range(d.rule_offsets[i], d.rule_offsets[i + 1])
+                 if regex_ok(C[i], d.rule_k[r], d.rule_j[r], d.rule_c[r])]
+            choices.append(A if A else [None])
+        else:
+            choices.append([None])
+    if all(ch == [None] for ch in choices) and all(p == -1 for p in P):
+        return None
+    res = []
+    for combo in itertools.product(*choices):
+        emit = [0] * q
+        recv = [True] * q
+        Cn, Dn, Pn = list(map(int, C)), list(map(int, D)), list(map(int, P))
+        for i in range(q):
+            if P[i] != -1 and D[i] == 0:
+                emit[i] = int(d.rule_p[P[i]]); Pn[i] = -1; Dn[i] = 0
+            elif P[i] != -1:
+                recv[i] = False; Dn[i] = D[i] - 1
+            elif combo[i] is not None:
+                r = combo[i]
+                Cn[i] -= int(d.rule_c[r])
+                if d.rule_d[r] == 0:
+                    emit[i] = int(d.rule_p[r])
+                else:
+                    recv[i] = False; Pn[i] = r; Dn[i] = int(d.rule_d[r]) - 1
+        for j in range(q):
+            if recv[j]:
+                Cn[j] += sum(emit[i] for i in inn[j])
+        forced = [choices[i].index(combo[i]) if combo[i] is not None else 0 for i in range(q)]
+        res.append((forced, (tuple(Cn), tuple(Dn), tuple(Pn))))
+    return res
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_bruteforce_tree(seed):
+    """On tiny systems the oracle's forced-choice step reproduces every branch
+    of the independent enumerator, and the FIRST / PHILOX runs are paths of
+    the computation tree."""
+    d = tiny_random(1000 + seed, q=int(np.random.default_rng(seed).integers(2, 6)))
+    frontier = [oracle.initial_state(d)]
+    for k in range(5):
+        nxt = []
+        for st in frontier:
+            succ = py_successors(d, *st)
+            assert oracle.is_halted(d, st[0], st[2]) == (succ is None)
+            if succ is None:
+                continue
+            for forced, expect in succ[:20]:
+                s2 = tuple(x.copy() for x in st)
+                oracle.step(d, s2, k, oracle.FORCED, forced=np.asarray(forced, np.int32))
+                assert (tuple(map(int, s2[0])), tuple(map(int, s2[1])), tuple(map(int, s2[2]))) == expect
+                nxt.append(s2)
+        frontier = nxt[:30]
+    # FIRST and PHILOX trajectories lie in the tree
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        st = oracle.initial_state(d)
+        for k in range(5):
+            succ = py_successors(d, *st)
+            S, _, halted = oracle.step(d, st, k, mode, seed=seed)
+            if succ is None:
+                assert halted
+                break
+            got = (tuple(map(int, st[0])), tuple(map(int, st[1])), tuple(map(int, st[2])))
+            assert got in {e for _, e in succ}
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_fixed_point_and_empty_system():
+    d = make_desc(3, [[], [(2, 0, 2, 1, 0)], []], [(1, 0)], [5, 1, 0])
+    st = oracle.initial_state(d)
+    ex, S = oracle.run(d, st, 10)
+    assert ex == 0 and (S == -1).all() and st[0].tolist() == [5, 1, 0]
+    d1 = make_desc(1, [[]], [], [0])
+    ex, _ = oracle.run(d1, oracle.initial_state(d1), 3)
+    assert ex == 0
+
+
+def test_overflow_is_detected():
+    d = make_desc(2, [[(1, 1, 1, 1000, 0)], []], [(0, 1)], [10, 2**31 - 600])
+    st = oracle.initial_state(d)
+    with pytest.raises(oracle.OracleOverflow):
+        oracle.run(d, st, 5)
+
+
+def test_forgetting_rule_needs_exact_count():
+    # forgetting a^2 -> lambda stored as k=c=2, j=0, p=0
+    d = make_desc(2, [[(2, 0, 2, 0, 0)], []], [(0, 1)], [3, 0])
+    ex, _ = oracle.run(d, oracle.initial_state(d), 5)
+    assert ex == 0
+    d2 = make_desc(2, [[(2, 0, 2, 0, 0)], []], [(0, 1)], [2, 0])
+    st = oracle.initial_state(d2)
+    ex, S = oracle.run(d2, st, 5)
+    assert ex == 1 and st[0].tolist() == [0, 0] and S.tolist() == [0, -1]
