@@ -1,0 +1,243 @@
+/*
+ * libsnp -- a GB300 (sm_103a) simulator of spiking neural P systems with
+ * delays over compressed sparse representations.
+ *
+ * Paper: J. Hernandez-Tello, M.A. Martinez-del-Amor, D. Orellana-Martin,
+ * F.G.C. Cabarle, "Sparse Spiking Neural-like Membrane Systems on Graphics
+ * Processing Units", IJNS 34(7) 2450038, 2024 (arXiv 2408.04343).
+ *
+ * Conventions for every call below:
+ *  - Every call returns an int status: SNP_OK (0) or one of SNP_ERR_*.  No
+ *    C++ exception crosses this boundary.  snp_last_error() returns a
+ *    thread-local message about the last failure on the calling thread.
+ *  - Input arrays are owned by the caller and copied before the call returns.
+ *  - Handles (snp_system, snp_batch) are owned by the library and released
+ *    with the matching destroy call.
+ *  - Output pointers may be host or device memory; the library asks the
+ *    CUDA runtime which one it was given.  Copies to host memory complete
+ *    before the call returns; copies to device memory are ordered on the
+ *    system's stream.
+ *  - All device work of a system is ordered on the stream given at creation
+ *    (options.stream; NULL = the legacy default stream).
+ *  - Neuron and rule numbering at this boundary is the caller's: neuron i
+ *    is position i of init_spikes, rule r is position r of the rule arrays.
+ *    Internally neurons are renumbered (sorted by in-degree); that order
+ *    never leaks out.
+ */
+#ifndef SNP_H
+#define SNP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SNP_OK 0
+#define SNP_ERR_INVALID 1     /* bad argument or malformed system          */
+#define SNP_ERR_OOM 2         /* device or host allocation failed          */
+#define SNP_ERR_CUDA 3        /* a CUDA runtime call failed                */
+#define SNP_ERR_TIMEOUT 4     /* a bounded device-side wait gave up        */
+#define SNP_ERR_OVERFLOW 5    /* a spike count left the int32 range        */
+#define SNP_ERR_BUSY 6        /* system is owned by an unfinished batch    */
+#define SNP_ERR_UNSUPPORTED 7 /* option combination not available          */
+
+/* ---- options ----------------------------------------------------------- */
+/* Representation of the transition matrix (Sec. 3):
+ *   SNP_FORM_OPT   -- the "Compressed"/"optimized" form: rule vector with
+ *                     (c, p) per rule plus per-neuron synapse lists;
+ *   SNP_FORM_ELL   -- the ELL form: per-rule columns of (neuron, value);
+ *   SNP_FORM_DENSE -- the uncompressed m x q matrix (the paper's "Sparse"
+ *                     format), a baseline for small systems only.          */
+#define SNP_FORM_OPT 0
+#define SNP_FORM_ELL 1
+#define SNP_FORM_DENSE 2
+/* Direction of spike propagation:
+ *   SNP_PROP_PULL -- every neuron sums over its in-neighbours (no atomics);
+ *   SNP_PROP_PUSH -- every emitter adds into its targets with atomics, as
+ *                    Algorithms 4 and 5 do (warp-aggregated).              */
+#define SNP_PROP_PULL 0
+#define SNP_PROP_PUSH 1
+/* Choice of one applicable rule per neuron (Sec. 5, SV_CALC/SAMPLE_ONE):
+ *   SNP_SELECT_FIRST  -- the lowest-index applicable rule (the paper's
+ *                        deterministic choice);
+ *   SNP_SELECT_PHILOX -- uniform over the applicable rules, drawn from
+ *                        Philox4x32-10 (Salmon et al., SC'11) at counter
+ *                        (k mod 2^32, i, k >> 32, 0) and key (seed mod 2^32,
+ *                        seed >> 32) for step k and neuron i: the index into
+ *                        the applicable list is floor(x0 * |A| / 2^32).    */
+#define SNP_SELECT_FIRST 0
+#define SNP_SELECT_PHILOX 1
+/* How snp_step runs its steps:
+ *   SNP_ENGINE_AUTO     -- library's choice by size;
+ *   SNP_ENGINE_LAUNCH   -- one grid-wide launch per step (CUDA graph of
+ *                          launches), every CTA working on one step;
+ *   SNP_ENGINE_RESIDENT -- one CTA owns the whole system and runs all steps
+ *                          in one launch with the spike emissions kept in
+ *                          shared memory (systems up to SNP_RESIDENT_MAX_Q). */
+#define SNP_ENGINE_AUTO 0
+#define SNP_ENGINE_LAUNCH 1
+#define SNP_ENGINE_RESIDENT 2
+#define SNP_RESIDENT_MAX_Q 262144
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Both
+ * callbacks are called on the thread that calls into the library.        */
+typedef struct snp_allocator {
+    void* (*alloc)(void* ctx, size_t bytes, void* stream); /* NULL = OOM */
+    void (*release)(void* ctx, void* ptr, size_t bytes, void* stream);
+    void* ctx;
+} snp_allocator;
+
+typedef struct snp_options {
+    int32_t form;     /* SNP_FORM_*                                   */
+    int32_t prop;     /* SNP_PROP_*                                   */
+    int32_t select;   /* SNP_SELECT_*                                 */
+    int32_t engine;   /* SNP_ENGINE_*                                 */
+    uint64_t seed;    /* Philox key of this system                    */
+    void* stream;     /* cudaStream_t; NULL = legacy default stream   */
+    const snp_allocator* alloc; /* NULL = cudaMalloc/cudaFree         */
+    int32_t threads;  /* CTA size hint for the kernels; 0 = default   */
+    int32_t reserved;
+} snp_options;
+
+/* A system Pi = (O, syn, sigma_1..sigma_q, i_out) (Sec. 2) as the user
+ * defines it (Sec. 5, "Initialization").  All arrays are HOST memory.
+ *
+ *   init_spikes[q]     n_i, the initial configuration C_0 (>= 0).
+ *   rule_offsets[q+1]  N_Pi: the rules of neuron i are rule_offsets[i] ..
+ *                      rule_offsets[i+1]-1 (rule_offsets[0] = 0, monotone,
+ *                      at most 32766 rules per neuron).
+ *   rule_k/j/c/p/d[m]  rule r is E/a^c -> a^p; d with the regular expression
+ *                      E = a^k (a^j)* (j = 0: exactly a^k).  The paper's
+ *                      three regex types map to (k = n, j = 0) for a^n,
+ *                      (k = 0, j = 1) for a* and (k = 1, j = 1) for a+.
+ *                      A forgetting rule a^s -> lambda is k = c = s, j = 0,
+ *                      p = 0, d = 0.  Ranges: k, j, c >= 0; 0 <= p <= 65535;
+ *                      0 <= d <= 65535; p = 0 requires d = 0.
+ *   num_syn            |syn|.
+ *   syn_offsets[q+1]   out-list of neuron i: syn_targets[syn_offsets[i] ..
+ *   syn_targets[]      syn_offsets[i+1]-1]; no self-loops, no duplicates.
+ *   out_neuron         i_out (kept, not used by the step).                */
+typedef struct snp_desc {
+    int32_t q;
+    const int32_t* init_spikes;
+    const int64_t* rule_offsets;
+    const int32_t* rule_k;
+    const int32_t* rule_j;
+    const int32_t* rule_c;
+    const int32_t* rule_p;
+    const int32_t* rule_d;
+    int64_t num_syn;
+    const int64_t* syn_offsets;
+    const int32_t* syn_targets;
+    int32_t out_neuron;
+} snp_desc;
+
+/* Sizes of a created system, for accounting and roofline arithmetic. */
+typedef struct snp_info {
+    int32_t q;
+    int32_t form, prop, select, engine;
+    int64_t m;
+    int64_t num_syn;
+    int64_t in_entries;      /* stored in-list entries incl. padding       */
+    int64_t out_entries;     /* stored out-list entries incl. padding      */
+    int64_t rule_words;      /* 32-bit words of the stored rule table      */
+    int64_t device_bytes;    /* device memory held by the system           */
+    int32_t max_rules;       /* largest |R_i|                              */
+    int32_t max_p;           /* largest p                                  */
+    int32_t compact_rules;   /* 1 if rules are stored in one word each     */
+    int32_t e_bits;          /* bits per stored emission in shared memory  */
+    uint64_t step;           /* absolute step counter k                    */
+} snp_info;
+
+typedef struct snp_system snp_system;
+typedef struct snp_batch snp_batch;
+
+/* Builds a system from its description (Sec. 5, "Initialization"): validates
+ * it, packs the rule vector RV_Pi, the neuron-rule map N_Pi and the synapse
+ * lists straight from the edge list (no dense intermediate), uploads them
+ * and sets C = C_0, D = 0, no pending rules, k = 0 (Alg. 1, INIT).
+ * Returns SNP_ERR_INVALID for malformed input (self-loop, duplicate synapse,
+ * out-of-range id or field), SNP_ERR_OOM when memory runs out.            */
+int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out);
+
+/* Releases a system and its device memory.  NULL is accepted.            */
+int snp_destroy(snp_system* sys);
+
+/* Runs up to n transition steps (Alg. 1's loop body: SV_CALC with the
+ * choice, STEP and UPDATE_DELAYS) and stops early at a fixed point, i.e.
+ * when no neuron is pending and no open neuron has an applicable rule.
+ * If steps_done is not NULL the call waits for the device and stores the
+ * number of steps executed; if it is NULL the call returns once the work is
+ * queued on the system's stream.  Returns SNP_ERR_OVERFLOW when a spike
+ * count left the int32 range (checked when the call waits).              */
+int snp_step(snp_system* sys, int64_t n, int64_t* steps_done);
+
+/* C_k: spikes per neuron, out[q].                                          */
+int snp_get_config(const snp_system* sys, int32_t* out, int64_t len);
+/* S_k of the last executed step: per neuron the global id of the rule it
+ * selected at that step, or -1 (Sec. 3, the Compressed spiking vector of
+ * length q with 0-based rule ids).  All -1 before the first step.         */
+int snp_get_spiking(const snp_system* sys, int32_t* out, int64_t len);
+/* D_k: per neuron the number of steps before it reopens, 0 = open (Sec. 2,
+ * delays vector).                                                          */
+int snp_get_status(const snp_system* sys, int32_t* out, int64_t len);
+/* Pending delayed rule per neuron (global rule id) or -1.                 */
+int snp_get_pending(const snp_system* sys, int32_t* out, int64_t len);
+/* Checkpoint: (C, D, P) as above plus the absolute step counter k.  Any
+ * of C, D, P may be NULL.  set_state validates ranges (pending rule must
+ * belong to its neuron; D > 0 only with a pending rule).                  */
+int snp_get_state(const snp_system* sys, int32_t* C, int32_t* D, int32_t* P, int64_t len,
+                  uint64_t* step);
+int snp_set_state(snp_system* sys, const int32_t* C, const int32_t* D, const int32_t* P,
+                  int64_t len, uint64_t step);
+int snp_get_info(const snp_system* sys, snp_info* info);
+
+/* ---- batched and served forms ----------------------------------------- */
+/* A batch runs many independent systems in one persistent launch, each
+ * system owned by one CTA for all its steps, systems taken largest first
+ * from a device work counter.  mem_budget (bytes) bounds the device memory
+ * of the systems a batch keeps admitted at once; 0 = no bound.            */
+int snp_batch_create(const snp_options* opts, size_t mem_budget, snp_batch** out);
+int snp_batch_destroy(snp_batch* b);
+/* Queues count systems, each to advance steps[i] steps (stopping early at
+ * a fixed point).  The systems must have been created with the same form
+ * and must not be stepped or read until the ticket completes (calls on them
+ * return SNP_ERR_BUSY meanwhile).  Work is admitted as memory allows and
+ * overlaps with work already running.                                     */
+int snp_batch_submit(snp_batch* b, snp_system* const* sys, const int64_t* steps, int32_t count,
+                     int64_t* ticket);
+int snp_batch_poll(snp_batch* b, int64_t ticket, int* done);
+int snp_batch_wait(snp_batch* b, int64_t ticket);
+/* Executed steps of system `index` of a completed ticket.                 */
+int snp_batch_steps_done(snp_batch* b, int64_t ticket, int32_t index, int64_t* steps_done);
+
+/* ---- paper formats, host only (inspection and memory accounting) -------- */
+/* The paper's matrices for a system, written densely on the host:
+ *   snp_export_dense: M_Pi, m x q row-major (Table 1 layout);
+ *   snp_export_ell:   M^s_Pi, z' = max out-degree + 1 rows x m columns,
+ *                     row-major, values[] and neurons[] with -1 neuron for
+ *                     null; the consumption pair (-c, own neuron) is row 0
+ *                     (Table 2 layout);
+ *   snp_export_compressed: Sy_Pi, z = max out-degree rows x q columns,
+ *                     row-major, -1 for null (Table 3 layout).
+ * rows_out (may be NULL) receives the number of rows; capacity is the
+ * number of int32 elements each output array holds.                       */
+int snp_export_dense(const snp_desc* desc, int32_t* M, int64_t capacity);
+int snp_export_ell(const snp_desc* desc, int32_t* values, int32_t* neurons, int64_t capacity,
+                   int64_t* rows_out);
+int snp_export_compressed(const snp_desc* desc, int32_t* sy, int64_t capacity, int64_t* rows_out);
+/* Element counts of the paper's three formats (Sec. 6):
+ *   SNP_FORM_DENSE: m q + 3m + 2q + 1; SNP_FORM_ELL: m (2z + 5) + 2q + 1;
+ *   SNP_FORM_OPT: q (z + 3) + 4m + 1, z = max out-degree.                 */
+int64_t snp_paper_format_elements(int32_t form, int64_t q, int64_t m, int64_t z);
+
+const char* snp_strerror(int status);
+const char* snp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNP_H */

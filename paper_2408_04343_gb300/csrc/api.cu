@@ -1,0 +1,451 @@
+// C-ABI of libsnp: system life cycle, stepping, state access.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "snp_internal.h"
+#include "system.h"
+
+namespace snp {
+
+const char* last_error();
+
+// ---- device memory -----------------------------------------------------
+
+void* sys_alloc(snp_system* s, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (s->alloc.alloc) {
+        p = s->alloc.alloc(s->alloc.ctx, bytes, (void*)s->stream);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        s->allocs.push_back({p, bytes});
+        s->device_bytes += bytes;
+    }
+    return p;
+}
+
+static void sys_free_all(snp_system* s) {
+    for (auto& a : s->allocs) {
+        if (s->alloc.release)
+            s->alloc.release(s->alloc.ctx, a.first, a.second, (void*)s->stream);
+        else
+            cudaFree(a.first);
+    }
+    s->allocs.clear();
+    s->device_bytes = 0;
+}
+
+template <typename T>
+static T* upload(snp_system* s, const std::vector<T>& v, int* err) {
+    T* p = (T*)sys_alloc(s, v.size() * sizeof(T));
+    if (!p) {
+        *err = fail(SNP_ERR_OOM, "device allocation failed");
+        return nullptr;
+    }
+    if (!v.empty() && cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+        *err = fail(SNP_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(cudaGetLastError()));
+        return nullptr;
+    }
+    return p;
+}
+
+static int cuda_fail(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    return fail(SNP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- chunk graphs of the grid-wide engine ------------------------------
+
+static int build_chunk_graph(snp_system* s) {
+    if (s->chunk_exec) return SNP_OK;
+    if (!s->cap_stream && cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail("stream create");
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return cuda_fail("begin capture");
+    const bool compact = s->compact;
+    const int sel = s->opt.select;
+    for (int t = 0; t < kChunk; ++t) {
+        if (s->opt.prop == SNP_PROP_PUSH)
+            launch_push_step(s->dev, t, s->cap_stream, compact, sel);
+        else
+            launch_pull(s->dev, kPullFused, t, s->cap_stream, compact, sel);
+    }
+    launch_advance(s->dev, kChunk, s->cap_stream);
+    if (cudaStreamEndCapture(s->cap_stream, &g) != cudaSuccess) return cuda_fail("end capture");
+    cudaError_t e = cudaGraphInstantiate(&s->chunk_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->chunk_exec = nullptr;
+        return cuda_fail("graph instantiate");
+    }
+    return SNP_OK;
+}
+
+static int step_launch_engine(snp_system* s, int64_t n) {
+    const bool compact = s->compact;
+    const int sel = s->opt.select;
+    cudaStream_t st = s->stream;
+    if (launch_begin(s->dev, st) != cudaSuccess) return cuda_fail("begin");
+    if (s->opt.prop == SNP_PROP_PUSH) {
+        int64_t left = n;
+        if (left >= kChunk) {
+            int rc = build_chunk_graph(s);
+            if (rc) return rc;
+        }
+        while (left >= kChunk) {
+            if (cudaGraphLaunch(s->chunk_exec, st) != cudaSuccess) return cuda_fail("graph launch");
+            left -= kChunk;
+        }
+        for (int64_t t = 0; t < left; ++t)
+            if (launch_push_step(s->dev, (int32_t)t, st, compact, sel) != cudaSuccess) return cuda_fail("push step");
+        if (launch_finish(s->dev, (int32_t)left, st) != cudaSuccess) return cuda_fail("finish");
+        return SNP_OK;
+    }
+    if (launch_pull(s->dev, kPullSelectOnly, 0, st, compact, sel) != cudaSuccess) return cuda_fail("select");
+    int64_t rem = n - 1;
+    if (rem >= kChunk) {
+        int rc = build_chunk_graph(s);
+        if (rc) return rc;
+    }
+    while (rem >= kChunk) {
+        if (cudaGraphLaunch(s->chunk_exec, st) != cudaSuccess) return cuda_fail("graph launch");
+        rem -= kChunk;
+    }
+    for (int64_t t = 0; t < rem; ++t)
+        if (launch_pull(s->dev, kPullFused, (int32_t)t, st, compact, sel) != cudaSuccess) return cuda_fail("step");
+    if (launch_pull(s->dev, kPullGatherOnly, (int32_t)rem, st, compact, sel) != cudaSuccess) return cuda_fail("gather");
+    if (launch_finish(s->dev, (int32_t)(rem + 1), st) != cudaSuccess) return cuda_fail("finish");
+    return SNP_OK;
+}
+
+bool resident_fits(const snp_system* s, ResidentPlan* plan) {
+    const int eb = resident_e_bits(s->max_p);
+    const size_t smem = resident_smem_bytes(s->q, eb);
+    if ((long long)smem + 1024 > (long long)resident_max_smem()) return false;
+    if (plan) {
+        plan->e_bits = eb;
+        plan->max_q = s->q;
+        plan->smem = smem;
+        plan->threads = s->opt.threads > 0 ? s->opt.threads : 1024;
+        plan->ctas = 1;
+    }
+    return true;
+}
+
+static int step_resident(snp_system* s, int64_t n) {
+    ResidentPlan plan;
+    if (!resident_fits(s, &plan))
+        return fail(SNP_ERR_UNSUPPORTED, "system too large for the resident engine (shared memory)");
+    if (cudaMemcpyAsync(s->d_nsteps, &n, sizeof(long long), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        return cuda_fail("nsteps upload");
+    if (cudaMemsetAsync(s->d_work, 0, sizeof(unsigned int), s->stream) != cudaSuccess) return cuda_fail("work reset");
+    if (launch_resident(s->d_self, s->d_nsteps, 1, s->d_work, plan, s->compact, s->opt.select, s->stream) != cudaSuccess)
+        return cuda_fail("resident launch");
+    return SNP_OK;
+}
+
+int effective_engine(const snp_system* s) {
+    if (s->opt.prop == SNP_PROP_PUSH) return SNP_ENGINE_LAUNCH;
+    if (s->opt.engine == SNP_ENGINE_RESIDENT) return SNP_ENGINE_RESIDENT;
+    if (s->opt.engine == SNP_ENGINE_LAUNCH) return SNP_ENGINE_LAUNCH;
+    return (s->q <= kAutoResidentMaxQ && resident_fits(s, nullptr)) ? SNP_ENGINE_RESIDENT : SNP_ENGINE_LAUNCH;
+}
+
+int read_flags(snp_system* s, int64_t* exec) {
+    uint32_t fl[kNumFlags];
+    unsigned long long steps[kNumStepWords];
+    if (cudaMemcpyAsync(fl, s->dev.flags, sizeof(fl), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(steps, s->dev.step, sizeof(steps), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return cuda_fail("flag read");
+    if (exec) *exec = (int64_t)steps[kStepExec];
+    s->host_step = steps[kStepBase];
+    if (fl[kFlagOverflow]) {
+        const uint32_t zero = 0;
+        cudaMemcpyAsync(s->dev.flags + kFlagOverflow, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream);
+        cudaStreamSynchronize(s->stream);
+        return fail(SNP_ERR_OVERFLOW, "a spike count left the int32 range");
+    }
+    if (fl[kFlagTimeout]) return fail(SNP_ERR_TIMEOUT, "a bounded device wait gave up");
+    return SNP_OK;
+}
+
+int run_steps(snp_system* s, int64_t n) {
+    if (n <= 0) return SNP_OK;
+    return effective_engine(s) == SNP_ENGINE_RESIDENT ? step_resident(s, n) : step_launch_engine(s, n);
+}
+
+}  // namespace snp
+
+using namespace snp;
+
+extern "C" {
+
+const char* snp_strerror(int st) {
+    switch (st) {
+        case SNP_OK: return "ok";
+        case SNP_ERR_INVALID: return "invalid argument or malformed system";
+        case SNP_ERR_OOM: return "out of memory";
+        case SNP_ERR_CUDA: return "CUDA runtime error";
+        case SNP_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SNP_ERR_OVERFLOW: return "spike count overflowed int32";
+        case SNP_ERR_BUSY: return "system is owned by an unfinished batch";
+        case SNP_ERR_UNSUPPORTED: return "unsupported option combination";
+        default: return "unknown status";
+    }
+}
+
+const char* snp_last_error(void) { return snp::last_error(); }
+
+int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) {
+    if (!out) return fail(SNP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int st = validate_desc(desc);
+    if (st) return st;
+    snp_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.form != SNP_FORM_OPT) return fail(SNP_ERR_UNSUPPORTED, "only SNP_FORM_OPT is built in this library");
+    if (o.prop != SNP_PROP_PULL && o.prop != SNP_PROP_PUSH) return fail(SNP_ERR_INVALID, "bad prop");
+    if (o.select != SNP_SELECT_FIRST && o.select != SNP_SELECT_PHILOX) return fail(SNP_ERR_INVALID, "bad select");
+    if (o.engine < SNP_ENGINE_AUTO || o.engine > SNP_ENGINE_RESIDENT) return fail(SNP_ERR_INVALID, "bad engine");
+    if (o.prop == SNP_PROP_PUSH && o.engine == SNP_ENGINE_RESIDENT)
+        return fail(SNP_ERR_UNSUPPORTED, "the resident engine is pull-only");
+
+    snp_system* s = new (std::nothrow) snp_system();
+    if (!s) return fail(SNP_ERR_OOM, "host allocation failed");
+    s->opt = o;
+    s->stream = (cudaStream_t)o.stream;
+    if (o.alloc) s->alloc = *o.alloc;
+    HostPack hp;
+    st = pack_system(desc, o.prop == SNP_PROP_PUSH, kSortWindow, &hp);
+    if (st) {
+        delete s;
+        return st;
+    }
+    s->q = hp.q;
+    s->m = hp.m;
+    s->nsyn = hp.nsyn;
+    s->max_p = hp.max_p;
+    s->max_rules = hp.max_rules;
+    s->compact = hp.compact;
+    s->in_entries = (int64_t)hp.in_idx.size();
+    s->out_entries = (int64_t)hp.out_idx.size();
+    s->rule_words = (int64_t)hp.rules.size();
+    s->perm = hp.perm;
+    s->rule_offsets.assign(desc->rule_offsets, desc->rule_offsets + (size_t)desc->q + 1);
+
+    int err = SNP_OK;
+    DevSys& d = s->dev;
+    d.q = hp.q;
+    d.nslices = (hp.q + kSlice - 1) / kSlice;
+    d.slice_ptr = upload(s, hp.slice_ptr, &err);
+    if (!err) d.in_idx = upload(s, hp.in_idx, &err);
+    if (!err && o.prop == SNP_PROP_PUSH) {
+        d.out_ptr = upload(s, hp.out_ptr, &err);
+        if (!err) d.out_idx = upload(s, hp.out_idx, &err);
+    }
+    if (!err) d.rule_off = upload(s, hp.rule_off, &err);
+    if (!err) d.rules = upload(s, hp.rules, &err);
+    if (!err) d.orig = upload(s, hp.perm, &err);
+    if (!err) s->d_rule_base = upload(s, hp.rule_base, &err);
+    if (!err) d.C = upload(s, hp.C0, &err);
+    if (!err) {
+        std::vector<uint32_t> zeros((size_t)hp.q, 0u);
+        d.st = upload(s, zeros, &err);
+    }
+    if (!err) {
+        std::vector<int32_t> ez((size_t)hp.q + 1, 0), sm((size_t)hp.q, -1);
+        for (int b = 0; b < 2 && !err; ++b) {
+            d.E[b] = upload(s, ez, &err);
+            if (!err) d.S[b] = upload(s, sm, &err);
+        }
+    }
+    if (!err) {
+        std::vector<uint32_t> fz(kNumFlags, 0u);
+        d.flags = upload(s, fz, &err);
+    }
+    if (!err) {
+        std::vector<unsigned long long> sz(kNumStepWords, 0ull);
+        d.step = upload(s, sz, &err);
+    }
+    if (!err) {
+        s->scratch = (int32_t*)sys_alloc(s, sizeof(int32_t) * (size_t)hp.q);
+        s->d_nsteps = (long long*)sys_alloc(s, sizeof(long long));
+        s->d_work = (unsigned int*)sys_alloc(s, sizeof(unsigned int));
+        s->d_self = (DevSys*)sys_alloc(s, sizeof(DevSys));
+        if (!s->scratch || !s->d_nsteps || !s->d_work || !s->d_self) err = fail(SNP_ERR_OOM, "device allocation failed");
+    }
+    d.seed = o.seed;
+    d.select = o.select;
+    d.max_p = hp.max_p;
+    if (!err && cudaMemcpyAsync(s->d_self, &d, sizeof(DevSys), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        err = cuda_fail("descriptor upload");
+    if (!err && cudaStreamSynchronize(s->stream) != cudaSuccess) err = cuda_fail("create sync");
+    if (err) {
+        sys_free_all(s);
+        delete s;
+        return err;
+    }
+    *out = s;
+    return SNP_OK;
+}
+
+int snp_destroy(snp_system* s) {
+    if (!s) return SNP_OK;
+    if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    else cudaDeviceSynchronize();
+    if (s->chunk_exec) cudaGraphExecDestroy(s->chunk_exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    sys_free_all(s);
+    delete s;
+    return SNP_OK;
+}
+
+int snp_step(snp_system* s, int64_t n, int64_t* steps_done) {
+    if (!s) return fail(SNP_ERR_INVALID, "system is NULL");
+    if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
+    if (n < 0) return fail(SNP_ERR_INVALID, "n < 0");
+    if (steps_done) *steps_done = 0;
+    if (n == 0) return SNP_OK;
+    int rc = run_steps(s, n);
+    if (rc) return rc;
+    if (steps_done) return read_flags(s, steps_done);
+    return SNP_OK;
+}
+
+static int export_vec(const snp_system* sc, int what, int32_t* out, int64_t len) {
+    snp_system* s = const_cast<snp_system*>(sc);
+    if (!s || !out) return fail(SNP_ERR_INVALID, "NULL argument");
+    if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
+    if (len < s->q) return fail(SNP_ERR_INVALID, "output shorter than q");
+    const bool dev = is_device_ptr(out);
+    int32_t* dst = dev ? out : s->scratch;
+    if (launch_export(s->dev, s->d_rule_base, what, dst, -1, s->stream) != cudaSuccess) return cuda_fail("export");
+    if (!dev) {
+        if (cudaMemcpyAsync(out, s->scratch, sizeof(int32_t) * (size_t)s->q, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            return cuda_fail("export copy");
+    }
+    return SNP_OK;
+}
+
+int snp_get_config(const snp_system* s, int32_t* out, int64_t len) { return export_vec(s, kExportConfig, out, len); }
+int snp_get_spiking(const snp_system* s, int32_t* out, int64_t len) { return export_vec(s, kExportSpiking, out, len); }
+int snp_get_status(const snp_system* s, int32_t* out, int64_t len) { return export_vec(s, kExportStatus, out, len); }
+int snp_get_pending(const snp_system* s, int32_t* out, int64_t len) { return export_vec(s, kExportPending, out, len); }
+
+int snp_get_state(const snp_system* s, int32_t* C, int32_t* D, int32_t* P, int64_t len, uint64_t* step) {
+    if (!s) return fail(SNP_ERR_INVALID, "system is NULL");
+    int rc;
+    if (C && (rc = snp_get_config(s, C, len))) return rc;
+    if (D && (rc = snp_get_status(s, D, len))) return rc;
+    if (P && (rc = snp_get_pending(s, P, len))) return rc;
+    if (step) {
+        unsigned long long v = 0;
+        if (cudaMemcpyAsync(&v, s->dev.step + kStepBase, sizeof(v), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            return cuda_fail("step read");
+        *step = v;
+    }
+    return SNP_OK;
+}
+
+static int fetch_host(const int32_t* src, int64_t q, std::vector<int32_t>& dst, snp_system* s) {
+    dst.resize((size_t)q);
+    if (is_device_ptr(src)) {
+        if (cudaMemcpyAsync(dst.data(), src, sizeof(int32_t) * (size_t)q, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            return cuda_fail("state fetch");
+    } else {
+        std::memcpy(dst.data(), src, sizeof(int32_t) * (size_t)q);
+    }
+    return SNP_OK;
+}
+
+int snp_set_state(snp_system* s, const int32_t* C, const int32_t* D, const int32_t* P, int64_t len, uint64_t step) {
+    if (!s || !C || !D || !P) return fail(SNP_ERR_INVALID, "NULL argument");
+    if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
+    if (len < s->q) return fail(SNP_ERR_INVALID, "state shorter than q");
+    std::vector<int32_t> hc, hd, hpv;
+    int rc;
+    if ((rc = fetch_host(C, s->q, hc, s)) || (rc = fetch_host(D, s->q, hd, s)) || (rc = fetch_host(P, s->q, hpv, s)))
+        return rc;
+    std::vector<int32_t> c_slot((size_t)s->q);
+    std::vector<uint32_t> st_slot((size_t)s->q);
+    for (int32_t slot = 0; slot < s->q; ++slot) {
+        const int32_t i = s->perm[slot];
+        if (hc[i] < 0) return fail(SNP_ERR_INVALID, "negative spike count at neuron " + std::to_string(i));
+        if (hd[i] < 0 || hd[i] > kMaxDelay) return fail(SNP_ERR_INVALID, "D out of range at neuron " + std::to_string(i));
+        uint32_t w = 0;
+        if (hpv[i] == -1) {
+            if (hd[i] != 0) return fail(SNP_ERR_INVALID, "D > 0 without a pending rule at neuron " + std::to_string(i));
+        } else {
+            const int64_t r0 = s->rule_offsets[i], r1 = s->rule_offsets[i + 1];
+            if (hpv[i] < r0 || hpv[i] >= r1)
+                return fail(SNP_ERR_INVALID, "pending rule does not belong to neuron " + std::to_string(i));
+            w = ((uint32_t)(hpv[i] - r0 + 1) << kPendShift) | (uint32_t)hd[i];
+        }
+        c_slot[slot] = hc[i];
+        st_slot[slot] = w;
+    }
+    std::vector<int32_t> sm((size_t)s->q, -1);
+    unsigned long long steps[kNumStepWords] = {step, step, 0ull, 0ull};
+    uint32_t fz[kNumFlags] = {0};
+    if (cudaMemcpyAsync(s->dev.C, c_slot.data(), sizeof(int32_t) * c_slot.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->dev.st, st_slot.data(), sizeof(uint32_t) * st_slot.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->dev.S[0], sm.data(), sizeof(int32_t) * sm.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->dev.S[1], sm.data(), sizeof(int32_t) * sm.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->dev.step, steps, sizeof(steps), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->dev.flags, fz, sizeof(fz), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return cuda_fail("state upload");
+    return SNP_OK;
+}
+
+int snp_get_info(const snp_system* s, snp_info* info) {
+    if (!s || !info) return fail(SNP_ERR_INVALID, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->q = s->q;
+    info->form = s->opt.form;
+    info->prop = s->opt.prop;
+    info->select = s->opt.select;
+    info->engine = effective_engine(s);
+    info->m = s->m;
+    info->num_syn = s->nsyn;
+    info->in_entries = s->in_entries;
+    info->out_entries = s->out_entries;
+    info->rule_words = s->rule_words;
+    info->device_bytes = (int64_t)s->device_bytes;
+    info->max_rules = s->max_rules;
+    info->max_p = s->max_p;
+    info->compact_rules = s->compact ? 1 : 0;
+    info->e_bits = resident_e_bits(s->max_p);
+    info->step = s->host_step;
+    return SNP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,39 @@
+// Host-side launchers of the libsnp kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "snp_internal.h"
+
+namespace snp {
+
+enum PullKind : int { kPullSelectOnly = 0, kPullFused = 1, kPullGatherOnly = 2 };
+enum ExportWhat : int { kExportConfig = 0, kExportStatus = 1, kExportPending = 2, kExportSpiking = 3 };
+
+// Grid-wide engine (kernels_step.cu).  t is the step index relative to the
+// system's device base step k.
+cudaError_t launch_pull(const DevSys& s, int kind, int32_t t, cudaStream_t st, bool compact, int sel);
+cudaError_t launch_push_step(const DevSys& s, int32_t t, cudaStream_t st, bool compact, int sel);
+cudaError_t launch_begin(const DevSys& s, cudaStream_t st);
+cudaError_t launch_advance(const DevSys& s, int32_t count, cudaStream_t st);
+cudaError_t launch_finish(const DevSys& s, int32_t tail, cudaStream_t st);
+cudaError_t launch_export(const DevSys& s, const int32_t* rule_base, int what, int32_t* out, int parity,
+                          cudaStream_t st);
+
+// CTA-resident engine (kernels_resident.cu): each CTA takes whole systems
+// from `work` (largest first as listed) and runs all their steps.
+struct ResidentPlan {
+    int threads;     // CTA size
+    int e_bits;      // bits per emission in shared memory (4, 8, 16 or 32)
+    int max_q;       // largest system of the launch
+    int ctas;        // grid size
+    size_t smem;     // dynamic shared memory per CTA
+};
+int resident_e_bits(int max_p);
+size_t resident_smem_bytes(int max_q, int e_bits);
+cudaError_t launch_resident(const DevSys* d_systems, const long long* d_nsteps, int nsys, unsigned int* d_work,
+                            const ResidentPlan& plan, bool compact, int sel, cudaStream_t st);
+int resident_max_smem();
+cudaError_t launch_gather_results(const DevSys* d_systems, int nsys, unsigned long long* d_out, cudaStream_t st);
+
+}  // namespace snp

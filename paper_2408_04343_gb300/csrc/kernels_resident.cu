@@ -1,0 +1,225 @@
+// CTA-resident engine: one CTA owns one whole system and runs all its steps.
+//
+// Used for the batched form (thousands of independent systems in one
+// persistent launch, each CTA taking the next system from a device work
+// counter, largest first) and for single systems small enough that their
+// emission vector fits in shared memory.
+//
+// Per step and system the CTA makes one pass over its slices (one warp per
+// slice, one lane per neuron) that gathers step k and selects step k+1, the
+// same fusion as the grid-wide engine.  The emission vectors E_k and E_{k+1}
+// live in shared memory, bit-packed at e_bits per neuron, so the random
+// in-neighbour reads of the gather never leave the SM.  __syncthreads_or at
+// the end of a pass is both the barrier between steps and the fixed-point
+// test (Alg. 1 stop condition).
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace snp {
+
+template <int EB>
+__device__ __forceinline__ int32_t e_get(const uint32_t* __restrict__ e, int32_t i) {
+    if (EB == 32) return (int32_t)e[i];
+    constexpr uint32_t mask = (1u << EB) - 1u;
+    const uint32_t bit = (uint32_t)i * EB;
+    return (int32_t)((e[bit >> 5] >> (bit & 31u)) & mask);
+}
+
+// All 32 lanes call this for one slice; lane l contributes slot 32*slice+l.
+template <int EB>
+__device__ __forceinline__ void e_put_slice(uint32_t* e, int32_t slice, int lane, int32_t v) {
+    if (EB == 32) {
+        e[slice * 32 + lane] = (uint32_t)v;
+        return;
+    }
+    constexpr int per = 32 / EB;  // neurons per word
+    uint32_t w = ((uint32_t)v) << ((lane % per) * EB);
+#pragma unroll
+    for (int off = 1; off < per; off <<= 1) w |= __shfl_xor_sync(0xffffffffu, w, off);
+    if (lane % per == 0) e[slice * EB + lane / per] = w;
+}
+
+template <bool COMPACT, int SEL, int EB>
+__device__ void run_resident(const DevSys& s, long long n, uint32_t* esm) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int words = (int)(((long long)(s.nslices * 32 + 32) * EB + 31) / 32);
+    uint32_t* Eb[2] = {esm, esm + words};
+    for (int i = threadIdx.x; i < 2 * words; i += blockDim.x) esm[i] = 0u;
+    const unsigned long long base = s.step[kStepBase];
+    __syncthreads();
+
+    // select pass for step `base`
+    bool act = false;
+    for (int32_t slice = warp; slice < s.nslices; slice += nwarps) {
+        const int32_t slot = slice * kSlice + lane;
+        int32_t emit = 0;
+        if (slot < s.q) {
+            const SelOut o = select_neuron<COMPACT, SEL>(
+                s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), s.C[slot], s.st[slot], base,
+                SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
+            s.C[slot] = o.c_after;
+            s.st[slot] = o.st;
+            s.S[base & 1ull][slot] = o.s;
+            emit = o.emit;
+            act |= o.active;
+        }
+        e_put_slice<EB>(Eb[base & 1ull], slice, lane, emit);
+    }
+    bool any = __syncthreads_or(act);
+
+    long long exec = 0;
+    bool halted = false;
+    for (long long t = 0; t < n; ++t) {
+        if (!any) {
+            halted = true;
+            break;
+        }
+        const unsigned long long kg = base + (unsigned long long)t;
+        const bool do_sel = (t + 1) < n;
+        const uint32_t* __restrict__ Ek = Eb[kg & 1ull];
+        uint32_t* En = Eb[(kg + 1ull) & 1ull];
+        act = false;
+        for (int32_t slice = warp; slice < s.nslices; slice += nwarps) {
+            const int32_t slot = slice * kSlice + lane;
+            const bool valid = slot < s.q;
+            int32_t c = 0;
+            uint32_t st = 0u;
+            if (valid) {
+                c = s.C[slot];
+                st = s.st[slot];
+            }
+            const int32_t b = __ldg(s.slice_ptr + slice);
+            const int32_t w = __ldg(s.slice_ptr + slice + 1) - b;
+            const int32_t* __restrict__ p = s.in_idx + (size_t)b * kSlice + lane;
+            long long sum = 0;
+            int32_t col = 0;
+            for (; col + 4 <= w; col += 4) {
+                const int32_t i0 = __ldg(p + (col + 0) * kSlice);
+                const int32_t i1 = __ldg(p + (col + 1) * kSlice);
+                const int32_t i2 = __ldg(p + (col + 2) * kSlice);
+                const int32_t i3 = __ldg(p + (col + 3) * kSlice);
+                sum += (long long)e_get<EB>(Ek, i0) + e_get<EB>(Ek, i1) + e_get<EB>(Ek, i2) + e_get<EB>(Ek, i3);
+            }
+            for (; col < w; ++col) sum += e_get<EB>(Ek, __ldg(p + col * kSlice));
+            if (valid && (st >> kPendShift) == 0u) {
+                long long nc = (long long)c + sum;
+                if (nc > 2147483647ll) {
+                    atomicOr(s.flags + kFlagOverflow, 1u);
+                    nc = 2147483647ll;
+                }
+                c = (int32_t)nc;
+            }
+            int32_t emit = 0;
+            if (do_sel && valid) {
+                const SelOut o = select_neuron<COMPACT, SEL>(
+                    s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), c, st, kg + 1ull,
+                    SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
+                c = o.c_after;
+                s.st[slot] = o.st;
+                s.S[(kg + 1ull) & 1ull][slot] = o.s;
+                emit = o.emit;
+                act |= o.active;
+            }
+            if (valid) s.C[slot] = c;
+            if (do_sel) e_put_slice<EB>(En, slice, lane, emit);
+        }
+        ++exec;
+        any = __syncthreads_or(act);
+    }
+    if (threadIdx.x == 0) {
+        s.step[kStepCallStart] = base;
+        s.step[kStepBase] = base + (unsigned long long)exec;
+        s.step[kStepExec] = (unsigned long long)exec;
+        s.step[kStepHalt] = halted ? base + (unsigned long long)exec : 0ull;
+        s.flags[kFlagHalted] = halted ? 1u : 0u;
+    }
+}
+
+template <bool COMPACT, int SEL, int EB>
+__global__ void __launch_bounds__(1024) k_resident(const DevSys* __restrict__ systems,
+                                                   const long long* __restrict__ nsteps, int nsys,
+                                                   unsigned int* work) {
+    extern __shared__ uint32_t esm[];
+    __shared__ int s_id;
+    for (;;) {
+        if (threadIdx.x == 0) s_id = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int id = s_id;
+        if (id >= nsys) return;
+        const DevSys s = systems[id];
+        run_resident<COMPACT, SEL, EB>(s, nsteps[id], esm);
+        __syncthreads();
+    }
+}
+
+// Per-system results of a batch launch: base step, executed steps, overflow.
+__global__ void k_gather_results(const DevSys* __restrict__ systems, int nsys, unsigned long long* out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nsys) return;
+    const DevSys& s = systems[r];
+    out[3 * r + 0] = s.step[kStepBase];
+    out[3 * r + 1] = s.step[kStepExec];
+    out[3 * r + 2] = s.flags[kFlagOverflow];
+}
+
+cudaError_t launch_gather_results(const DevSys* d_systems, int nsys, unsigned long long* d_out, cudaStream_t st) {
+    if (nsys <= 0) return cudaSuccess;
+    k_gather_results<<<(nsys + 255) / 256, 256, 0, st>>>(d_systems, nsys, d_out);
+    return cudaGetLastError();
+}
+
+int resident_e_bits(int max_p) {
+    if (max_p < 16) return 4;
+    if (max_p < 256) return 8;
+    return 16;
+}
+
+size_t resident_smem_bytes(int max_q, int e_bits) {
+    const long long nslices = ((long long)max_q + 31) / 32;
+    const long long words = ((nslices * 32 + 32) * e_bits + 31) / 32;
+    return (size_t)(2 * words * 4);
+}
+
+int resident_max_smem() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+template <bool C, int S, int EB>
+static cudaError_t launch_res_t(const DevSys* d_systems, const long long* d_nsteps, int nsys, unsigned int* d_work,
+                                const ResidentPlan& plan, cudaStream_t st) {
+    auto fn = k_resident<C, S, EB>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    if (e != cudaSuccess) return e;
+    fn<<<plan.ctas, plan.threads, plan.smem, st>>>(d_systems, d_nsteps, nsys, d_work);
+    return cudaGetLastError();
+}
+
+template <bool C, int S>
+static cudaError_t launch_res_eb(const DevSys* d_systems, const long long* d_nsteps, int nsys, unsigned int* d_work,
+                                 const ResidentPlan& plan, cudaStream_t st) {
+    switch (plan.e_bits) {
+        case 4: return launch_res_t<C, S, 4>(d_systems, d_nsteps, nsys, d_work, plan, st);
+        case 8: return launch_res_t<C, S, 8>(d_systems, d_nsteps, nsys, d_work, plan, st);
+        case 16: return launch_res_t<C, S, 16>(d_systems, d_nsteps, nsys, d_work, plan, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_resident(const DevSys* d_systems, const long long* d_nsteps, int nsys, unsigned int* d_work,
+                            const ResidentPlan& plan, bool compact, int sel, cudaStream_t st) {
+    if (compact) {
+        if (sel == SNP_SELECT_FIRST) return launch_res_eb<true, SNP_SELECT_FIRST>(d_systems, d_nsteps, nsys, d_work, plan, st);
+        return launch_res_eb<true, SNP_SELECT_PHILOX>(d_systems, d_nsteps, nsys, d_work, plan, st);
+    }
+    if (sel == SNP_SELECT_FIRST) return launch_res_eb<false, SNP_SELECT_FIRST>(d_systems, d_nsteps, nsys, d_work, plan, st);
+    return launch_res_eb<false, SNP_SELECT_PHILOX>(d_systems, d_nsteps, nsys, d_work, plan, st);
+}
+
+}  // namespace snp

@@ -1,0 +1,287 @@
+// Grid-wide step kernels: one launch covers one step of one system.
+//
+// Pull form (SNP_FORM_OPT, SNP_PROP_PULL).  Each warp owns a slice of 32
+// slots; lane l owns slot 32*slice + l.  One launch fuses the end of step k
+// with the start of step k+1 (the paper's STEP of k, UPDATE_DELAYS, then
+// SV_CALC of k+1, Alg. 1 and Sec. 5):
+//   gather : C_{k+1}[j] = C'_k[j] + [j open] * sum_{i in in(j)} E_k[i]
+//   select : per neuron, complete / count down / pick a rule for step k+1,
+//            consume, and write E_{k+1}, S_{k+1} and the status word.
+// E is double-buffered by step parity, so one launch per step needs no
+// grid-wide barrier; the kernel boundary is the barrier between the paper's
+// "choose the spiking vector" and "update the configuration" phases.
+//
+// Push form (SNP_PROP_PUSH) follows Alg. 5's direction: a select launch, then
+// every emitter adds p into each open target with atomics aggregated across
+// the warp (lanes that hit the same target add once).
+//
+// Fixed point: a select pass raises a per-step activity word when any neuron
+// is pending or selected.  A gather launch that finds its step's word clear
+// marks the system halted; later launches of the call return at once.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace snp {
+
+// Returns true if the launch gathering absolute step kg must not run.
+__device__ __forceinline__ bool check_halt(uint32_t* fl, unsigned long long* steps, unsigned long long kg) {
+    if (ld_volatile(fl + kFlagHalted)) return true;
+    if (ld_volatile(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
+        if (threadIdx.x == 0) {
+            steps[kStepHalt] = kg;
+            __threadfence();
+            atomicExch(fl + kFlagHalted, 1u);
+        }
+        return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void raise_activity(uint32_t* fl, unsigned long long ks, bool active) {
+    if (__syncthreads_or(active) && threadIdx.x == 0) {
+        uint32_t* a = fl + kFlagAct0 + (int)(ks % 3ull);
+        if (ld_volatile(a) == 0u) atomicExch(a, 1u);
+    }
+}
+
+template <bool GATHER, bool SELECT, bool COMPACT, int SEL>
+__global__ void __launch_bounds__(256) k_step_pull(DevSys s, int32_t t) {
+    uint32_t* fl = s.flags;
+    const unsigned long long base = s.step[kStepBase];
+    const unsigned long long kg = base + (unsigned long long)t;
+    const unsigned long long ks = GATHER ? kg + 1ull : kg;
+    if (GATHER) {
+        if (check_halt(fl, s.step, kg)) return;
+        if (SELECT && blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
+    }
+    const int lane = threadIdx.x & 31;
+    const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t slot = slice * kSlice + lane;
+    bool active = false;
+    if (slice < s.nslices) {
+        const bool valid = slot < s.q;
+        int32_t c = 0;
+        uint32_t st = 0u;
+        if (valid) {
+            c = s.C[slot];
+            st = s.st[slot];
+        }
+        if (GATHER) {
+            const int32_t* __restrict__ E = s.E[kg & 1ull];
+            const int32_t b = __ldg(s.slice_ptr + slice);
+            const int32_t w = __ldg(s.slice_ptr + slice + 1) - b;
+            const int32_t* __restrict__ p = s.in_idx + (size_t)b * kSlice + lane;
+            long long sum = 0;
+            int32_t col = 0;
+            for (; col + 4 <= w; col += 4) {
+                const int32_t i0 = __ldg(p + (col + 0) * kSlice);
+                const int32_t i1 = __ldg(p + (col + 1) * kSlice);
+                const int32_t i2 = __ldg(p + (col + 2) * kSlice);
+                const int32_t i3 = __ldg(p + (col + 3) * kSlice);
+                sum += (long long)E[i0] + E[i1] + E[i2] + E[i3];
+            }
+            for (; col < w; ++col) sum += E[__ldg(p + col * kSlice)];
+            if (valid && (st >> kPendShift) == 0u) {
+                long long nc = (long long)c + sum;
+                if (nc > 2147483647ll) {
+                    atomicOr(fl + kFlagOverflow, 1u);
+                    nc = 2147483647ll;
+                }
+                c = (int32_t)nc;
+            }
+        }
+        if (SELECT && valid) {
+            const SelOut o = select_neuron<COMPACT, SEL>(
+                s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), c, st, ks,
+                SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
+            c = o.c_after;
+            active = o.active;
+            s.E[ks & 1ull][slot] = o.emit;
+            s.S[ks & 1ull][slot] = o.s;
+            s.st[slot] = o.st;
+        }
+        if (valid) s.C[slot] = c;
+    }
+    if (SELECT) raise_activity(fl, ks, active);
+}
+
+// Push propagation of step kg = base + t: select already ran for kg.
+__global__ void __launch_bounds__(256) k_push_scatter(DevSys s, int32_t t) {
+    uint32_t* fl = s.flags;
+    const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
+    if (check_halt(fl, s.step, kg)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 1ull) % 3ull)] = 0u;
+    const int lane = threadIdx.x & 31;
+    const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (slice >= s.nslices) return;  // warp-uniform
+    const int32_t slot = slice * kSlice + lane;
+    const int32_t emit = slot < s.q ? s.E[kg & 1ull][slot] : 0;
+    const int32_t b = __ldg(s.out_ptr + slice);
+    const int32_t w = __ldg(s.out_ptr + slice + 1) - b;
+    const int32_t* __restrict__ p = s.out_idx + (size_t)b * kSlice + lane;
+    for (int32_t col = 0; col < w; ++col) {
+        int32_t tg = emit > 0 ? __ldg(p + col * kSlice) : -1;
+        if (tg >= 0 && (s.st[tg] >> kPendShift) != 0u) tg = -1;  // closed target: spikes lost
+        const unsigned grp = __match_any_sync(0xffffffffu, tg);
+        const unsigned add = __reduce_add_sync(grp, tg >= 0 ? (unsigned)emit : 0u);
+        if (tg >= 0 && (__ffs(grp) - 1) == lane) {
+            const int old = atomicAdd(s.C + tg, (int)add);
+            if ((long long)old + (long long)add > 2147483647ll) atomicOr(fl + kFlagOverflow, 1u);
+        }
+    }
+}
+
+// Select-only launch for the push form: step kg = base + t.
+template <bool COMPACT, int SEL>
+__global__ void __launch_bounds__(256) k_select_push(DevSys s, int32_t t) {
+    uint32_t* fl = s.flags;
+    const unsigned long long ks = s.step[kStepBase] + (unsigned long long)t;
+    if (ld_volatile(fl + kFlagHalted)) return;
+    const int lane = threadIdx.x & 31;
+    const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t slot = slice * kSlice + lane;
+    bool active = false;
+    if (slice < s.nslices && slot < s.q) {
+        const SelOut o = select_neuron<COMPACT, SEL>(
+            s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), s.C[slot], s.st[slot], ks,
+            SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
+        active = o.active;
+        s.C[slot] = o.c_after;
+        s.E[ks & 1ull][slot] = o.emit;
+        s.S[ks & 1ull][slot] = o.s;
+        s.st[slot] = o.st;
+    }
+    raise_activity(fl, ks, active);
+}
+
+// Call bookkeeping: remember where the call started and clear its flags.
+__global__ void k_begin(DevSys s) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        uint32_t* fl = s.flags;
+        fl[kFlagAct0 + 0] = 0u;
+        fl[kFlagAct0 + 1] = 0u;
+        fl[kFlagAct0 + 2] = 0u;
+        fl[kFlagHalted] = 0u;
+        s.step[kStepHalt] = 0ull;
+        s.step[kStepCallStart] = s.step[kStepBase];
+    }
+}
+
+// Advances the base step after `count` launched steps unless the call halted.
+__global__ void k_advance(DevSys s, int32_t count) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && !ld_volatile(s.flags + kFlagHalted))
+        s.step[kStepBase] += (unsigned long long)count;
+}
+
+// Ends a call: settles the base step at the halt point if the call halted
+// and records the executed step count of the call.
+__global__ void k_finish(DevSys s, int32_t tail) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        uint32_t* fl = s.flags;
+        if (ld_volatile(fl + kFlagHalted))
+            s.step[kStepBase] = s.step[kStepHalt];
+        else
+            s.step[kStepBase] += (unsigned long long)tail;
+        s.step[kStepExec] = s.step[kStepBase] - s.step[kStepCallStart];
+    }
+}
+
+// ---- host launchers -------------------------------------------------------
+
+static inline dim3 grid_for(const DevSys& s, int threads) {
+    const long long warps = s.nslices;
+    const long long wpb = threads / 32;
+    return dim3((unsigned)((warps + wpb - 1) / wpb));
+}
+
+template <bool G, bool S>
+static cudaError_t launch_pull_t(const DevSys& s, int32_t t, cudaStream_t st, bool compact, int sel) {
+    const dim3 grid = grid_for(s, 256);
+    if (compact) {
+        if (sel == SNP_SELECT_FIRST)
+            k_step_pull<G, S, true, SNP_SELECT_FIRST><<<grid, 256, 0, st>>>(s, t);
+        else
+            k_step_pull<G, S, true, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, t);
+    } else {
+        if (sel == SNP_SELECT_FIRST)
+            k_step_pull<G, S, false, SNP_SELECT_FIRST><<<grid, 256, 0, st>>>(s, t);
+        else
+            k_step_pull<G, S, false, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, t);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pull(const DevSys& s, int kind, int32_t t, cudaStream_t st, bool compact, int sel) {
+    switch (kind) {
+        case kPullSelectOnly: return launch_pull_t<false, true>(s, t, st, compact, sel);
+        case kPullFused: return launch_pull_t<true, true>(s, t, st, compact, sel);
+        case kPullGatherOnly: return launch_pull_t<true, false>(s, t, st, compact, sel);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_push_step(const DevSys& s, int32_t t, cudaStream_t st, bool compact, int sel) {
+    const dim3 grid = grid_for(s, 256);
+    if (compact) {
+        if (sel == SNP_SELECT_FIRST)
+            k_select_push<true, SNP_SELECT_FIRST><<<grid, 256, 0, st>>>(s, t);
+        else
+            k_select_push<true, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, t);
+    } else {
+        if (sel == SNP_SELECT_FIRST)
+            k_select_push<false, SNP_SELECT_FIRST><<<grid, 256, 0, st>>>(s, t);
+        else
+            k_select_push<false, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, t);
+    }
+    k_push_scatter<<<grid, 256, 0, st>>>(s, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_begin(const DevSys& s, cudaStream_t st) {
+    k_begin<<<1, 32, 0, st>>>(s);
+    return cudaGetLastError();
+}
+cudaError_t launch_advance(const DevSys& s, int32_t count, cudaStream_t st) {
+    k_advance<<<1, 32, 0, st>>>(s, count);
+    return cudaGetLastError();
+}
+cudaError_t launch_finish(const DevSys& s, int32_t tail, cudaStream_t st) {
+    k_finish<<<1, 32, 0, st>>>(s, tail);
+    return cudaGetLastError();
+}
+
+// ---- state export / import ------------------------------------------------
+
+__global__ void k_export(const DevSys s, const int32_t* __restrict__ rule_base, int what, int32_t* out,
+                         int parity) {
+    const int32_t slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= s.q) return;
+    const int32_t nid = s.orig[slot];
+    int32_t v = 0;
+    const uint32_t st = s.st[slot];
+    switch (what) {
+        case kExportConfig: v = s.C[slot]; break;
+        case kExportStatus: v = (st >> kPendShift) ? (int32_t)(st & kDMask) : 0; break;
+        case kExportPending: v = (st >> kPendShift) ? rule_base[slot] + (int32_t)(st >> kPendShift) - 1 : -1; break;
+        case kExportSpiking: {
+            // S of the last executed step k-1 (parity < 0: read k on the device)
+            const unsigned long long k = s.step[kStepBase];
+            const int par = parity >= 0 ? parity : (int)((k + 1ull) & 1ull);
+            const int32_t x = (parity < 0 && k == 0ull) ? -1 : s.S[par][slot];
+            v = x >= 0 ? rule_base[slot] + x : -1;
+            break;
+        }
+    }
+    out[nid] = v;
+}
+
+cudaError_t launch_export(const DevSys& s, const int32_t* rule_base, int what, int32_t* out, int parity,
+                          cudaStream_t st) {
+    if (s.q == 0) return cudaSuccess;
+    k_export<<<(s.q + 255) / 256, 256, 0, st>>>(s, rule_base, what, out, parity);
+    return cudaGetLastError();
+}
+
+}  // namespace snp

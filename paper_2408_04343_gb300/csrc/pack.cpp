@@ -1,0 +1,294 @@
+// Validation of a system description and packing into the device layouts.
+//
+// The paper builds a dense transition matrix first and compresses it
+// afterwards (Sec. 5, "Initialization"), which it names as the reason ELL
+// could not reach the largest subset-sum instances (Sec. 6).  Here every
+// layout is built straight from the edge list in O(|syn| + m) memory.
+//
+// Layouts (all in slot order, see below):
+//  * rule table: N_Pi offsets (Sec. 2) and one compact word per rule when
+//    every field fits (k, j, c < 256, p, d < 16), else four words per rule;
+//  * in-lists (pull): sliced ELL.  Slots are grouped by 32 (one warp); a slice
+//    stores its in-neighbour columns column-major, padded to the widest list
+//    in the slice with the dummy slot q (whose emission is always 0).  This is
+//    the transpose of the paper's synapse matrix Sy_Pi (Sec. 3) cut into
+//    warp-sized slices;
+//  * out-lists (push): the paper's Sy_Pi in the same sliced layout, padded
+//    with -1 (the null entry that ends a column in Alg. 5).
+//
+// Slot order: inside windows of `window` neurons, neurons are stably sorted
+// by decreasing in-degree so that the 32 lists of a slice have similar
+// lengths and padding stays small.  The caller never sees slot numbers.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <numeric>
+
+#include "snp_internal.h"
+
+namespace snp {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int status, const std::string& msg) {
+    g_err = msg;
+    return status;
+}
+const char* last_error() { return g_err.c_str(); }
+
+int validate_desc(const snp_desc* d) {
+    if (!d) return fail(SNP_ERR_INVALID, "desc is NULL");
+    if (d->q < 1) return fail(SNP_ERR_INVALID, "q must be >= 1");
+    if (d->q > INT32_MAX - 64) return fail(SNP_ERR_INVALID, "q too large");
+    if (!d->init_spikes || !d->rule_offsets || !d->syn_offsets)
+        return fail(SNP_ERR_INVALID, "init_spikes, rule_offsets and syn_offsets are required");
+    const int32_t q = d->q;
+    if (d->rule_offsets[0] != 0) return fail(SNP_ERR_INVALID, "rule_offsets[0] != 0");
+    for (int32_t i = 0; i < q; ++i) {
+        int64_t a = d->rule_offsets[i], b = d->rule_offsets[i + 1];
+        if (b < a) return fail(SNP_ERR_INVALID, "rule_offsets not monotone at neuron " + std::to_string(i));
+        if (b - a > kMaxRulesPerNeuron)
+            return fail(SNP_ERR_INVALID, "more than 32766 rules in neuron " + std::to_string(i));
+        if (d->init_spikes[i] < 0) return fail(SNP_ERR_INVALID, "negative initial spikes at neuron " + std::to_string(i));
+    }
+    const int64_t m = d->rule_offsets[q];
+    if (m > INT32_MAX - 1) return fail(SNP_ERR_INVALID, "too many rules");
+    if (m > 0 && (!d->rule_k || !d->rule_j || !d->rule_c || !d->rule_p || !d->rule_d))
+        return fail(SNP_ERR_INVALID, "rule arrays are required when m > 0");
+    for (int64_t r = 0; r < m; ++r) {
+        if (d->rule_k[r] < 0 || d->rule_j[r] < 0 || d->rule_c[r] < 0)
+            return fail(SNP_ERR_INVALID, "negative k, j or c in rule " + std::to_string(r));
+        if (d->rule_p[r] < 0 || d->rule_p[r] > kMaxP)
+            return fail(SNP_ERR_INVALID, "p out of [0, 65535] in rule " + std::to_string(r));
+        if (d->rule_d[r] < 0 || d->rule_d[r] > kMaxDelay)
+            return fail(SNP_ERR_INVALID, "d out of [0, 65535] in rule " + std::to_string(r));
+        if (d->rule_p[r] == 0 && d->rule_d[r] != 0)
+            return fail(SNP_ERR_INVALID, "forgetting rule with a delay: rule " + std::to_string(r));
+    }
+    if (d->syn_offsets[0] != 0) return fail(SNP_ERR_INVALID, "syn_offsets[0] != 0");
+    if (d->syn_offsets[q] != d->num_syn) return fail(SNP_ERR_INVALID, "syn_offsets[q] != num_syn");
+    if (d->num_syn > 0 && !d->syn_targets) return fail(SNP_ERR_INVALID, "syn_targets is NULL");
+    std::vector<int32_t> row;
+    for (int32_t i = 0; i < q; ++i) {
+        int64_t a = d->syn_offsets[i], b = d->syn_offsets[i + 1];
+        if (b < a) return fail(SNP_ERR_INVALID, "syn_offsets not monotone at neuron " + std::to_string(i));
+        row.assign(d->syn_targets + a, d->syn_targets + b);
+        for (int32_t t : row) {
+            if (t < 0 || t >= q) return fail(SNP_ERR_INVALID, "synapse target out of range from neuron " + std::to_string(i));
+            if (t == i) return fail(SNP_ERR_INVALID, "self-loop at neuron " + std::to_string(i));
+        }
+        std::sort(row.begin(), row.end());
+        if (std::adjacent_find(row.begin(), row.end()) != row.end())
+            return fail(SNP_ERR_INVALID, "duplicate synapse from neuron " + std::to_string(i));
+    }
+    if (d->out_neuron < -1 || d->out_neuron >= q) return fail(SNP_ERR_INVALID, "out_neuron out of range");
+    return SNP_OK;
+}
+
+int pack_system(const snp_desc* d, bool want_out_lists, int window, HostPack* hp) {
+    const int32_t q = d->q;
+    const int64_t m = d->rule_offsets[q];
+    const int64_t nsyn = d->num_syn;
+    hp->q = q;
+    hp->m = m;
+    hp->nsyn = nsyn;
+    if (window < kSlice) window = kSlice;
+
+    // in-degrees
+    std::vector<int32_t> indeg(q, 0);
+    for (int64_t e = 0; e < nsyn; ++e) indeg[d->syn_targets[e]]++;
+    hp->max_in = q ? *std::max_element(indeg.begin(), indeg.end()) : 0;
+    hp->max_out = 0;
+    for (int32_t i = 0; i < q; ++i)
+        hp->max_out = std::max<int32_t>(hp->max_out, (int32_t)(d->syn_offsets[i + 1] - d->syn_offsets[i]));
+
+    // slot order: stable sort by decreasing in-degree inside windows
+    hp->perm.resize(q);
+    std::iota(hp->perm.begin(), hp->perm.end(), 0);
+    for (int64_t w0 = 0; w0 < q; w0 += window) {
+        int64_t w1 = std::min<int64_t>(q, w0 + window);
+        std::stable_sort(hp->perm.begin() + w0, hp->perm.begin() + w1,
+                         [&](int32_t a, int32_t b) { return indeg[a] > indeg[b]; });
+    }
+    hp->inv.assign(q, 0);
+    for (int32_t s = 0; s < q; ++s) hp->inv[hp->perm[s]] = s;
+
+    // rule table in slot order
+    hp->rule_off.assign((size_t)q + 1, 0);
+    hp->rule_base.assign(q, 0);
+    int32_t max_rules = 0, max_p = 0, max_d = 0;
+    bool compact = true;
+    for (int32_t s = 0; s < q; ++s) {
+        int32_t i = hp->perm[s];
+        int32_t R = (int32_t)(d->rule_offsets[i + 1] - d->rule_offsets[i]);
+        hp->rule_off[s + 1] = hp->rule_off[s] + R;
+        hp->rule_base[s] = (int32_t)d->rule_offsets[i];
+        max_rules = std::max(max_rules, R);
+    }
+    for (int64_t r = 0; r < m; ++r) {
+        max_p = std::max(max_p, d->rule_p[r]);
+        max_d = std::max(max_d, d->rule_d[r]);
+        if (d->rule_k[r] > 255 || d->rule_j[r] > 255 || d->rule_c[r] > 255 || d->rule_p[r] > 15 ||
+            d->rule_d[r] > 15)
+            compact = false;
+    }
+    hp->max_rules = max_rules;
+    hp->max_p = max_p;
+    hp->max_d = max_d;
+    hp->compact = compact;
+    hp->rules.assign(compact ? (size_t)m : (size_t)m * 4, 0);
+    for (int32_t s = 0; s < q; ++s) {
+        int32_t i = hp->perm[s];
+        int64_t r0 = d->rule_offsets[i];
+        int32_t R = hp->rule_off[s + 1] - hp->rule_off[s];
+        for (int32_t t = 0; t < R; ++t) {
+            int64_t r = r0 + t;
+            int64_t dst = hp->rule_off[s] + t;
+            if (compact) {
+                hp->rules[dst] = pack_rule_compact(d->rule_k[r], d->rule_j[r], d->rule_c[r], d->rule_p[r],
+                                                   d->rule_d[r]);
+            } else {
+                hp->rules[dst * 4 + 0] = (uint32_t)d->rule_k[r];
+                hp->rules[dst * 4 + 1] = (uint32_t)d->rule_j[r];
+                hp->rules[dst * 4 + 2] = (uint32_t)d->rule_c[r];
+                hp->rules[dst * 4 + 3] = (uint32_t)d->rule_p[r] | ((uint32_t)d->rule_d[r] << 16);
+            }
+        }
+    }
+
+    // in-lists: sliced ELL, pad = q
+    const int32_t nslices = (q + kSlice - 1) / kSlice;
+    hp->slice_ptr.assign((size_t)nslices + 1, 0);
+    int64_t acc = 0;
+    for (int32_t sl = 0; sl < nslices; ++sl) {
+        int32_t w = 0;
+        for (int32_t l = 0; l < kSlice; ++l) {
+            int64_t s = (int64_t)sl * kSlice + l;
+            if (s < q) w = std::max(w, indeg[hp->perm[s]]);
+        }
+        hp->slice_ptr[sl] = (int32_t)acc;
+        acc += w;
+        if (acc > INT32_MAX) return fail(SNP_ERR_INVALID, "in-lists too large for 32-bit slice offsets");
+    }
+    hp->slice_ptr[nslices] = (int32_t)acc;
+    hp->in_idx.assign((size_t)acc * kSlice, q);
+    {
+        std::vector<int32_t> fill(q, 0);
+        for (int32_t i = 0; i < q; ++i) {
+            const int32_t si = hp->inv[i];
+            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e) {
+                const int32_t s = hp->inv[d->syn_targets[e]];
+                const int32_t col = fill[s]++;
+                const int64_t sl = s / kSlice, lane = s % kSlice;
+                hp->in_idx[((int64_t)hp->slice_ptr[sl] + col) * kSlice + lane] = si;
+            }
+        }
+    }
+
+    // out-lists (push): sliced ELL by source slot, pad = -1
+    if (want_out_lists) {
+        hp->out_ptr.assign((size_t)nslices + 1, 0);
+        int64_t oacc = 0;
+        for (int32_t sl = 0; sl < nslices; ++sl) {
+            int32_t w = 0;
+            for (int32_t l = 0; l < kSlice; ++l) {
+                int64_t s = (int64_t)sl * kSlice + l;
+                if (s < q) {
+                    int32_t i = hp->perm[s];
+                    w = std::max<int32_t>(w, (int32_t)(d->syn_offsets[i + 1] - d->syn_offsets[i]));
+                }
+            }
+            hp->out_ptr[sl] = (int32_t)oacc;
+            oacc += w;
+            if (oacc > INT32_MAX) return fail(SNP_ERR_INVALID, "out-lists too large for 32-bit slice offsets");
+        }
+        hp->out_ptr[nslices] = (int32_t)oacc;
+        hp->out_idx.assign((size_t)oacc * kSlice, -1);
+        for (int32_t s = 0; s < q; ++s) {
+            int32_t i = hp->perm[s];
+            const int64_t sl = s / kSlice, lane = s % kSlice;
+            int32_t col = 0;
+            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e, ++col)
+                hp->out_idx[((int64_t)hp->out_ptr[sl] + col) * kSlice + lane] = hp->inv[d->syn_targets[e]];
+        }
+    }
+
+    hp->C0.resize(q);
+    for (int32_t s = 0; s < q; ++s) hp->C0[s] = d->init_spikes[hp->perm[s]];
+    return SNP_OK;
+}
+
+}  // namespace snp
+
+// ---- paper formats on the host (inspection / memory accounting) ---------
+
+extern "C" int snp_export_dense(const snp_desc* d, int32_t* M, int64_t capacity) {
+    int st = snp::validate_desc(d);
+    if (st) return st;
+    const int64_t q = d->q, m = d->rule_offsets[q];
+    if (!M || capacity < m * q) return snp::fail(SNP_ERR_INVALID, "dense output too small");
+    std::memset(M, 0, sizeof(int32_t) * (size_t)(m * q));
+    for (int64_t i = 0; i < q; ++i)
+        for (int64_t r = d->rule_offsets[i]; r < d->rule_offsets[i + 1]; ++r) {
+            M[r * q + i] -= d->rule_c[r];
+            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e)
+                M[r * q + d->syn_targets[e]] += d->rule_p[r];
+        }
+    return SNP_OK;
+}
+
+extern "C" int snp_export_ell(const snp_desc* d, int32_t* values, int32_t* neurons, int64_t capacity,
+                              int64_t* rows_out) {
+    int st = snp::validate_desc(d);
+    if (st) return st;
+    const int64_t q = d->q, m = d->rule_offsets[q];
+    int64_t z = 0;
+    for (int64_t i = 0; i < q; ++i) z = std::max<int64_t>(z, d->syn_offsets[i + 1] - d->syn_offsets[i]);
+    const int64_t rows = z + 1;
+    if (rows_out) *rows_out = rows;
+    if (!values && !neurons) return SNP_OK;
+    if (!values || !neurons || capacity < rows * m) return snp::fail(SNP_ERR_INVALID, "ELL output too small");
+    for (int64_t x = 0; x < rows * m; ++x) {
+        values[x] = 0;
+        neurons[x] = -1;
+    }
+    for (int64_t i = 0; i < q; ++i)
+        for (int64_t r = d->rule_offsets[i]; r < d->rule_offsets[i + 1]; ++r) {
+            values[r] = -d->rule_c[r];   // row 0: consumption at the owner
+            neurons[r] = (int32_t)i;
+            if (d->rule_p[r] == 0) continue;  // forgetting rules have no +p entries
+            int64_t row = 1;
+            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e, ++row) {
+                values[row * m + r] = d->rule_p[r];
+                neurons[row * m + r] = d->syn_targets[e];
+            }
+        }
+    return SNP_OK;
+}
+
+extern "C" int snp_export_compressed(const snp_desc* d, int32_t* sy, int64_t capacity, int64_t* rows_out) {
+    int st = snp::validate_desc(d);
+    if (st) return st;
+    const int64_t q = d->q;
+    int64_t z = 0;
+    for (int64_t i = 0; i < q; ++i) z = std::max<int64_t>(z, d->syn_offsets[i + 1] - d->syn_offsets[i]);
+    if (rows_out) *rows_out = z;
+    if (!sy) return SNP_OK;
+    if (capacity < z * q) return snp::fail(SNP_ERR_INVALID, "compressed output too small");
+    for (int64_t x = 0; x < z * q; ++x) sy[x] = -1;
+    for (int64_t i = 0; i < q; ++i) {
+        int64_t row = 0;
+        for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e, ++row) sy[row * q + i] = d->syn_targets[e];
+    }
+    return SNP_OK;
+}
+
+extern "C" int64_t snp_paper_format_elements(int32_t form, int64_t q, int64_t m, int64_t z) {
+    switch (form) {
+        case SNP_FORM_DENSE: return m * q + 3 * m + 2 * q + 1;
+        case SNP_FORM_ELL: return m * (2 * z + 5) + 2 * q + 1;
+        case SNP_FORM_OPT: return q * (z + 3) + 4 * m + 1;
+        default: return -1;
+    }
+}

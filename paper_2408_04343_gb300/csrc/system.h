@@ -1,0 +1,53 @@
+// The snp_system handle (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <utility>
+#include <vector>
+
+#include "kernels.h"
+#include "snp_internal.h"
+
+namespace snp {
+
+constexpr int kChunk = 48;                 // steps per captured CUDA graph
+constexpr int kSortWindow = 8192;          // in-degree sort window (slots)
+constexpr int kAutoResidentMaxQ = 8192;    // AUTO picks the resident engine up to here
+
+}  // namespace snp
+
+struct snp_system {
+    snp_options opt{};
+    snp_allocator alloc{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t chunk_exec = nullptr;
+    snp::DevSys dev{};
+    snp::DevSys* d_self = nullptr;     // device copy of dev (resident engine)
+    long long* d_nsteps = nullptr;
+    unsigned int* d_work = nullptr;
+    int32_t* d_rule_base = nullptr;
+    int32_t* scratch = nullptr;
+    std::vector<std::pair<void*, size_t>> allocs;
+    size_t device_bytes = 0;
+    int32_t q = 0;
+    int64_t m = 0, nsyn = 0;
+    int32_t max_p = 0, max_rules = 0;
+    bool compact = true;
+    int64_t in_entries = 0, out_entries = 0, rule_words = 0;
+    std::vector<int32_t> perm;          // slot -> caller's neuron
+    std::vector<int64_t> rule_offsets;  // caller's N_Pi (for set_state checks)
+    unsigned long long host_step = 0;   // last step counter read back
+    std::atomic<int> busy{0};
+};
+
+namespace snp {
+void* sys_alloc(snp_system* s, size_t bytes);
+bool is_device_ptr(const void* p);
+bool resident_fits(const snp_system* s, ResidentPlan* plan);
+int effective_engine(const snp_system* s);
+int read_flags(snp_system* s, int64_t* exec);
+int run_steps(snp_system* s, int64_t n);
+}  // namespace snp

@@ -1,0 +1,326 @@
+"""Thin ctypes binding of libsnp (include/snp.h), same names as the C-ABI.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  There is no CPU fallback; if ``_build/libsnp.so`` is missing the
+import of a function raises.  Device buffers may be passed as torch CUDA
+tensors (their data_ptr is handed over) or as raw integer pointers.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SNP_OK, SNP_ERR_INVALID, SNP_ERR_OOM, SNP_ERR_CUDA, SNP_ERR_TIMEOUT, SNP_ERR_OVERFLOW, \
+    SNP_ERR_BUSY, SNP_ERR_UNSUPPORTED = range(8)
+SNP_FORM_OPT, SNP_FORM_ELL, SNP_FORM_DENSE = 0, 1, 2
+SNP_PROP_PULL, SNP_PROP_PUSH = 0, 1
+SNP_SELECT_FIRST, SNP_SELECT_PHILOX = 0, 1
+SNP_ENGINE_AUTO, SNP_ENGINE_LAUNCH, SNP_ENGINE_RESIDENT = 0, 1, 2
+
+
+class SnpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p)
+RELEASE_FN = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p)
+
+
+class snp_allocator(ct.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", ct.c_void_p)]
+
+
+class snp_options(ct.Structure):
+    _fields_ = [("form", ct.c_int32), ("prop", ct.c_int32), ("select", ct.c_int32), ("engine", ct.c_int32),
+                ("seed", ct.c_uint64), ("stream", ct.c_void_p), ("alloc", ct.POINTER(snp_allocator)),
+                ("threads", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class snp_desc(ct.Structure):
+    _fields_ = [("q", ct.c_int32), ("init_spikes", ct.c_void_p), ("rule_offsets", ct.c_void_p),
+                ("rule_k", ct.c_void_p), ("rule_j", ct.c_void_p), ("rule_c", ct.c_void_p),
+                ("rule_p", ct.c_void_p), ("rule_d", ct.c_void_p), ("num_syn", ct.c_int64),
+                ("syn_offsets", ct.c_void_p), ("syn_targets", ct.c_void_p), ("out_neuron", ct.c_int32)]
+
+
+class snp_info(ct.Structure):
+    _fields_ = [("q", ct.c_int32), ("form", ct.c_int32), ("prop", ct.c_int32), ("select", ct.c_int32),
+                ("engine", ct.c_int32), ("m", ct.c_int64), ("num_syn", ct.c_int64),
+                ("in_entries", ct.c_int64), ("out_entries", ct.c_int64), ("rule_words", ct.c_int64),
+                ("device_bytes", ct.c_int64), ("max_rules", ct.c_int32), ("max_p", ct.c_int32),
+                ("compact_rules", ct.c_int32), ("e_bits", ct.c_int32), ("step", ct.c_uint64)]
+
+
+_P = ct.c_void_p
+_SIGS = {
+    "snp_create": (ct.c_int, [ct.POINTER(snp_desc), ct.POINTER(snp_options), ct.POINTER(ct.c_void_p)]),
+    "snp_destroy": (ct.c_int, [_P]),
+    "snp_step": (ct.c_int, [_P, ct.c_int64, ct.POINTER(ct.c_int64)]),
+    "snp_get_config": (ct.c_int, [_P, _P, ct.c_int64]),
+    "snp_get_spiking": (ct.c_int, [_P, _P, ct.c_int64]),
+    "snp_get_status": (ct.c_int, [_P, _P, ct.c_int64]),
+    "snp_get_pending": (ct.c_int, [_P, _P, ct.c_int64]),
+    "snp_get_state": (ct.c_int, [_P, _P, _P, _P, ct.c_int64, ct.POINTER(ct.c_uint64)]),
+    "snp_set_state": (ct.c_int, [_P, _P, _P, _P, ct.c_int64, ct.c_uint64]),
+    "snp_get_info": (ct.c_int, [_P, ct.POINTER(snp_info)]),
+    "snp_batch_create": (ct.c_int, [ct.POINTER(snp_options), ct.c_size_t, ct.POINTER(ct.c_void_p)]),
+    "snp_batch_destroy": (ct.c_int, [_P]),
+    "snp_batch_submit": (ct.c_int, [_P, _P, _P, ct.c_int32, ct.POINTER(ct.c_int64)]),
+    "snp_batch_poll": (ct.c_int, [_P, ct.c_int64, ct.POINTER(ct.c_int)]),
+    "snp_batch_wait": (ct.c_int, [_P, ct.c_int64]),
+    "snp_batch_steps_done": (ct.c_int, [_P, ct.c_int64, ct.c_int32, ct.POINTER(ct.c_int64)]),
+    "snp_export_dense": (ct.c_int, [ct.POINTER(snp_desc), _P, ct.c_int64]),
+    "snp_export_ell": (ct.c_int, [ct.POINTER(snp_desc), _P, _P, ct.c_int64, ct.POINTER(ct.c_int64)]),
+    "snp_export_compressed": (ct.c_int, [ct.POINTER(snp_desc), _P, ct.c_int64, ct.POINTER(ct.c_int64)]),
+    "snp_paper_format_elements": (ct.c_int64, [ct.c_int32, ct.c_int64, ct.c_int64, ct.c_int64]),
+    "snp_strerror": (ct.c_char_p, [ct.c_int]),
+    "snp_last_error": (ct.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads libsnp.so.  Raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libsnp is not built ({path} missing); run "
+                                   "paper_2408_04343_gb300.build.build() first")
+            lib = ct.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(rc: int):
+    if rc != SNP_OK:
+        lib = load()
+        raise SnpError(rc, lib.snp_last_error().decode(errors="replace") or lib.snp_strerror(rc).decode())
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class _DescHolder:
+    """Builds an snp_desc over numpy arrays and keeps them alive."""
+
+    def __init__(self, desc):
+        a = desc.arrays()
+        self.a = a
+        self.d = snp_desc(desc.q, _ptr(a["init_spikes"]), _ptr(a["rule_offsets"]), _ptr(a["rule_k"]),
+                          _ptr(a["rule_j"]), _ptr(a["rule_c"]), _ptr(a["rule_p"]), _ptr(a["rule_d"]),
+                          int(a["syn_offsets"][-1]), _ptr(a["syn_offsets"]), _ptr(a["syn_targets"]),
+                          int(getattr(desc, "out_neuron", 0)))
+
+
+def make_options(form=SNP_FORM_OPT, prop=SNP_PROP_PULL, select=SNP_SELECT_FIRST, engine=SNP_ENGINE_AUTO,
+                 seed=0, stream=None, threads=0, allocator=None) -> snp_options:
+    o = snp_options(form, prop, select, engine, seed & (2**64 - 1), _stream_handle(stream), None, threads, 0)
+    if allocator is not None:
+        o.alloc = ct.pointer(allocator)
+    return o
+
+
+class System:
+    """One SNP system on the GPU (snp_create .. snp_destroy)."""
+
+    def __init__(self, desc, *, form=SNP_FORM_OPT, prop=SNP_PROP_PULL, select=SNP_SELECT_FIRST,
+                 engine=SNP_ENGINE_AUTO, seed=None, stream=None, threads=0, allocator=None):
+        lib = load()
+        self._lib = lib
+        self.q = int(desc.q)
+        self.m = int(desc.rule_offsets[-1])
+        self.num_syn = int(desc.syn_offsets[-1])
+        h = _DescHolder(desc)
+        seed = getattr(desc, "seed", 0) if seed is None else seed
+        self._alloc = allocator
+        opts = make_options(form, prop, select, engine, int(seed), stream, threads, allocator)
+        out = ct.c_void_p()
+        check(lib.snp_create(ct.byref(h.d), ct.byref(opts), ct.byref(out)))
+        self.handle = out.value
+
+    # -- life cycle
+    def close(self):
+        if getattr(self, "handle", None):
+            check(self._lib.snp_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- stepping
+    def step(self, n: int, wait: bool = True):
+        """snp_step: returns executed steps when wait, else None (queued)."""
+        if wait:
+            done = ct.c_int64(0)
+            check(self._lib.snp_step(self.handle, int(n), ct.byref(done)))
+            return int(done.value)
+        check(self._lib.snp_step(self.handle, int(n), None))
+        return None
+
+    # -- state
+    def _get(self, fn, out=None):
+        if out is None:
+            out = np.empty(self.q, np.int32)
+        n = out.numel() if hasattr(out, "numel") else out.size
+        check(fn(self.handle, _ptr(out), int(n)))
+        return out
+
+    def config(self, out=None):
+        return self._get(self._lib.snp_get_config, out)
+
+    def spiking(self, out=None):
+        return self._get(self._lib.snp_get_spiking, out)
+
+    def status(self, out=None):
+        return self._get(self._lib.snp_get_status, out)
+
+    def pending(self, out=None):
+        return self._get(self._lib.snp_get_pending, out)
+
+    def get_state(self):
+        C = np.empty(self.q, np.int32)
+        D = np.empty(self.q, np.int32)
+        P = np.empty(self.q, np.int32)
+        k = ct.c_uint64(0)
+        check(self._lib.snp_get_state(self.handle, _ptr(C), _ptr(D), _ptr(P), self.q, ct.byref(k)))
+        return C, D, P, int(k.value)
+
+    def set_state(self, C, D, P, step: int):
+        n = C.numel() if hasattr(C, "numel") else np.asarray(C).size
+        if isinstance(C, np.ndarray):
+            C, D, P = (np.ascontiguousarray(x, np.int32) for x in (C, D, P))
+        check(self._lib.snp_set_state(self.handle, _ptr(C), _ptr(D), _ptr(P), int(n), int(step)))
+
+    def info(self) -> snp_info:
+        inf = snp_info()
+        check(self._lib.snp_get_info(self.handle, ct.byref(inf)))
+        return inf
+
+
+class Batch:
+    """snp_batch_*: many systems advanced by persistent launches."""
+
+    def __init__(self, *, mem_budget: int = 0, stream=None, threads=0):
+        lib = load()
+        self._lib = lib
+        opts = make_options(stream=stream, threads=threads)
+        out = ct.c_void_p()
+        check(lib.snp_batch_create(ct.byref(opts), int(mem_budget), ct.byref(out)))
+        self.handle = out.value
+        self._keep = {}
+
+    def submit(self, systems, steps) -> int:
+        handles = (ct.c_void_p * len(systems))(*[s.handle for s in systems])
+        st = np.ascontiguousarray(np.broadcast_to(np.asarray(steps, np.int64), (len(systems),)))
+        t = ct.c_int64(0)
+        check(self._lib.snp_batch_submit(self.handle, ct.cast(handles, ct.c_void_p), _ptr(st), len(systems),
+                                         ct.byref(t)))
+        self._keep[t.value] = (handles, st, len(systems))
+        return int(t.value)
+
+    def poll(self, ticket: int) -> bool:
+        d = ct.c_int(0)
+        check(self._lib.snp_batch_poll(self.handle, int(ticket), ct.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int):
+        check(self._lib.snp_batch_wait(self.handle, int(ticket)))
+        n = self._keep[ticket][2]
+        out = []
+        for i in range(n):
+            v = ct.c_int64(0)
+            check(self._lib.snp_batch_steps_done(self.handle, int(ticket), i, ct.byref(v)))
+            out.append(int(v.value))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            check(self._lib.snp_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- paper formats (host only) --------------------------------------------
+
+def export_dense(desc) -> np.ndarray:
+    h = _DescHolder(desc)
+    m, q = int(desc.rule_offsets[-1]), int(desc.q)
+    M = np.zeros((m, q), np.int32)
+    check(load().snp_export_dense(ct.byref(h.d), _ptr(M), M.size))
+    return M
+
+
+def export_ell(desc):
+    h = _DescHolder(desc)
+    rows = ct.c_int64(0)
+    lib = load()
+    check(lib.snp_export_ell(ct.byref(h.d), None, None, 0, ct.byref(rows)))
+    m = int(desc.rule_offsets[-1])
+    vals = np.zeros((rows.value, m), np.int32)
+    nrn = np.zeros((rows.value, m), np.int32)
+    check(lib.snp_export_ell(ct.byref(h.d), _ptr(vals), _ptr(nrn), vals.size, ct.byref(rows)))
+    return vals, nrn
+
+
+def export_compressed(desc) -> np.ndarray:
+    h = _DescHolder(desc)
+    rows = ct.c_int64(0)
+    lib = load()
+    check(lib.snp_export_compressed(ct.byref(h.d), None, 0, ct.byref(rows)))
+    sy = np.zeros((rows.value, int(desc.q)), np.int32)
+    check(lib.snp_export_compressed(ct.byref(h.d), _ptr(sy), sy.size, ct.byref(rows)))
+    return sy
+
+
+def paper_format_elements(form: int, q: int, m: int, z: int) -> int:
+    return int(load().snp_paper_format_elements(form, q, m, z))

@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Bit-exact on every compared step: configuration C, spiking vector S (global
+rule ids), delay status D and pending rules P, and the executed step count.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_04343_gb300 import libsnp, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ENGINES = {"launch": libsnp.SNP_ENGINE_LAUNCH, "resident": libsnp.SNP_ENGINE_RESIDENT}
+SEL = {oracle.FIRST: libsnp.SNP_SELECT_FIRST, oracle.PHILOX: libsnp.SNP_SELECT_PHILOX}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_04343_gb300 import build
+    build.build()
+    libsnp.load()
+
+
+def compare(desc, nsteps, mode, seed, *, engine="launch", prop=libsnp.SNP_PROP_PULL, chunks=(1,),
+            check_every=True):
+    """Steps the GPU system in chunks and compares with the oracle after each."""
+    gs = libsnp.System(desc, select=SEL[mode], engine=ENGINES[engine], prop=prop, seed=seed)
+    st = oracle.initial_state(desc)
+    k = 0
+    last_S = np.full(desc.q, -1, np.int32)
+    ci = 0
+    while k < nsteps:
+        n = min(chunks[ci % len(chunks)], nsteps - k)
+        ci += 1
+        done = gs.step(n)
+        ex, S = oracle.run(desc, st, n, mode, seed, step0=k)
+        assert done == ex, (k, done, ex)
+        if ex:
+            last_S = S
+        if check_every or k + n >= nsteps or ex < n:
+            C, D, P, kk = gs.get_state()
+            assert kk == k + ex
+            assert (C == st[0]).all(), f"C differs after step {k + ex}"
+            assert (D == st[1]).all(), f"D differs after step {k + ex}"
+            assert (P == st[2]).all(), f"P differs after step {k + ex}"
+            assert (gs.spiking() == last_S).all(), f"S differs after step {k + ex}"
+        k += ex
+        if ex < n:
+            break
+    gs.close()
+    return k
+
+
+@pytest.mark.parametrize("engine", ["launch", "resident"])
+@pytest.mark.parametrize("q", [1, 2, 31, 32, 33, 100, 1000, 4099])
+def test_ragged_sizes_every_step(engine, q):
+    d = synth.random_system(q, 50 + q, outdeg=(1, 8), rules=(2, 4), d_range=(0, 3), spikes=(0, 10))
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        compare(d, 40, mode, 977 + q, engine=engine)
+
+
+@pytest.mark.parametrize("engine", ["launch", "resident"])
+def test_small_1k_workload_every_step(engine):
+    d, nsteps, mode = synth.small_1k()
+    compare(d, nsteps, mode, d.seed, engine=engine)
+
+
+def test_small_1k_push_every_step():
+    d, nsteps, mode = synth.small_1k()
+    compare(d, nsteps, mode, d.seed, prop=libsnp.SNP_PROP_PUSH)
+    compare(d, 60, oracle.PHILOX, 5, prop=libsnp.SNP_PROP_PUSH)
+
+
+@pytest.mark.parametrize("engine", ["launch", "resident"])
+def test_chunked_calls_and_graphs(engine):
+    """Calls of many sizes (crossing the captured-graph chunk length)."""
+    d = synth.random_system(3000, 99, outdeg=(4, 16), rules=(3, 4), d_range=(0, 5), spikes=(0, 20))
+    compare(d, 400, oracle.PHILOX, 4242, engine=engine, chunks=(1, 7, 48, 49, 100, 3), check_every=True)
+
+
+def test_push_matches_with_delays_and_skew():
+    d = synth.random_system(20000, 5, zipf=(2.1, 1, 4096), rules=(3, 3), d_range=(0, 3), spikes=(0, 20))
+    compare(d, 60, oracle.PHILOX, 31, prop=libsnp.SNP_PROP_PUSH, chunks=(1, 10, 49))
+    compare(d, 60, oracle.PHILOX, 31, chunks=(1, 10, 49))
+
+
+def test_sort_system_sorts():
+    for v in ([3, 2, 1], [5, 1, 4, 4, 2], list(range(40, 0, -1))):
+        d = synth.sort_system(v)
+        for eng in ("launch", "resident"):
+            n = compare(d, 1000, oracle.FIRST, 0, engine=eng, chunks=(1, 50))
+            assert n == max(v) + 1
+        gs = libsnp.System(d)
+        gs.step(1000)
+        assert gs.config()[2 * len(v):].tolist() == sorted(v)
+
+
+def test_hand_delay_traces():
+    from tests.test_oracle import make_desc
+    cases = [
+        make_desc(2, [[(1, 0, 1, 1, 3)], []], [(0, 1)], [1, 0]),
+        make_desc(3, [[(1, 0, 1, 1, 2)], [], [(1, 0, 1, 1, 0)]], [(2, 0), (0, 1)], [1, 0, 1]),
+        make_desc(4, [[(1, 0, 1, 1, 1)], [], [(2, 0, 2, 1, 0)], [(1, 0, 1, 1, 0)]],
+                  [(0, 1), (2, 0), (3, 2)], [1, 0, 1, 1]),
+    ]
+    for d in cases:
+        for eng in ("launch", "resident"):
+            compare(d, 20, oracle.FIRST, 0, engine=eng)
+        compare(d, 20, oracle.FIRST, 0, prop=libsnp.SNP_PROP_PUSH)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    d = synth.random_system(5000, 3, outdeg=(4, 16), rules=(3, 4), d_range=(0, 5), spikes=(0, 20))
+    a = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=77)
+    a.step(60)
+    ref = a.get_state()
+    b = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=77)
+    b.step(30)
+    C, D, P, k = b.get_state()
+    c = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=77, engine=libsnp.SNP_ENGINE_RESIDENT)
+    c.set_state(C, D, P, k)
+    c.step(30)
+    got = c.get_state()
+    for x, y in zip(ref[:3], got[:3]):
+        assert (x == y).all()
+    assert ref[3] == got[3] == 60
+
+
+def test_device_outputs_and_stream():
+    d = synth.random_system(3000, 8, outdeg=(4, 16), rules=(3, 4), d_range=(0, 5), spikes=(0, 20))
+    s = torch.cuda.Stream()
+    g = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=3, stream=s)
+    g.step(25, wait=False)
+    out = torch.empty(d.q, dtype=torch.int32, device="cuda")
+    g.config(out)
+    s.synchronize()
+    st = oracle.initial_state(d)
+    oracle.run(d, st, 25, oracle.PHILOX, 3)
+    assert (out.cpu().numpy() == st[0]).all()
+
+
+def test_overflow_is_reported():
+    from tests.test_oracle import make_desc
+    d = make_desc(2, [[(1, 1, 1, 1000, 0)], []], [(0, 1)], [10, 2**31 - 600])
+    for eng in (libsnp.SNP_ENGINE_LAUNCH, libsnp.SNP_ENGINE_RESIDENT):
+        g = libsnp.System(d, engine=eng)
+        with pytest.raises(libsnp.SnpError) as ei:
+            g.step(5)
+        assert ei.value.status == libsnp.SNP_ERR_OVERFLOW
+
+
+def test_halted_system_reports_zero_steps():
+    from tests.test_oracle import make_desc
+    d = make_desc(3, [[], [(2, 0, 2, 1, 0)], []], [(1, 0)], [5, 1, 0])
+    for eng in ("launch", "resident"):
+        g = libsnp.System(d, engine=ENGINES[eng])
+        assert g.step(10) == 0
+        assert g.config().tolist() == [5, 1, 0]
+        assert (g.spiking() == -1).all()
+
+
+def test_batch_matches_alone_and_oracle():
+    rng = np.random.default_rng(11)
+    sizes = synth.batch_sizes(rng, 48, 64, 6000)
+    descs = [synth.random_system(int(q), 1000 + i, outdeg=(4, 16), rules=(3, 3), d_range=(0, 4),
+                                 spikes=(0, 10)) for i, q in enumerate(sizes)]
+    steps = [int(x) for x in rng.integers(1, 120, size=len(descs))]
+    systems = [libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=d.seed) for d in descs]
+    b = libsnp.Batch()
+    t = b.submit(systems, steps)
+    done = b.wait(t)
+    for d, g, n, dn in zip(descs, systems, steps, done):
+        st = oracle.initial_state(d)
+        ex, S = oracle.run(d, st, n, oracle.PHILOX, d.seed)
+        assert dn == ex
+        C, D, P, k = g.get_state()
+        assert (C == st[0]).all() and (D == st[1]).all() and (P == st[2]).all() and k == ex
+        if ex:
+            assert (g.spiking() == S).all()
+        alone = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=d.seed, engine=libsnp.SNP_ENGINE_LAUNCH)
+        alone.step(n)
+        assert (alone.config() == C).all()
+    b.close()
+
+
+def test_busy_system_is_refused_during_batch():
+    d = synth.random_system(60000, 1, outdeg=(8, 24), rules=(4, 4), d_range=(0, 5), spikes=(0, 20))
+    g = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=1)
+    b = libsnp.Batch()
+    t = b.submit([g], [300])
+    if not b.poll(t):
+        with pytest.raises(libsnp.SnpError) as ei:
+            g.step(1)
+        assert ei.value.status == libsnp.SNP_ERR_BUSY
+    b.wait(t)
+    g.step(1)
+    b.close()
+
+
+def test_large_1m_full_size_sampled():
+    """The 1,048,576-neuron workload in the launch configuration the bench
+    times (grid-wide engine, Philox selection): every state is compared
+    after steps 1, 2, 3, 10, 58 and 150."""
+    d, _, mode = synth.large_1m()
+    compare(d, 150, mode, d.seed, engine="launch", chunks=(1, 1, 1, 7, 48, 92))
