@@ -72,5 +72,17 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     return LIB
 
 
+
+def sources_hash() -> str:
+    """Digest of every kernel and host source of libsnp (ties profiles to code)."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
