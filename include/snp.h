@@ -234,6 +234,61 @@ int snp_export_compressed(const snp_desc* desc, int32_t* sy, int64_t capacity, i
  *   SNP_FORM_OPT: q (z + 3) + 4m + 1, z = max out-degree.                 */
 int64_t snp_paper_format_elements(int32_t form, int64_t q, int64_t m, int64_t z);
 
+/* ---- stepping without allocation ----------------------------------------- */
+/* The paper has no counterpart to this call; it exists for callers of this
+ * library that cannot call cudaMalloc: code living inside a host framework
+ * that owns all device memory and hands it out only through its own pool
+ * (plugins, custom operators), and latency-critical loops in which an
+ * allocation could synchronize the device at an unpredictable moment.
+ *
+ * snp_step_noalloc runs up to n pull steps (same semantics, selection and
+ * results as snp_step) on a system whose tables and state the caller keeps
+ * in its own DEVICE arrays, in the caller's neuron and rule numbering:
+ *   rule_offsets[q+1], rule_k/j/c/p/d[m]  as in snp_desc, but int32 and on
+ *                                         the device;
+ *   in_offsets[q+1], in_sources[num_in]  the in-neighbours of neuron j are
+ *                                         in_sources[in_offsets[j] ..
+ *                                         in_offsets[j+1]-1] (the transpose
+ *                                         of the synapse lists);
+ *   C, D, P [q]   the state (spikes, steps until reopening, pending rule
+ *                 or -1) at absolute step `step`; read and overwritten with
+ *                 the state after the executed steps;
+ *   S [q]         receives the spiking vector (global rule ids, -1 none) of
+ *                 the last executed step; untouched if no step executes.
+ * The library allocates nothing: its working memory (two emission vectors
+ * and a few flag words, about 2 MB) is one static device array that every
+ * GPU which loads the library holds until the process exits, which caps q
+ * at SNP_NOALLOC_MAX_Q; larger q returns SNP_ERR_INVALID.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress,
+ * with the device current); make that first call before any stream capture.
+ * All calls share the one array and the next call overwrites it (the flag
+ * words are cleared at the start of every call), so calls whose work
+ * overlaps on the GPU, from any thread or stream, race and must be
+ * serialised by the caller.  Work is ordered on `stream`; with steps_done
+ * non-NULL the call waits for it and reports the executed step count,
+ * SNP_ERR_OVERFLOW, or SNP_ERR_INVALID if the kernels found an index in the
+ * device arrays out of range.                                              */
+#define SNP_NOALLOC_MAX_Q 262144
+typedef struct snp_device_system {
+    int32_t q;
+    int64_t m;
+    int64_t num_in;
+    const int32_t* rule_offsets;
+    const int32_t* rule_k;
+    const int32_t* rule_j;
+    const int32_t* rule_c;
+    const int32_t* rule_p;
+    const int32_t* rule_d;
+    const int32_t* in_offsets;
+    const int32_t* in_sources;
+    int32_t* C;
+    int32_t* D;
+    int32_t* P;
+    int32_t* S;
+} snp_device_system;
+int snp_step_noalloc(const snp_device_system* sys, int32_t select, uint64_t seed, uint64_t step, int64_t n,
+                     void* stream, int64_t* steps_done);
+
 const char* snp_strerror(int status);
 const char* snp_last_error(void);
 

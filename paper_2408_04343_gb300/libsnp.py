@@ -58,6 +58,16 @@ class snp_info(ct.Structure):
                 ("compact_rules", ct.c_int32), ("e_bits", ct.c_int32), ("step", ct.c_uint64)]
 
 
+class snp_device_system(ct.Structure):
+    _fields_ = [("q", ct.c_int32), ("m", ct.c_int64), ("num_in", ct.c_int64),
+                ("rule_offsets", ct.c_void_p), ("rule_k", ct.c_void_p), ("rule_j", ct.c_void_p),
+                ("rule_c", ct.c_void_p), ("rule_p", ct.c_void_p), ("rule_d", ct.c_void_p),
+                ("in_offsets", ct.c_void_p), ("in_sources", ct.c_void_p),
+                ("C", ct.c_void_p), ("D", ct.c_void_p), ("P", ct.c_void_p), ("S", ct.c_void_p)]
+
+
+SNP_NOALLOC_MAX_Q = 262144
+
 _P = ct.c_void_p
 _SIGS = {
     "snp_create": (ct.c_int, [ct.POINTER(snp_desc), ct.POINTER(snp_options), ct.POINTER(ct.c_void_p)]),
@@ -80,6 +90,8 @@ _SIGS = {
     "snp_export_ell": (ct.c_int, [ct.POINTER(snp_desc), _P, _P, ct.c_int64, ct.POINTER(ct.c_int64)]),
     "snp_export_compressed": (ct.c_int, [ct.POINTER(snp_desc), _P, ct.c_int64, ct.POINTER(ct.c_int64)]),
     "snp_paper_format_elements": (ct.c_int64, [ct.c_int32, ct.c_int64, ct.c_int64, ct.c_int64]),
+    "snp_step_noalloc": (ct.c_int, [ct.POINTER(snp_device_system), ct.c_int32, ct.c_uint64, ct.c_uint64,
+                                     ct.c_int64, _P, ct.POINTER(ct.c_int64)]),
     "snp_strerror": (ct.c_char_p, [ct.c_int]),
     "snp_last_error": (ct.c_char_p, []),
 }
@@ -324,3 +336,21 @@ def export_compressed(desc) -> np.ndarray:
 
 def paper_format_elements(form: int, q: int, m: int, z: int) -> int:
     return int(load().snp_paper_format_elements(form, q, m, z))
+
+
+# ---- stepping without allocation -------------------------------------------
+
+def snp_step_noalloc(q, m, rule_offsets, rule_k, rule_j, rule_c, rule_p, rule_d, in_offsets, in_sources,
+                     C, D, P, S, *, select=SNP_SELECT_FIRST, seed=0, step=0, n=1, stream=None, wait=True):
+    """snp_step_noalloc over caller-owned device buffers (torch CUDA tensors
+    or raw pointers, int32).  For callers that cannot allocate device memory:
+    the library uses its fixed static scratch (q <= SNP_NOALLOC_MAX_Q).
+    Returns the executed step count when wait, else None."""
+    num_in = in_sources.numel() if hasattr(in_sources, "numel") else 0
+    d = snp_device_system(int(q), int(m), int(num_in), _ptr(rule_offsets), _ptr(rule_k), _ptr(rule_j),
+                          _ptr(rule_c), _ptr(rule_p), _ptr(rule_d), _ptr(in_offsets), _ptr(in_sources),
+                          _ptr(C), _ptr(D), _ptr(P), _ptr(S))
+    done = ct.c_int64(0)
+    check(load().snp_step_noalloc(ct.byref(d), int(select), int(seed) & (2**64 - 1), int(step), int(n),
+                                  _stream_handle(stream), ct.byref(done) if wait else None))
+    return int(done.value) if wait else None
