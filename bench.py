@@ -6,7 +6,8 @@ a^k(a^j)*/a^c -> a^p;d plus one forgetting rule per neuron, d in [0,5],
 initial spikes uniform in 0..20, Philox-keyed nondeterministic selection.
 
 One bench step = one snp_step call advancing one system by `--call-steps`
-SNP steps (default 48) on the grid-wide pull engine.  To keep the inputs of
+SNP steps (default 48) on the tiled pull engine (emissions in shared
+memory, one fused launch per SNP step).  To keep the inputs of
 consecutive timed iterations out of L2 (129 MB), R replicas of the system
 (same graph, different Philox seeds; 4 x ~126 MB on the device) are stepped
 round-robin, so a system's data has been evicted by the time it is stepped
@@ -207,6 +208,8 @@ def main():
     ap.add_argument("--call-steps", type=int, default=48)
     ap.add_argument("--replicas", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--engine", default="tiled", choices=["tiled", "launch"],
+                    help="tiled: emissions in shared memory (default); launch: emissions gathered from L2")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -223,8 +226,9 @@ def main():
     desc, _, mode = synth.large_1m()
     stream = torch.cuda.Stream()
     T = args.call_steps
+    engine = {"tiled": libsnp.SNP_ENGINE_TILED, "launch": libsnp.SNP_ENGINE_LAUNCH}[args.engine]
     systems = [libsnp.System(desc, select=libsnp.SNP_SELECT_PHILOX, seed=desc.seed + 7919 * r + 104729 * rank,
-                             engine=libsnp.SNP_ENGINE_LAUNCH, stream=stream) for r in range(args.replicas)]
+                             engine=engine, stream=stream) for r in range(args.replicas)]
     foot = sum(s.info().device_bytes for s in systems)
     for i in range(args.warmup):
         systems[i % len(systems)].step(T, wait=False)
@@ -284,7 +288,7 @@ def main():
     alg = algorithmic_bytes_per_step(desc)
     achieved = alg * executed / dev_s / 1e9
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "step_pull_1m_traffic.json")
+    prof = os.path.join(ROOT, "profiles", f"{args.engine}_1m_traffic.txt")
     if os.path.exists(prof):
         try:
             with open(prof) as f:
@@ -301,14 +305,15 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "engine": "grid-wide pull, one fused launch per SNP step",
+            "config": {"workload": WORKLOAD, "engine": {"tiled": "tiled pull (emissions in shared memory), one fused launch per SNP step",
+                                                     "launch": "grid-wide pull, emissions gathered from L2, one fused launch per SNP step"}[args.engine],
                        "snp_steps_per_bench_step": T, "replicas_round_robin": len(systems),
                        "l2": f"inputs larger than L2: {len(systems)} replicas, {foot / 1e6:.0f} MB on the device, "
                              f"stepped round-robin", "parallelism": f"replicas x{ws}",
                        "q": desc.q, "num_syn": desc.num_syn, "snp_steps_timed": int(executed)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_step_pull (fused gather + select)",
+                         "kernel": {"tiled": "k_tiled (fused gather + select)", "launch": "k_step_pull (fused gather + select)"}[args.engine],
                          "algorithmic_bytes_per_snp_step": alg},
             "e2e": {"value": e2e_value, "unit": "synaptic updates/s", "h2d_bytes_per_step": 3 * 4 * q,
                     "d2h_bytes_per_step": 4 * q,

@@ -76,11 +76,19 @@ extern "C" {
  *                          launches), every CTA working on one step;
  *   SNP_ENGINE_RESIDENT -- one CTA owns the whole system and runs all steps
  *                          in one launch with the spike emissions kept in
- *                          shared memory (systems up to SNP_RESIDENT_MAX_Q). */
+ *                          shared memory (systems whose two bit-packed
+ *                          emission vectors fit in one CTA's shared memory,
+ *                          about 460,000 neurons at 4 bits).               */
 #define SNP_ENGINE_AUTO 0
 #define SNP_ENGINE_LAUNCH 1
 #define SNP_ENGINE_RESIDENT 2
-#define SNP_RESIDENT_MAX_Q 262144
+/*   SNP_ENGINE_TILED    -- one grid-wide launch per step like LAUNCH, but
+ *                          every CTA copies the bit-packed emission vector
+ *                          into shared memory (in source partitions when it
+ *                          does not fit at once) so in-neighbour reads are
+ *                          shared-memory reads; the default for large
+ *                          systems under AUTO.                              */
+#define SNP_ENGINE_TILED 3
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both
  * callbacks are called on the thread that calls into the library.        */

@@ -75,7 +75,15 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// ---- chunk graphs of the grid-wide engine ------------------------------
+// ---- chunk graphs of the grid-wide engines ------------------------------
+
+// One pull launch of the system's grid-wide engine (L2-gather or tiled).
+static cudaError_t launch_pull_any(snp_system* s, int kind, int32_t t, cudaStream_t st) {
+    if (effective_engine(s) == SNP_ENGINE_TILED)
+        return launch_tiled(s->dev, s->tiled, kind, t, st, s->compact, s->opt.select, s->tiled_smem,
+                            s->tiled_threads);
+    return launch_pull(s->dev, kind, t, st, s->compact, s->opt.select);
+}
 
 static int build_chunk_graph(snp_system* s) {
     if (s->chunk_exec) return SNP_OK;
@@ -90,7 +98,7 @@ static int build_chunk_graph(snp_system* s) {
         if (s->opt.prop == SNP_PROP_PUSH)
             launch_push_step(s->dev, t, s->cap_stream, compact, sel);
         else
-            launch_pull(s->dev, kPullFused, t, s->cap_stream, compact, sel);
+            launch_pull_any(s, kPullFused, t, s->cap_stream);
     }
     launch_advance(s->dev, kChunk, s->cap_stream);
     if (cudaStreamEndCapture(s->cap_stream, &g) != cudaSuccess) return cuda_fail("end capture");
@@ -123,7 +131,7 @@ static int step_launch_engine(snp_system* s, int64_t n) {
         if (launch_finish(s->dev, (int32_t)left, st) != cudaSuccess) return cuda_fail("finish");
         return SNP_OK;
     }
-    if (launch_pull(s->dev, kPullSelectOnly, 0, st, compact, sel) != cudaSuccess) return cuda_fail("select");
+    if (launch_pull_any(s, kPullSelectOnly, 0, st) != cudaSuccess) return cuda_fail("select");
     int64_t rem = n - 1;
     if (rem >= kChunk) {
         int rc = build_chunk_graph(s);
@@ -134,13 +142,14 @@ static int step_launch_engine(snp_system* s, int64_t n) {
         rem -= kChunk;
     }
     for (int64_t t = 0; t < rem; ++t)
-        if (launch_pull(s->dev, kPullFused, (int32_t)t, st, compact, sel) != cudaSuccess) return cuda_fail("step");
-    if (launch_pull(s->dev, kPullGatherOnly, (int32_t)rem, st, compact, sel) != cudaSuccess) return cuda_fail("gather");
+        if (launch_pull_any(s, kPullFused, (int32_t)t, st) != cudaSuccess) return cuda_fail("step");
+    if (launch_pull_any(s, kPullGatherOnly, (int32_t)rem, st) != cudaSuccess) return cuda_fail("gather");
     if (launch_finish(s->dev, (int32_t)(rem + 1), st) != cudaSuccess) return cuda_fail("finish");
     return SNP_OK;
 }
 
 bool resident_fits(const snp_system* s, ResidentPlan* plan) {
+    if (!s->has_in_lists) return false;
     const int eb = resident_e_bits(s->max_p);
     const size_t smem = resident_smem_bytes(s->q, eb);
     if ((long long)smem + 1024 > (long long)resident_max_smem()) return false;
@@ -170,7 +179,17 @@ int effective_engine(const snp_system* s) {
     if (s->opt.prop == SNP_PROP_PUSH) return SNP_ENGINE_LAUNCH;
     if (s->opt.engine == SNP_ENGINE_RESIDENT) return SNP_ENGINE_RESIDENT;
     if (s->opt.engine == SNP_ENGINE_LAUNCH) return SNP_ENGINE_LAUNCH;
-    return (s->q <= kAutoResidentMaxQ && resident_fits(s, nullptr)) ? SNP_ENGINE_RESIDENT : SNP_ENGINE_LAUNCH;
+    if (s->opt.engine == SNP_ENGINE_TILED) return SNP_ENGINE_TILED;
+    if (s->q <= kAutoResidentMaxQ && resident_fits(s, nullptr)) return SNP_ENGINE_RESIDENT;
+    return s->has_tiled ? SNP_ENGINE_TILED : SNP_ENGINE_LAUNCH;
+}
+
+// Which layouts a system needs, from its options and size (before packing).
+static void plan_layouts(const snp_options& o, int32_t q, bool* want_tiled, bool* want_in_lists) {
+    *want_tiled = o.prop == SNP_PROP_PULL &&
+                  (o.engine == SNP_ENGINE_TILED || (o.engine == SNP_ENGINE_AUTO && q > kAutoResidentMaxQ));
+    // sliced ELL in-lists: the L2-gather and resident engines and the batch
+    *want_in_lists = o.engine != SNP_ENGINE_TILED;
 }
 
 int read_flags(snp_system* s, int64_t* exec) {
@@ -194,7 +213,10 @@ int read_flags(snp_system* s, int64_t* exec) {
 
 int run_steps(snp_system* s, int64_t n) {
     if (n <= 0) return SNP_OK;
-    return effective_engine(s) == SNP_ENGINE_RESIDENT ? step_resident(s, n) : step_launch_engine(s, n);
+    const int eng = effective_engine(s);
+    if ((eng == SNP_ENGINE_LAUNCH || eng == SNP_ENGINE_RESIDENT) && s->opt.prop == SNP_PROP_PULL && !s->has_in_lists)
+        return fail(SNP_ERR_UNSUPPORTED, "system was created for the tiled engine only");
+    return eng == SNP_ENGINE_RESIDENT ? step_resident(s, n) : step_launch_engine(s, n);
 }
 
 }  // namespace snp
@@ -230,21 +252,50 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     if (o.form != SNP_FORM_OPT) return fail(SNP_ERR_UNSUPPORTED, "only SNP_FORM_OPT is built in this library");
     if (o.prop != SNP_PROP_PULL && o.prop != SNP_PROP_PUSH) return fail(SNP_ERR_INVALID, "bad prop");
     if (o.select != SNP_SELECT_FIRST && o.select != SNP_SELECT_PHILOX) return fail(SNP_ERR_INVALID, "bad select");
-    if (o.engine < SNP_ENGINE_AUTO || o.engine > SNP_ENGINE_RESIDENT) return fail(SNP_ERR_INVALID, "bad engine");
-    if (o.prop == SNP_PROP_PUSH && o.engine == SNP_ENGINE_RESIDENT)
-        return fail(SNP_ERR_UNSUPPORTED, "the resident engine is pull-only");
+    if (o.engine < SNP_ENGINE_AUTO || o.engine > SNP_ENGINE_TILED) return fail(SNP_ERR_INVALID, "bad engine");
+    if (o.prop == SNP_PROP_PUSH && (o.engine == SNP_ENGINE_RESIDENT || o.engine == SNP_ENGINE_TILED))
+        return fail(SNP_ERR_UNSUPPORTED, "the resident and tiled engines are pull-only");
 
     snp_system* s = new (std::nothrow) snp_system();
     if (!s) return fail(SNP_ERR_OOM, "host allocation failed");
     s->opt = o;
     s->stream = (cudaStream_t)o.stream;
     if (o.alloc) s->alloc = *o.alloc;
+    bool want_tiled = false, want_in = false;
+    plan_layouts(o, desc->q, &want_tiled, &want_in);
     HostPack hp;
-    st = pack_system(desc, o.prop == SNP_PROP_PUSH, kSortWindow, &hp);
+    st = pack_system(desc, o.prop == SNP_PROP_PUSH, false, kSortWindow, &hp);
     if (st) {
         delete s;
         return st;
     }
+    TiledPack tp;
+    if (want_tiled) {
+        int dev = 0, sms = 0, optin = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+            delete s;
+            return cuda_fail("device query");
+        }
+        st = pack_tiled(desc, hp, sms, (size_t)optin - 2048, &tp);
+        if (st == SNP_OK) {
+            s->has_tiled = true;
+            // the resident engine (batches) still needs in-lists when the system fits one CTA
+            if (o.engine == SNP_ENGINE_AUTO && resident_smem_bytes(hp.q, resident_e_bits(hp.max_p)) + 1024 <=
+                                                   (size_t)optin)
+                want_in = true;
+            else if (o.engine == SNP_ENGINE_AUTO)
+                want_in = false;
+        } else if (o.engine == SNP_ENGINE_TILED) {
+            delete s;
+            return st;
+        } else {
+            want_in = true;  // AUTO falls back to the L2-gather engine
+        }
+    }
+    if (want_in) pack_in_lists(desc, &hp);
+    s->has_in_lists = want_in;
     s->q = hp.q;
     s->m = hp.m;
     s->nsyn = hp.nsyn;
@@ -262,7 +313,25 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     d.q = hp.q;
     d.nslices = (hp.q + kSlice - 1) / kSlice;
     d.slice_ptr = upload(s, hp.slice_ptr, &err);
-    if (!err) d.in_idx = upload(s, hp.in_idx, &err);
+    if (!err && want_in) d.in_idx = upload(s, hp.in_idx, &err);
+    if (!err && s->has_tiled) {
+        TiledSys& tl = s->tiled;
+        tl.P = tp.P;
+        tl.part_words = tp.part_words;
+        tl.e_bits = tp.e_bits;
+        tl.G = tp.G;
+        tl.blk = upload(s, tp.blk, &err);
+        if (!err) tl.cnt = upload(s, tp.cnt, &err);
+        if (!err) tl.ent = upload(s, tp.ent, &err);
+        if (!err) tl.cta_lo = upload(s, tp.cta_lo, &err);
+        for (int b = 0; b < 2 && !err; ++b) {
+            std::vector<uint32_t> z((size_t)tp.P * tp.part_words, 0u);
+            tl.Eg[b] = upload(s, z, &err);
+        }
+        s->tiled_smem = tiled_smem_bytes(tp);
+        s->tiled_entries = (int64_t)tp.ent.size();
+        s->tiled_threads = o.threads > 0 ? o.threads : 1024;
+    }
     if (!err && o.prop == SNP_PROP_PUSH) {
         d.out_ptr = upload(s, hp.out_ptr, &err);
         if (!err) d.out_idx = upload(s, hp.out_idx, &err);
@@ -436,14 +505,14 @@ int snp_get_info(const snp_system* s, snp_info* info) {
     info->engine = effective_engine(s);
     info->m = s->m;
     info->num_syn = s->nsyn;
-    info->in_entries = s->in_entries;
+    info->in_entries = info->engine == SNP_ENGINE_TILED ? s->tiled_entries : s->in_entries;
     info->out_entries = s->out_entries;
     info->rule_words = s->rule_words;
     info->device_bytes = (int64_t)s->device_bytes;
     info->max_rules = s->max_rules;
     info->max_p = s->max_p;
     info->compact_rules = s->compact ? 1 : 0;
-    info->e_bits = resident_e_bits(s->max_p);
+    info->e_bits = info->engine == SNP_ENGINE_TILED ? s->tiled.e_bits : resident_e_bits(s->max_p);
     info->step = s->host_step;
     return SNP_OK;
 }

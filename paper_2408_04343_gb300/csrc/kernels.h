@@ -34,6 +34,18 @@ size_t resident_smem_bytes(int max_q, int e_bits);
 cudaError_t launch_resident(const DevSys* d_systems, const long long* d_nsteps, int nsys, unsigned int* d_work,
                             const ResidentPlan& plan, bool compact, int sel, cudaStream_t st);
 int resident_max_smem();
+
+// Tiled engine (kernels_tiled.cu): device view of a TiledPack.
+struct TiledSys {
+    int32_t P, part_words, e_bits, G;
+    const int32_t* blk;
+    const uint8_t* cnt;
+    const int32_t* ent;
+    const int32_t* cta_lo;
+    uint32_t* Eg[2];  // packed emissions of step k in Eg[k & 1]
+};
+cudaError_t launch_tiled(const DevSys& s, const TiledSys& tl, int kind, int32_t t, cudaStream_t st, bool compact,
+                         int sel, size_t smem, int threads);
 cudaError_t launch_gather_results(const DevSys* d_systems, int nsys, unsigned long long* d_out, cudaStream_t st);
 
 }  // namespace snp

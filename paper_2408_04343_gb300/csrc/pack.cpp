@@ -86,7 +86,23 @@ int validate_desc(const snp_desc* d) {
     return SNP_OK;
 }
 
-int pack_system(const snp_desc* d, bool want_out_lists, int window, HostPack* hp) {
+void pack_in_lists(const snp_desc* d, HostPack* hp) {
+    const int32_t q = hp->q;
+    const int32_t nslices = (q + kSlice - 1) / kSlice;
+    hp->in_idx.assign((size_t)hp->slice_ptr[nslices] * kSlice, q);
+    std::vector<int32_t> fill(q, 0);
+    for (int32_t i = 0; i < q; ++i) {
+        const int32_t si = hp->inv[i];
+        for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e) {
+            const int32_t s = hp->inv[d->syn_targets[e]];
+            const int32_t col = fill[s]++;
+            const int64_t sl = s / kSlice, lane = s % kSlice;
+            hp->in_idx[((int64_t)hp->slice_ptr[sl] + col) * kSlice + lane] = si;
+        }
+    }
+}
+
+int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int window, HostPack* hp) {
     const int32_t q = d->q;
     const int64_t m = d->rule_offsets[q];
     const int64_t nsyn = d->num_syn;
@@ -172,19 +188,7 @@ int pack_system(const snp_desc* d, bool want_out_lists, int window, HostPack* hp
         if (acc > INT32_MAX) return fail(SNP_ERR_INVALID, "in-lists too large for 32-bit slice offsets");
     }
     hp->slice_ptr[nslices] = (int32_t)acc;
-    hp->in_idx.assign((size_t)acc * kSlice, q);
-    {
-        std::vector<int32_t> fill(q, 0);
-        for (int32_t i = 0; i < q; ++i) {
-            const int32_t si = hp->inv[i];
-            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e) {
-                const int32_t s = hp->inv[d->syn_targets[e]];
-                const int32_t col = fill[s]++;
-                const int64_t sl = s / kSlice, lane = s % kSlice;
-                hp->in_idx[((int64_t)hp->slice_ptr[sl] + col) * kSlice + lane] = si;
-            }
-        }
-    }
+    if (want_in_lists) pack_in_lists(d, hp);
 
     // out-lists (push): sliced ELL by source slot, pad = -1
     if (want_out_lists) {
@@ -216,6 +220,119 @@ int pack_system(const snp_desc* d, bool want_out_lists, int window, HostPack* hp
 
     hp->C0.resize(q);
     for (int32_t s = 0; s < q; ++s) hp->C0[s] = d->init_spikes[hp->perm[s]];
+    return SNP_OK;
+}
+
+int tiled_e_bits(int max_p) {
+    if (max_p <= 3) return 2;
+    if (max_p <= 15) return 4;
+    if (max_p <= 255) return 8;
+    return 16;
+}
+
+size_t tiled_smem_bytes(const TiledPack& tp) {
+    size_t b = (size_t)tp.part_words * 4;
+    if (tp.P > 1) b += (size_t)tp.max_slices * kSlice * 4;
+    return b;
+}
+
+int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget, TiledPack* tp) {
+    const int32_t q = hp.q;
+    const int32_t nslices = (q + kSlice - 1) / kSlice;
+    const int eb = tiled_e_bits(hp.max_p);
+    if (G < 1) G = 1;
+
+    // in-neighbour lists by target slot, sources as slots, sorted
+    std::vector<int64_t> ioff((size_t)q + 1, 0);
+    for (int64_t e = 0; e < hp.nsyn; ++e) ioff[(size_t)hp.inv[d->syn_targets[e]] + 1]++;
+    for (int32_t s = 0; s < q; ++s) ioff[s + 1] += ioff[s];
+    std::vector<int32_t> isrc((size_t)hp.nsyn);
+    {
+        std::vector<int64_t> fill(ioff.begin(), ioff.end() - 1);
+        for (int32_t i = 0; i < q; ++i) {
+            const int32_t si = hp.inv[i];
+            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e)
+                isrc[(size_t)fill[hp.inv[d->syn_targets[e]]]++] = si;
+        }
+        for (int32_t s = 0; s < q; ++s) std::sort(isrc.begin() + ioff[s], isrc.begin() + ioff[s + 1]);
+    }
+
+    // CTA ranges of slices, balanced by entries plus a per-slice cost
+    std::vector<int32_t> cta_lo((size_t)G + 1, nslices);
+    {
+        std::vector<int64_t> cost((size_t)nslices + 1, 0);
+        for (int32_t sl = 0; sl < nslices; ++sl) {
+            const int64_t a = ioff[std::min<int64_t>(q, (int64_t)sl * kSlice)];
+            const int64_t b = ioff[std::min<int64_t>(q, (int64_t)(sl + 1) * kSlice)];
+            cost[sl + 1] = cost[sl] + (b - a) + 64;
+        }
+        int32_t sl = 0;
+        for (int g = 0; g < G; ++g) {
+            cta_lo[g] = sl;
+            const int64_t target = cost[nslices] * (g + 1) / G;
+            while (sl < nslices && cost[sl + 1] <= target) ++sl;
+        }
+        cta_lo[G] = nslices;
+    }
+    int32_t max_slices = 0;
+    for (int g = 0; g < G; ++g) max_slices = std::max(max_slices, cta_lo[g + 1] - cta_lo[g]);
+
+    // partitions: the fewest whose shared memory fits the budget
+    int P = 0, part_size = 0, part_words = 0;
+    for (int p = 1; p <= 64; ++p) {
+        int64_t ps = ((int64_t)q + p - 1) / p;
+        ps = (ps + 511) / 512 * 512;
+        const int64_t words = ps * eb / 32;
+        size_t need = (size_t)words * 4 + (p > 1 ? (size_t)max_slices * kSlice * 4 : 0);
+        if (need <= smem_budget) {
+            P = p;
+            part_size = (int)ps;
+            part_words = (int)words;
+            break;
+        }
+    }
+    if (P == 0) return fail(SNP_ERR_UNSUPPORTED, "no source partitioning fits shared memory");
+
+    tp->e_bits = eb;
+    tp->P = P;
+    tp->part_size = part_size;
+    tp->part_words = part_words;
+    tp->G = G;
+    tp->max_slices = max_slices;
+    tp->cta_lo = cta_lo;
+    tp->blk.assign((size_t)nslices * P + 1, 0);
+    tp->cnt.assign((size_t)nslices * P * kSlice, 0);
+    tp->ent.clear();
+    tp->ent.reserve((size_t)hp.nsyn);
+    // per lane and partition: the range of its sorted in-list in that partition
+    std::vector<int64_t> cur(kSlice), end(kSlice);
+    for (int32_t sl = 0; sl < nslices; ++sl) {
+        for (int h = 0; h < P; ++h) {
+            const int64_t blk_id = (int64_t)sl * P + h;
+            tp->blk[blk_id] = (int32_t)tp->ent.size();
+            const int32_t lo_src = h * part_size, hi_src = (int32_t)std::min<int64_t>(q, (int64_t)(h + 1) * part_size);
+            int32_t maxn = 0;
+            for (int l = 0; l < kSlice; ++l) {
+                const int64_t s = (int64_t)sl * kSlice + l;
+                if (s >= q) {
+                    cur[l] = end[l] = 0;
+                    continue;
+                }
+                auto b = isrc.begin() + ioff[s], e = isrc.begin() + ioff[s + 1];
+                cur[l] = std::lower_bound(b, e, lo_src) - isrc.begin();
+                end[l] = std::lower_bound(b, e, hi_src) - isrc.begin();
+                const int64_t n = end[l] - cur[l];
+                if (n > 255) return fail(SNP_ERR_UNSUPPORTED, "more than 255 in-neighbours of one neuron in one partition");
+                tp->cnt[blk_id * kSlice + l] = (uint8_t)n;
+                maxn = std::max<int32_t>(maxn, (int32_t)n);
+            }
+            for (int32_t t = 0; t < maxn; ++t)
+                for (int l = 0; l < kSlice; ++l)
+                    if (cur[l] + t < end[l]) tp->ent.push_back(isrc[(size_t)(cur[l] + t)] - lo_src);
+            if (tp->ent.size() > (size_t)INT32_MAX) return fail(SNP_ERR_UNSUPPORTED, "too many entries");
+        }
+    }
+    tp->blk[(size_t)nslices * P] = (int32_t)tp->ent.size();
     return SNP_OK;
 }
 

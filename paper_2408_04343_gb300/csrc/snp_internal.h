@@ -90,6 +90,35 @@ struct HostPack {
     std::vector<int32_t> C0;          // slot order
 };
 
+// Layout of the tiled engine (shared-memory emissions, source partitions).
+// Sources are cut into P partitions of part_size slots so that one
+// partition's bit-packed emissions fit in shared memory.  For slice s and
+// partition h, the in-neighbours of the 32 lanes that lie in h form one
+// block: lane l has cnt[(s*P+h)*32+l] of them, stored "jagged column-major":
+// column t holds, in lane order, the t-th entry of every lane with more than
+// t entries, so a warp reads each column with one coalesced load and no
+// padding.  Entries are source slots relative to the partition start.
+struct TiledPack {
+    int e_bits = 0;          // bits per emission (2, 4, 8, 16)
+    int P = 0;               // partitions
+    int part_size = 0;       // slots per partition (multiple of 512)
+    int part_words = 0;      // 32-bit words of one partition's emissions
+    int G = 0;               // CTAs of a launch (one range of slices each)
+    int max_slices = 0;      // most slices given to one CTA
+    std::vector<int32_t> blk;   // [nslices*P + 1] block starts in ent
+    std::vector<uint8_t> cnt;   // [nslices*P*32] entries per lane and block
+    std::vector<int32_t> ent;   // entries
+    std::vector<int32_t> cta_lo;  // [G + 1] first slice of each CTA
+};
+
+// Bits per packed emission for the largest p of a system.
+int tiled_e_bits(int max_p);
+// Builds the tiled layout; returns SNP_ERR_UNSUPPORTED when the system does
+// not fit it (a lane with more than 255 in-neighbours in one partition, or no
+// partitioning fits the shared-memory budget).
+int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget, TiledPack* out);
+size_t tiled_smem_bytes(const TiledPack& tp);
+
 // Thread-local error text for snp_last_error().
 void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
@@ -97,6 +126,8 @@ const char* last_error();
 
 // Validation and packing (pack.cpp).  window: in-degree sort window (slots).
 int validate_desc(const snp_desc* d);
-int pack_system(const snp_desc* d, bool want_out_lists, int window, HostPack* out);
+int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int window, HostPack* out);
+// Fills hp->in_idx (sliced ELL) from an already packed slot order.
+void pack_in_lists(const snp_desc* d, HostPack* hp);
 
 }  // namespace snp

@@ -41,6 +41,13 @@ struct snp_system {
     std::vector<int64_t> rule_offsets;  // caller's N_Pi (for set_state checks)
     unsigned long long host_step = 0;   // last step counter read back
     std::atomic<int> busy{0};
+    // tiled engine
+    bool has_tiled = false;
+    bool has_in_lists = false;
+    snp::TiledSys tiled{};
+    size_t tiled_smem = 0;
+    int64_t tiled_entries = 0;
+    int32_t tiled_threads = 1024;
 };
 
 namespace snp {

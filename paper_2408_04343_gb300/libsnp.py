@@ -20,7 +20,7 @@ SNP_OK, SNP_ERR_INVALID, SNP_ERR_OOM, SNP_ERR_CUDA, SNP_ERR_TIMEOUT, SNP_ERR_OVE
 SNP_FORM_OPT, SNP_FORM_ELL, SNP_FORM_DENSE = 0, 1, 2
 SNP_PROP_PULL, SNP_PROP_PUSH = 0, 1
 SNP_SELECT_FIRST, SNP_SELECT_PHILOX = 0, 1
-SNP_ENGINE_AUTO, SNP_ENGINE_LAUNCH, SNP_ENGINE_RESIDENT = 0, 1, 2
+SNP_ENGINE_AUTO, SNP_ENGINE_LAUNCH, SNP_ENGINE_RESIDENT, SNP_ENGINE_TILED = 0, 1, 2, 3
 
 
 class SnpError(RuntimeError):

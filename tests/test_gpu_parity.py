@@ -12,7 +12,8 @@ from paper_2408_04343_gb300 import libsnp, synth
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-ENGINES = {"launch": libsnp.SNP_ENGINE_LAUNCH, "resident": libsnp.SNP_ENGINE_RESIDENT}
+ENGINES = {"launch": libsnp.SNP_ENGINE_LAUNCH, "resident": libsnp.SNP_ENGINE_RESIDENT,
+           "tiled": libsnp.SNP_ENGINE_TILED, "auto": libsnp.SNP_ENGINE_AUTO}
 SEL = {oracle.FIRST: libsnp.SNP_SELECT_FIRST, oracle.PHILOX: libsnp.SNP_SELECT_PHILOX}
 
 
@@ -55,7 +56,7 @@ def compare(desc, nsteps, mode, seed, *, engine="launch", prop=libsnp.SNP_PROP_P
     return k
 
 
-@pytest.mark.parametrize("engine", ["launch", "resident"])
+@pytest.mark.parametrize("engine", ["launch", "resident", "tiled"])
 @pytest.mark.parametrize("q", [1, 2, 31, 32, 33, 100, 1000, 4099])
 def test_ragged_sizes_every_step(engine, q):
     d = synth.random_system(q, 50 + q, outdeg=(1, 8), rules=(2, 4), d_range=(0, 3), spikes=(0, 10))
@@ -63,7 +64,7 @@ def test_ragged_sizes_every_step(engine, q):
         compare(d, 40, mode, 977 + q, engine=engine)
 
 
-@pytest.mark.parametrize("engine", ["launch", "resident"])
+@pytest.mark.parametrize("engine", ["launch", "resident", "tiled", "auto"])
 def test_small_1k_workload_every_step(engine):
     d, nsteps, mode = synth.small_1k()
     compare(d, nsteps, mode, d.seed, engine=engine)
@@ -75,7 +76,7 @@ def test_small_1k_push_every_step():
     compare(d, 60, oracle.PHILOX, 5, prop=libsnp.SNP_PROP_PUSH)
 
 
-@pytest.mark.parametrize("engine", ["launch", "resident"])
+@pytest.mark.parametrize("engine", ["launch", "resident", "tiled"])
 def test_chunked_calls_and_graphs(engine):
     """Calls of many sizes (crossing the captured-graph chunk length)."""
     d = synth.random_system(3000, 99, outdeg=(4, 16), rules=(3, 4), d_range=(0, 5), spikes=(0, 20))
@@ -91,7 +92,7 @@ def test_push_matches_with_delays_and_skew():
 def test_sort_system_sorts():
     for v in ([3, 2, 1], [5, 1, 4, 4, 2], list(range(40, 0, -1))):
         d = synth.sort_system(v)
-        for eng in ("launch", "resident"):
+        for eng in ("launch", "resident", "tiled"):
             n = compare(d, 1000, oracle.FIRST, 0, engine=eng, chunks=(1, 50))
             assert n == max(v) + 1
         gs = libsnp.System(d)
@@ -108,7 +109,7 @@ def test_hand_delay_traces():
                   [(0, 1), (2, 0), (3, 2)], [1, 0, 1, 1]),
     ]
     for d in cases:
-        for eng in ("launch", "resident"):
+        for eng in ("launch", "resident", "tiled"):
             compare(d, 20, oracle.FIRST, 0, engine=eng)
         compare(d, 20, oracle.FIRST, 0, prop=libsnp.SNP_PROP_PUSH)
 
@@ -146,7 +147,7 @@ def test_device_outputs_and_stream():
 def test_overflow_is_reported():
     from tests.test_oracle import make_desc
     d = make_desc(2, [[(1, 1, 1, 1000, 0)], []], [(0, 1)], [10, 2**31 - 600])
-    for eng in (libsnp.SNP_ENGINE_LAUNCH, libsnp.SNP_ENGINE_RESIDENT):
+    for eng in (libsnp.SNP_ENGINE_LAUNCH, libsnp.SNP_ENGINE_RESIDENT, libsnp.SNP_ENGINE_TILED):
         g = libsnp.System(d, engine=eng)
         with pytest.raises(libsnp.SnpError) as ei:
             g.step(5)
@@ -156,7 +157,7 @@ def test_overflow_is_reported():
 def test_halted_system_reports_zero_steps():
     from tests.test_oracle import make_desc
     d = make_desc(3, [[], [(2, 0, 2, 1, 0)], []], [(1, 0)], [5, 1, 0])
-    for eng in ("launch", "resident"):
+    for eng in ("launch", "resident", "tiled"):
         g = libsnp.System(d, engine=ENGINES[eng])
         assert g.step(10) == 0
         assert g.config().tolist() == [5, 1, 0]
@@ -201,9 +202,27 @@ def test_busy_system_is_refused_during_batch():
     b.close()
 
 
+@pytest.mark.parametrize("p_range,q", [((1, 15), 70000), ((1, 200), 90000), ((1, 1000), 120000)])
+def test_tiled_emission_widths_and_partitions(p_range, q):
+    """4-, 8- and 16-bit packed emissions; the 16-bit case needs two source
+    partitions (the partial sums wait in shared memory)."""
+    d = synth.random_system(q, 77 + q, outdeg=(4, 16), rules=(3, 4), p_range=p_range, d_range=(0, 5),
+                            spikes=(0, 20))
+    g = libsnp.System(d, engine=libsnp.SNP_ENGINE_TILED)
+    inf = g.info()
+    assert inf.e_bits == {15: 4, 200: 8, 1000: 16}[p_range[1]]
+    g.close()
+    compare(d, 25, oracle.PHILOX, 5, engine="tiled", chunks=(1, 24))
+
+
 def test_large_1m_full_size_sampled():
     """The 1,048,576-neuron workload in the launch configuration the bench
-    times (grid-wide engine, Philox selection): every state is compared
-    after steps 1, 2, 3, 10, 58 and 150."""
+    times (tiled engine, two source partitions, Philox selection): every
+    state is compared after steps 1, 2, 3, 10, 58 and 150; the L2-gather
+    engine after steps 1 and 49."""
     d, _, mode = synth.large_1m()
-    compare(d, 150, mode, d.seed, engine="launch", chunks=(1, 1, 1, 7, 48, 92))
+    g = libsnp.System(d, engine=libsnp.SNP_ENGINE_TILED)
+    assert g.info().e_bits == 2
+    g.close()
+    compare(d, 150, mode, d.seed, engine="tiled", chunks=(1, 1, 1, 7, 48, 92))
+    compare(d, 49, mode, d.seed, engine="launch", chunks=(1, 48))
