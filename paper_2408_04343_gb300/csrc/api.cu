@@ -176,6 +176,7 @@ static int step_resident(snp_system* s, int64_t n) {
 }
 
 int effective_engine(const snp_system* s) {
+    if (s->opt.form != SNP_FORM_OPT) return SNP_ENGINE_LAUNCH;
     if (s->opt.prop == SNP_PROP_PUSH) return SNP_ENGINE_LAUNCH;
     if (s->opt.engine == SNP_ENGINE_RESIDENT) return SNP_ENGINE_RESIDENT;
     if (s->opt.engine == SNP_ENGINE_LAUNCH) return SNP_ENGINE_LAUNCH;
@@ -186,10 +187,46 @@ int effective_engine(const snp_system* s) {
 
 // Which layouts a system needs, from its options and size (before packing).
 static void plan_layouts(const snp_options& o, int32_t q, bool* want_tiled, bool* want_in_lists) {
+    if (o.form != SNP_FORM_OPT) {
+        *want_tiled = *want_in_lists = false;
+        return;
+    }
     *want_tiled = o.prop == SNP_PROP_PULL &&
                   (o.engine == SNP_ENGINE_TILED || (o.engine == SNP_ENGINE_AUTO && q > kAutoResidentMaxQ));
     // sliced ELL in-lists: the L2-gather and resident engines and the batch
     *want_in_lists = o.engine != SNP_ENGINE_TILED;
+}
+
+// ELL form (pull or push) and dense form: plain launches per step.
+static int step_ell_forms(snp_system* s, int64_t n) {
+    const bool compact = s->compact;
+    const int sel = s->opt.select;
+    cudaStream_t st = s->stream;
+    const EllSys& e = s->ell;
+    if (launch_begin(s->dev, st) != cudaSuccess) return cuda_fail("begin");
+    if (s->opt.form == SNP_FORM_ELL && s->opt.prop == SNP_PROP_PULL) {
+        if (launch_ell_pull(s->dev, e, kPullSelectOnly, 0, st, compact, sel) != cudaSuccess) return cuda_fail("select");
+        for (int64_t t = 0; t + 1 < n; ++t)
+            if (launch_ell_pull(s->dev, e, kPullFused, (int32_t)t, st, compact, sel) != cudaSuccess)
+                return cuda_fail("ell step");
+        if (launch_ell_pull(s->dev, e, kPullGatherOnly, (int32_t)(n - 1), st, compact, sel) != cudaSuccess)
+            return cuda_fail("ell gather");
+    } else if (s->opt.form == SNP_FORM_ELL) {
+        for (int64_t t = 0; t < n; ++t) {
+            if (launch_ell_select(s->dev, e, false, true, (int32_t)t, st, compact, sel) != cudaSuccess ||
+                launch_ell_push(s->dev, e, (int32_t)t, st) != cudaSuccess)
+                return cuda_fail("ell push step");
+        }
+    } else {
+        if (launch_ell_select(s->dev, e, false, true, 0, st, compact, sel) != cudaSuccess) return cuda_fail("select");
+        for (int64_t t = 0; t < n; ++t) {
+            if (launch_dense_accum(s->dev, e, (int32_t)t, st) != cudaSuccess ||
+                launch_ell_select(s->dev, e, true, t + 1 < n, (int32_t)(t + 1), st, compact, sel) != cudaSuccess)
+                return cuda_fail("dense step");
+        }
+    }
+    if (launch_finish(s->dev, (int32_t)n, st) != cudaSuccess) return cuda_fail("finish");
+    return SNP_OK;
 }
 
 int read_flags(snp_system* s, int64_t* exec) {
@@ -213,6 +250,7 @@ int read_flags(snp_system* s, int64_t* exec) {
 
 int run_steps(snp_system* s, int64_t n) {
     if (n <= 0) return SNP_OK;
+    if (s->opt.form != SNP_FORM_OPT) return step_ell_forms(s, n);
     const int eng = effective_engine(s);
     if ((eng == SNP_ENGINE_LAUNCH || eng == SNP_ENGINE_RESIDENT) && s->opt.prop == SNP_PROP_PULL && !s->has_in_lists)
         return fail(SNP_ERR_UNSUPPORTED, "system was created for the tiled engine only");
@@ -249,12 +287,17 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     snp_options o;
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    if (o.form != SNP_FORM_OPT) return fail(SNP_ERR_UNSUPPORTED, "only SNP_FORM_OPT is built in this library");
+    if (o.form != SNP_FORM_OPT && o.form != SNP_FORM_ELL && o.form != SNP_FORM_DENSE)
+        return fail(SNP_ERR_INVALID, "bad form");
     if (o.prop != SNP_PROP_PULL && o.prop != SNP_PROP_PUSH) return fail(SNP_ERR_INVALID, "bad prop");
     if (o.select != SNP_SELECT_FIRST && o.select != SNP_SELECT_PHILOX) return fail(SNP_ERR_INVALID, "bad select");
     if (o.engine < SNP_ENGINE_AUTO || o.engine > SNP_ENGINE_TILED) return fail(SNP_ERR_INVALID, "bad engine");
     if (o.prop == SNP_PROP_PUSH && (o.engine == SNP_ENGINE_RESIDENT || o.engine == SNP_ENGINE_TILED))
         return fail(SNP_ERR_UNSUPPORTED, "the resident and tiled engines are pull-only");
+    if (o.form != SNP_FORM_OPT && o.engine != SNP_ENGINE_AUTO && o.engine != SNP_ENGINE_LAUNCH)
+        return fail(SNP_ERR_UNSUPPORTED, "the ELL and dense forms run on the launch engine");
+    if (o.form == SNP_FORM_DENSE && o.prop != SNP_PROP_PULL)
+        return fail(SNP_ERR_UNSUPPORTED, "the dense form walks matrix columns (pull) only");
 
     snp_system* s = new (std::nothrow) snp_system();
     if (!s) return fail(SNP_ERR_OOM, "host allocation failed");
@@ -264,7 +307,15 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     bool want_tiled = false, want_in = false;
     plan_layouts(o, desc->q, &want_tiled, &want_in);
     HostPack hp;
-    st = pack_system(desc, o.prop == SNP_PROP_PUSH, false, kSortWindow, &hp);
+    st = pack_system(desc, o.form == SNP_FORM_OPT && o.prop == SNP_PROP_PUSH, false, kSortWindow, &hp);
+    if (st) {
+        delete s;
+        return st;
+    }
+    EllPack ep;
+    std::vector<int32_t> dense;
+    if (o.form == SNP_FORM_ELL) st = pack_ell(desc, hp, o.prop == SNP_PROP_PULL, o.prop == SNP_PROP_PUSH, &ep);
+    if (o.form == SNP_FORM_DENSE) st = pack_dense(desc, hp, &dense);
     if (st) {
         delete s;
         return st;
@@ -314,15 +365,42 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     d.nslices = (hp.q + kSlice - 1) / kSlice;
     d.slice_ptr = upload(s, hp.slice_ptr, &err);
     if (!err && want_in) d.in_idx = upload(s, hp.in_idx, &err);
+    if (!err && o.form != SNP_FORM_OPT) {
+        EllSys& e = s->ell;
+        e.m = hp.m;
+        if (!ep.in_ptr.empty()) {
+            e.in_ptr = upload(s, ep.in_ptr, &err);
+            if (!err) e.in_ent = reinterpret_cast<const int2*>(upload(s, ep.in_ent, &err));
+            s->in_entries = (int64_t)ep.in_ent.size() / 2;
+        }
+        if (!err && !ep.out_ptr.empty()) {
+            e.out_ptr = upload(s, ep.out_ptr, &err);
+            if (!err) e.out_ent = reinterpret_cast<const int2*>(upload(s, ep.out_ent, &err));
+            s->out_entries = (int64_t)ep.out_ent.size() / 2;
+        }
+        if (!err && o.form == SNP_FORM_DENSE) {
+            e.dense = upload(s, dense, &err);
+            std::vector<int32_t> z((size_t)hp.q, 0);
+            if (!err) e.inflow = upload(s, z, &err);
+            s->in_entries = (int64_t)dense.size();
+        }
+        std::vector<uint8_t> em((size_t)hp.m + 1, 0);
+        for (int b = 0; b < 2 && !err; ++b) e.Em[b] = upload(s, em, &err);
+    }
     if (!err && s->has_tiled) {
         TiledSys& tl = s->tiled;
         tl.P = tp.P;
         tl.part_words = tp.part_words;
         tl.e_bits = tp.e_bits;
         tl.G = tp.G;
-        tl.blk = upload(s, tp.blk, &err);
-        if (!err) tl.cnt = upload(s, tp.cnt, &err);
+        tl.acc_words = tp.acc_words;
+        tl.src_bits = tp.src_bits;
+        tl.grp = upload(s, tp.grp, &err);
         if (!err) tl.ent = upload(s, tp.ent, &err);
+        if (!err) {
+            std::vector<int32_t> z((size_t)d.nslices * kSlice, 0);
+            tl.inflow = upload(s, z, &err);
+        }
         if (!err) tl.cta_lo = upload(s, tp.cta_lo, &err);
         for (int b = 0; b < 2 && !err; ++b) {
             std::vector<uint32_t> z((size_t)tp.P * tp.part_words, 0u);

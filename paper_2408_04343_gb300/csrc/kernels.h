@@ -37,15 +37,33 @@ int resident_max_smem();
 
 // Tiled engine (kernels_tiled.cu): device view of a TiledPack.
 struct TiledSys {
-    int32_t P, part_words, e_bits, G;
-    const int32_t* blk;
-    const uint8_t* cnt;
-    const int32_t* ent;
-    const int32_t* cta_lo;
-    uint32_t* Eg[2];  // packed emissions of step k in Eg[k & 1]
+    int32_t P, part_words, e_bits, G, acc_words, src_bits;
+    const int32_t* grp;     // [G*P+1] group starts (words, multiples of 4)
+    const uint32_t* ent;    // (dst_local << src_bits) | src_local
+    const int32_t* cta_lo;  // [G+1] slice ranges
+    uint32_t* Eg[2];        // packed emissions of step k in Eg[k & 1]
+    int32_t* inflow;        // [nslices*32] in-flow of the step being finished
 };
 cudaError_t launch_tiled(const DevSys& s, const TiledSys& tl, int kind, int32_t t, cudaStream_t st, bool compact,
                          int sel, size_t smem, int threads);
 cudaError_t launch_gather_results(const DevSys* d_systems, int nsys, unsigned long long* d_out, cudaStream_t st);
+
+// ELL and dense forms (kernels_ell.cu).
+struct EllSys {
+    int64_t m;
+    const int32_t* in_ptr;   // in-ELL slice starts (units of 32 pairs)
+    const int2* in_ent;      // (rule, p) pairs, pad (m, 0)
+    const int32_t* out_ptr;  // out-ELL rule-slice starts (units of 32 pairs)
+    const int2* out_ent;     // (target, p) pairs, pad (-1, 0)
+    uint8_t* Em[2];          // [m+1] rule r emits at step k: Em[k & 1][r]
+    const int32_t* dense;    // m x q positive part of M_Pi (dense form)
+    int32_t* inflow;         // [q] in-flow of the step being finished (dense form)
+};
+cudaError_t launch_ell_pull(const DevSys& s, const EllSys& e, int kind, int32_t t, cudaStream_t st, bool compact,
+                            int sel);
+cudaError_t launch_ell_select(const DevSys& s, const EllSys& e, bool inflow, bool select, int32_t t, cudaStream_t st,
+                              bool compact, int sel);
+cudaError_t launch_ell_push(const DevSys& s, const EllSys& e, int32_t t, cudaStream_t st);
+cudaError_t launch_dense_accum(const DevSys& s, const EllSys& e, int32_t t, cudaStream_t st);
 
 }  // namespace snp

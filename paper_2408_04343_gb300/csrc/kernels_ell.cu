@@ -1,0 +1,257 @@
+// The ELL form and the uncompressed ("Sparse") form of the transition matrix.
+//
+// Both forms keep the paper's per-rule view: the spiking vector has one entry
+// per rule (Sec. 2: S_k of length m), and spikes travel as (rule, value)
+// pairs.  Em_k[r] = 1 when rule r emits at step k (it fired with d = 0, or
+// its delay ran out), stored as bytes, double-buffered by step parity.
+//
+//  * ELL pull: each target neuron sums Em_k[r] * p over the (rule, p) pairs
+//    of its in-ELL column (the transpose of M^s_Pi's +p rows, Sec. 3);
+//  * ELL push: each emitting rule walks its column of M^s_Pi and adds p into
+//    every open target with warp-aggregated atomics (Alg. 4's direction);
+//  * dense: each neuron walks its column of M_Pi over all m rules and adds
+//    Em_k[r] * M[r, j] (Alg. 3's direction); the (row block x neuron tile)
+//    partial sums meet in an in-flow vector, and the select launch applies it.
+// Consumption (-c) is applied when a rule is selected (the pair in row 0 of
+// M^s_Pi is not walked): with delays a rule consumes at t and emits at t+d.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace snp {
+
+// Returns true if the launch for absolute step kg must not run (shared with
+// kernels_step.cu's protocol: activity words by step mod 3, sticky halt).
+__device__ __forceinline__ bool ell_check_halt(uint32_t* fl, unsigned long long* steps, unsigned long long kg) {
+    if (ld_volatile(fl + kFlagHalted)) return true;
+    if (ld_volatile(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
+        if (threadIdx.x == 0) {
+            steps[kStepHalt] = kg;
+            __threadfence();
+            atomicExch(fl + kFlagHalted, 1u);
+        }
+        return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void ell_raise_activity(uint32_t* fl, unsigned long long ks, bool active) {
+    if (__syncthreads_or(active) && threadIdx.x == 0) {
+        uint32_t* a = fl + kFlagAct0 + (int)(ks % 3ull);
+        if (ld_volatile(a) == 0u) atomicExch(a, 1u);
+    }
+}
+
+// Select for step ks on one slot, writing the per-rule emission bytes.
+template <bool COMPACT, int SEL>
+__device__ __forceinline__ bool ell_select_slot(const DevSys& s, const EllSys& e, int32_t slot, int32_t& c,
+                                                unsigned long long ks) {
+    const uint32_t st = s.st[slot];
+    const int32_t r0 = __ldg(s.rule_off + slot), r1 = __ldg(s.rule_off + slot + 1);
+    const SelOut o = select_neuron<COMPACT, SEL>(s.rules, r0, r1, c, st, ks,
+                                                 SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u,
+                                                 s.seed);
+    int32_t emitting = -1;  // local index of the rule that emits at ks
+    if ((st >> kPendShift) != 0u && (st & kDMask) == 0u) emitting = (int32_t)(st >> kPendShift) - 1;
+    else if (o.s >= 0 && o.emit > 0) emitting = o.s;
+    uint8_t* Em = e.Em[ks & 1ull];
+    for (int32_t r = r0; r < r1; ++r) Em[r] = (r - r0) == emitting ? 1 : 0;
+    c = o.c_after;
+    s.S[ks & 1ull][slot] = o.s;
+    s.st[slot] = o.st;
+    return o.active;
+}
+
+// ELL pull: gather of step kg (+ select of kg+1), like k_step_pull.
+template <bool GATHER, bool SELECT, bool COMPACT, int SEL>
+__global__ void __launch_bounds__(256) k_ell_pull(DevSys s, EllSys e, int32_t t) {
+    uint32_t* fl = s.flags;
+    const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
+    const unsigned long long ks = GATHER ? kg + 1ull : kg;
+    if (GATHER) {
+        if (ell_check_halt(fl, s.step, kg)) return;
+        if (SELECT && blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
+    }
+    const int lane = threadIdx.x & 31;
+    const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t slot = slice * kSlice + lane;
+    bool active = false;
+    if (slice < s.nslices) {
+        const bool valid = slot < s.q;
+        int32_t c = valid ? s.C[slot] : 0;
+        if (GATHER) {
+            const uint8_t* __restrict__ Em = e.Em[kg & 1ull];
+            const int32_t b = __ldg(e.in_ptr + slice);
+            const int32_t w = __ldg(e.in_ptr + slice + 1) - b;
+            const int2* __restrict__ p = e.in_ent + (size_t)b * kSlice + lane;
+            long long sum = 0;
+            int32_t col = 0;
+            for (; col + 4 <= w; col += 4) {
+                const int2 a0 = __ldg(p + (col + 0) * kSlice), a1 = __ldg(p + (col + 1) * kSlice);
+                const int2 a2 = __ldg(p + (col + 2) * kSlice), a3 = __ldg(p + (col + 3) * kSlice);
+                sum += (Em[a0.x] ? a0.y : 0) + (Em[a1.x] ? a1.y : 0) + (Em[a2.x] ? a2.y : 0) + (Em[a3.x] ? a3.y : 0);
+            }
+            for (; col < w; ++col) {
+                const int2 a = __ldg(p + col * kSlice);
+                sum += Em[a.x] ? a.y : 0;
+            }
+            if (valid && (s.st[slot] >> kPendShift) == 0u) {
+                long long nc = (long long)c + sum;
+                if (nc > 2147483647ll) {
+                    atomicOr(fl + kFlagOverflow, 1u);
+                    nc = 2147483647ll;
+                }
+                c = (int32_t)nc;
+            }
+        }
+        if (SELECT && valid) active = ell_select_slot<COMPACT, SEL>(s, e, slot, c, ks);
+        if (valid) s.C[slot] = c;
+    }
+    if (SELECT) ell_raise_activity(fl, ks, active);
+}
+
+// Select launch of step ks = base + t for the push and dense variants.  With
+// INFLOW it first finishes step ks - 1 by adding the in-flow accumulated by
+// the dense launch (to open neurons) and clears it; with !SELECT it only
+// finishes.
+template <bool INFLOW, bool SELECT, bool COMPACT, int SEL>
+__global__ void __launch_bounds__(256) k_ell_select(DevSys s, EllSys e, int32_t t) {
+    uint32_t* fl = s.flags;
+    const unsigned long long ks = s.step[kStepBase] + (unsigned long long)t;
+    if (ld_volatile(fl + kFlagHalted)) return;
+    const int32_t slot = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    bool active = false;
+    if (slot < s.q) {
+        int32_t c = s.C[slot];
+        if (INFLOW) {
+            const int32_t in = e.inflow[slot];
+            e.inflow[slot] = 0;
+            if ((s.st[slot] >> kPendShift) == 0u) {
+                long long nc = (long long)c + in;
+                if (nc > 2147483647ll) {
+                    atomicOr(fl + kFlagOverflow, 1u);
+                    nc = 2147483647ll;
+                }
+                c = (int32_t)nc;
+            }
+        }
+        if (SELECT) active = ell_select_slot<COMPACT, SEL>(s, e, slot, c, ks);
+        s.C[slot] = c;
+    }
+    if (SELECT) ell_raise_activity(fl, ks, active);
+}
+
+// ELL push of step kg = base + t: a warp per 32 consecutive rules.
+__global__ void __launch_bounds__(256) k_ell_push(DevSys s, EllSys e, int32_t t) {
+    uint32_t* fl = s.flags;
+    const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
+    if (ell_check_halt(fl, s.step, kg)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 1ull) % 3ull)] = 0u;
+    const int lane = threadIdx.x & 31;
+    const int64_t rs = (int64_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int64_t nrs = (e.m + kSlice - 1) / kSlice;
+    if (rs >= nrs) return;  // warp-uniform
+    const int64_t r = rs * kSlice + lane;
+    const bool on = r < e.m && e.Em[kg & 1ull][r];
+    const int32_t b = __ldg(e.out_ptr + rs);
+    const int32_t w = __ldg(e.out_ptr + rs + 1) - b;
+    const int2* __restrict__ p = e.out_ent + (size_t)b * kSlice + lane;
+    for (int32_t col = 0; col < w; ++col) {
+        int2 a = on ? __ldg(p + col * kSlice) : make_int2(-1, 0);
+        if (a.x >= 0 && (s.st[a.x] >> kPendShift) != 0u) a.x = -1;  // closed target: lost
+        const unsigned grp = __match_any_sync(0xffffffffu, a.x);
+        const unsigned add = __reduce_add_sync(grp, a.x >= 0 ? (unsigned)a.y : 0u);
+        if (a.x >= 0 && (__ffs(grp) - 1) == lane) {
+            const int old = atomicAdd(s.C + a.x, (int)add);
+            if ((long long)old + (long long)add > 2147483647ll) atomicOr(fl + kFlagOverflow, 1u);
+        }
+    }
+}
+
+// Dense accumulation of step kg = base + t: CTA (bx, by) covers neurons
+// [bx*256, bx*256+256) and rules [by*rows, (by+1)*rows); every rule row of
+// M_Pi is read whether or not the rule emits, as Alg. 3 walks all m rules.
+__global__ void __launch_bounds__(256) k_dense_accum(DevSys s, EllSys e, int32_t t, int32_t rows) {
+    uint32_t* fl = s.flags;
+    const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
+    if (ell_check_halt(fl, s.step, kg)) return;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * rows;
+    const int64_t r1 = r0 + rows < e.m ? r0 + rows : e.m;
+    const uint8_t* __restrict__ Em = e.Em[kg & 1ull];
+    if (j >= s.q) return;
+    long long sum = 0;
+    const int32_t* __restrict__ col = e.dense + j;
+    for (int64_t r = r0; r < r1; ++r) sum += (long long)Em[r] * __ldg(col + r * (int64_t)s.q);
+    if (sum) {
+        const int old = atomicAdd(e.inflow + j, (int)sum);
+        if ((long long)old + sum > 2147483647ll) atomicOr(fl + kFlagOverflow, 1u);
+    }
+}
+
+// ---- launchers ----------------------------------------------------------
+
+template <bool G, bool S>
+static cudaError_t ell_pull_t(const DevSys& s, const EllSys& e, int32_t t, cudaStream_t st, bool compact, int sel) {
+    const dim3 grid((unsigned)((s.nslices + 7) / 8));
+    if (compact) {
+        if (sel == SNP_SELECT_FIRST) k_ell_pull<G, S, true, SNP_SELECT_FIRST><<<grid, 256, 0, st>>>(s, e, t);
+        else k_ell_pull<G, S, true, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, e, t);
+    } else {
+        if (sel == SNP_SELECT_FIRST) k_ell_pull<G, S, false, SNP_SELECT_FIRST><<<grid, 256, 0, st>>>(s, e, t);
+        else k_ell_pull<G, S, false, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, e, t);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ell_pull(const DevSys& s, const EllSys& e, int kind, int32_t t, cudaStream_t st, bool compact,
+                            int sel) {
+    switch (kind) {
+        case kPullSelectOnly: return ell_pull_t<false, true>(s, e, t, st, compact, sel);
+        case kPullFused: return ell_pull_t<true, true>(s, e, t, st, compact, sel);
+        case kPullGatherOnly: return ell_pull_t<true, false>(s, e, t, st, compact, sel);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool IN, bool S>
+static cudaError_t ell_select_t(const DevSys& s, const EllSys& e, int32_t t, cudaStream_t st, bool compact, int sel) {
+    const dim3 grid((unsigned)((s.q + 255) / 256));
+    if (compact) {
+        if (sel == SNP_SELECT_FIRST) k_ell_select<IN, S, true, SNP_SELECT_FIRST><<<grid, 256, 0, st>>>(s, e, t);
+        else k_ell_select<IN, S, true, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, e, t);
+    } else {
+        if (sel == SNP_SELECT_FIRST) k_ell_select<IN, S, false, SNP_SELECT_FIRST><<<grid, 256, 0, st>>>(s, e, t);
+        else k_ell_select<IN, S, false, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, e, t);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ell_select(const DevSys& s, const EllSys& e, bool inflow, bool select, int32_t t, cudaStream_t st,
+                              bool compact, int sel) {
+    if (inflow) return select ? ell_select_t<true, true>(s, e, t, st, compact, sel)
+                              : ell_select_t<true, false>(s, e, t, st, compact, sel);
+    return ell_select_t<false, true>(s, e, t, st, compact, sel);
+}
+
+cudaError_t launch_ell_push(const DevSys& s, const EllSys& e, int32_t t, cudaStream_t st) {
+    const int64_t nrs = (e.m + kSlice - 1) / kSlice;
+    if (nrs == 0) {
+        k_ell_push<<<1, 32, 0, st>>>(s, e, t);  // still settles the halt test
+        return cudaGetLastError();
+    }
+    k_ell_push<<<(unsigned)((nrs + 7) / 8), 256, 0, st>>>(s, e, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_accum(const DevSys& s, const EllSys& e, int32_t t, cudaStream_t st) {
+    const int32_t rows = 512;
+    const unsigned gy = (unsigned)((e.m + rows - 1) / rows);
+    const dim3 grid((unsigned)((s.q + 255) / 256), gy > 0 ? gy : 1u);
+    k_dense_accum<<<grid, 256, 0, st>>>(s, e, t, rows);
+    return cudaGetLastError();
+}
+
+}  // namespace snp

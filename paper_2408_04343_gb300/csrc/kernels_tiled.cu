@@ -7,13 +7,17 @@
 // is at most 3) and every CTA copies it into its shared memory, one source
 // partition at a time, so the gathers become shared-memory reads.
 //
-// One persistent launch per step, one CTA per SM, each CTA owning a range of
-// slices (32 neurons, one warp each).  For every partition h the CTA loads
-// h's packed emissions, then each warp walks the jagged column-major blocks
-// of its slices (one coalesced load per column, no padding) and accumulates
-// per-lane sums; with more than one partition the sums wait in shared memory
-// for the select pass, which also writes the packed E_{k+1} for the next
-// launch.  Same fusion, halt test and status word as k_step_pull.
+// A step is two launches:
+//  * k_tiled_gather -- one CTA per SM, each owning a range of slices.  For
+//    every partition h the CTA loads h's packed emissions and streams its
+//    group of in-edge words edge-parallel (16-byte vector loads, no
+//    per-neuron bookkeeping): each word names a local target slot and a
+//    source, whose emission is added to the target's shared-memory
+//    accumulator.  The accumulators become the in-flow vector of step k.
+//  * k_tiled_select -- full occupancy, one warp per slice: finishes step k
+//    (C_{k+1} = C' + [open] * in-flow), selects step k+1 and writes the
+//    packed E_{k+1} that the next gather loads.
+// Same status word, fixed-point test and activity words as k_step_pull.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -21,16 +25,18 @@
 
 namespace snp {
 
-__device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
-    int32_t v;
-    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+__device__ __forceinline__ uint4 ld_stream_v4(const uint4* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
     return v;
 }
 
 template <int EB>
-__device__ __forceinline__ uint32_t pk_get(const uint32_t* __restrict__ e, int32_t i) {
-    constexpr uint32_t mask = (EB == 32) ? 0xffffffffu : ((1u << EB) - 1u);
-    const uint32_t bit = (uint32_t)i * EB;
+__device__ __forceinline__ uint32_t pk_get(const uint32_t* __restrict__ e, uint32_t i) {
+    constexpr uint32_t mask = (1u << EB) - 1u;
+    const uint32_t bit = i * EB;
     return (e[bit >> 5] >> (bit & 31u)) & mask;
 }
 
@@ -44,64 +50,85 @@ __device__ __forceinline__ void pk_put_slice(uint32_t* e, int32_t slice, int lan
     if (lane % per == 0) e[slice * EB + lane / per] = w;
 }
 
-// Sum of the packed emissions of one lane's in-neighbours in one block.
-template <int EB, int U>
-__device__ __forceinline__ int32_t block_sum(const TiledSys& tl, const uint32_t* __restrict__ Esm, int64_t blk_id,
-                                             int lane) {
-    const int32_t base = __ldg(tl.blk + blk_id);
-    const int32_t n = (int32_t)__ldg(tl.cnt + blk_id * kSlice + lane);
-    const int32_t maxn = __reduce_max_sync(0xffffffffu, (unsigned)n);
-    const unsigned lt = (1u << lane) - 1u;
-    int32_t pos = base;
-    int32_t sum = 0;
-    for (int32_t t = 0; t < maxn; t += U) {
-        int32_t idx[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool v = n > t + u;
-            const unsigned a = __ballot_sync(0xffffffffu, v);
-            idx[u] = v ? ld_stream_i32(tl.ent + pos + __popc(a & lt)) : -1;
-            pos += __popc(a);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (idx[u] >= 0) sum += (int32_t)pk_get<EB>(Esm, idx[u]);
-    }
-    return sum;
+template <int EB>
+__device__ __forceinline__ void edge(const uint32_t* __restrict__ Esm, int* acc, uint32_t w, uint32_t smask,
+                                     int sbits) {
+    const uint32_t v = pk_get<EB>(Esm, w & smask);
+    if (v) atomicAdd(acc + (w >> sbits), (int)v);
 }
 
-template <bool GATHER, bool SELECT, bool COMPACT, int SEL, int EB, bool MULTI>
-__global__ void __launch_bounds__(1024, 1) k_tiled(DevSys s, TiledSys tl, int32_t t) {
-    constexpr int U = 8;
+// In-flow of step kg = base + t into tl.inflow.
+template <int EB>
+__global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl, int32_t t) {
     extern __shared__ uint32_t smem[];
     uint32_t* Esm = smem;
-    int32_t* partial = reinterpret_cast<int32_t*>(smem + tl.part_words);
+    int* acc = reinterpret_cast<int*>(smem + tl.part_words);
     uint32_t* fl = s.flags;
-    const unsigned long long base = s.step[kStepBase];
-    const unsigned long long kg = base + (unsigned long long)t;
-    const unsigned long long ks = GATHER ? kg + 1ull : kg;
-    if (GATHER) {
-        if (ld_volatile(fl + kFlagHalted)) return;
-        if (ld_volatile(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
-            if (threadIdx.x == 0) {
-                s.step[kStepHalt] = kg;
-                __threadfence();
-                atomicExch(fl + kFlagHalted, 1u);
-            }
-            return;
+    const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
+    if (ld_volatile(fl + kFlagHalted)) return;
+    if (ld_volatile(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
+        if (threadIdx.x == 0) {
+            s.step[kStepHalt] = kg;
+            __threadfence();
+            atomicExch(fl + kFlagHalted, 1u);
         }
-        if (SELECT && blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
+        return;
     }
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
     const int32_t lo = __ldg(tl.cta_lo + blockIdx.x), hi = __ldg(tl.cta_lo + blockIdx.x + 1);
-    uint32_t* Enext = tl.Eg[ks & 1ull];
-    bool active = false;
+    for (int i = threadIdx.x; i < tl.acc_words; i += blockDim.x) acc[i] = 0;
+    const uint32_t* Eprev = tl.Eg[kg & 1ull];
+    const uint32_t smask = (tl.src_bits >= 32) ? 0xffffffffu : ((1u << tl.src_bits) - 1u);
+    const int sbits = tl.src_bits;
+    const uint4* ent = reinterpret_cast<const uint4*>(tl.ent);
+    for (int h = 0; h < tl.P; ++h) {
+        const uint4* src = reinterpret_cast<const uint4*>(Eprev + (size_t)h * tl.part_words);
+        uint4* dst = reinterpret_cast<uint4*>(Esm);
+        for (int i = threadIdx.x; i < tl.part_words / 4; i += blockDim.x) dst[i] = __ldcg(src + i);
+        __syncthreads();
+        const int64_t g = (int64_t)blockIdx.x * tl.P + h;
+        const int32_t g0 = __ldg(tl.grp + g) / 4, g1 = __ldg(tl.grp + g + 1) / 4;
+        const int32_t stride = blockDim.x;
+        int32_t i = g0 + threadIdx.x;
+        for (; i + 3 * stride < g1; i += 4 * stride) {
+            const uint4 a = ld_stream_v4(ent + i);
+            const uint4 b = ld_stream_v4(ent + i + stride);
+            const uint4 c = ld_stream_v4(ent + i + 2 * stride);
+            const uint4 d = ld_stream_v4(ent + i + 3 * stride);
+            edge<EB>(Esm, acc, a.x, smask, sbits); edge<EB>(Esm, acc, a.y, smask, sbits);
+            edge<EB>(Esm, acc, a.z, smask, sbits); edge<EB>(Esm, acc, a.w, smask, sbits);
+            edge<EB>(Esm, acc, b.x, smask, sbits); edge<EB>(Esm, acc, b.y, smask, sbits);
+            edge<EB>(Esm, acc, b.z, smask, sbits); edge<EB>(Esm, acc, b.w, smask, sbits);
+            edge<EB>(Esm, acc, c.x, smask, sbits); edge<EB>(Esm, acc, c.y, smask, sbits);
+            edge<EB>(Esm, acc, c.z, smask, sbits); edge<EB>(Esm, acc, c.w, smask, sbits);
+            edge<EB>(Esm, acc, d.x, smask, sbits); edge<EB>(Esm, acc, d.y, smask, sbits);
+            edge<EB>(Esm, acc, d.z, smask, sbits); edge<EB>(Esm, acc, d.w, smask, sbits);
+        }
+        for (; i < g1; i += stride) {
+            const uint4 a = ld_stream_v4(ent + i);
+            edge<EB>(Esm, acc, a.x, smask, sbits); edge<EB>(Esm, acc, a.y, smask, sbits);
+            edge<EB>(Esm, acc, a.z, smask, sbits); edge<EB>(Esm, acc, a.w, smask, sbits);
+        }
+        __syncthreads();
+    }
+    const int32_t slot0 = lo * kSlice;
+    const int32_t nloc = (hi - lo) * kSlice;
+    for (int i = threadIdx.x; i < nloc; i += blockDim.x) tl.inflow[slot0 + i] = acc[i];
+}
 
-    // select phase of one slice; `sum` is its gathered in-flow (GATHER only)
-    auto finish_slice = [&](int32_t slice, int32_t sum) {
-        const int32_t slot = slice * kSlice + lane;
+// Finishes step kg (GATHER: adds the in-flow to open neurons) and selects
+// step ks (SELECT), one warp per slice.
+template <bool GATHER, bool SELECT, bool COMPACT, int SEL, int EB>
+__global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int32_t t) {
+    uint32_t* fl = s.flags;
+    const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
+    const unsigned long long ks = GATHER ? kg + 1ull : kg;
+    if (ld_volatile(fl + kFlagHalted)) return;
+    const int lane = threadIdx.x & 31;
+    const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t slot = slice * kSlice + lane;
+    bool active = false;
+    if (slice < s.nslices) {
         const bool valid = slot < s.q;
         int32_t c = 0;
         uint32_t st = 0u;
@@ -110,7 +137,7 @@ __global__ void __launch_bounds__(1024, 1) k_tiled(DevSys s, TiledSys tl, int32_
             st = s.st[slot];
         }
         if (GATHER && valid && (st >> kPendShift) == 0u) {
-            const long long nc = (long long)c + sum;
+            const long long nc = (long long)c + tl.inflow[slot];
             if (nc > 2147483647ll) {
                 atomicOr(fl + kFlagOverflow, 1u);
                 c = 2147483647;
@@ -124,37 +151,13 @@ __global__ void __launch_bounds__(1024, 1) k_tiled(DevSys s, TiledSys tl, int32_
                 s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), c, st, ks,
                 SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
             c = o.c_after;
-            active |= o.active;
+            active = o.active;
             emit = (uint32_t)o.emit;
             s.S[ks & 1ull][slot] = o.s;
             s.st[slot] = o.st;
         }
         if (valid) s.C[slot] = c;
-        if (SELECT) pk_put_slice<EB>(Enext, slice, lane, emit);
-    };
-
-    if (GATHER) {
-        const uint32_t* Eprev = tl.Eg[kg & 1ull];
-        for (int h = 0; h < tl.P; ++h) {
-            const uint4* src = reinterpret_cast<const uint4*>(Eprev + (size_t)h * tl.part_words);
-            uint4* dst = reinterpret_cast<uint4*>(Esm);
-            for (int i = threadIdx.x; i < tl.part_words / 4; i += blockDim.x) dst[i] = __ldcg(src + i);
-            __syncthreads();
-            for (int32_t slice = lo + warp; slice < hi; slice += nwarps) {
-                const int32_t sum = block_sum<EB, U>(tl, Esm, (int64_t)slice * tl.P + h, lane);
-                if (MULTI) {
-                    int32_t* pp = partial + (slice - lo) * kSlice + lane;
-                    *pp = (h == 0) ? sum : *pp + sum;
-                } else {
-                    finish_slice(slice, sum);
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (!GATHER || MULTI) {
-        for (int32_t slice = lo + warp; slice < hi; slice += nwarps)
-            finish_slice(slice, GATHER ? partial[(slice - lo) * kSlice + lane] : 0);
+        if (SELECT) pk_put_slice<EB>(tl.Eg[ks & 1ull], slice, lane, emit);
     }
     if (SELECT) {
         if (__syncthreads_or(active) && threadIdx.x == 0) {
@@ -164,53 +167,53 @@ __global__ void __launch_bounds__(1024, 1) k_tiled(DevSys s, TiledSys tl, int32_
     }
 }
 
-template <bool G, bool S, bool C, int SEL, int EB>
-static cudaError_t launch_tiled_t(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st, size_t smem,
-                                  int threads) {
-    cudaError_t e;
-    if (tl.P > 1) {
-        auto fn = k_tiled<G, S, C, SEL, EB, true>;
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        fn<<<tl.G, threads, smem, st>>>(s, tl, t);
-    } else {
-        auto fn = k_tiled<G, S, C, SEL, EB, false>;
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        fn<<<tl.G, threads, smem, st>>>(s, tl, t);
-    }
+template <int EB>
+static cudaError_t launch_gather_eb(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st, size_t smem,
+                                    int threads) {
+    auto fn = k_tiled_gather<EB>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<tl.G, threads, smem, st>>>(s, tl, t);
     return cudaGetLastError();
 }
 
-template <bool G, bool S, bool C, int SEL>
-static cudaError_t launch_tiled_eb(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st, size_t smem,
-                                   int threads) {
-    switch (tl.e_bits) {
-        case 2: return launch_tiled_t<G, S, C, SEL, 2>(s, tl, t, st, smem, threads);
-        case 4: return launch_tiled_t<G, S, C, SEL, 4>(s, tl, t, st, smem, threads);
-        case 8: return launch_tiled_t<G, S, C, SEL, 8>(s, tl, t, st, smem, threads);
-        case 16: return launch_tiled_t<G, S, C, SEL, 16>(s, tl, t, st, smem, threads);
-        default: return cudaErrorInvalidValue;
-    }
+template <bool G, bool S, bool C, int SEL, int EB>
+static cudaError_t launch_select_t(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st) {
+    const dim3 grid((unsigned)((s.nslices + 7) / 8));
+    k_tiled_select<G, S, C, SEL, EB><<<grid, 256, 0, st>>>(s, tl, t);
+    return cudaGetLastError();
 }
 
-template <bool G, bool S>
-static cudaError_t launch_tiled_k(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st, bool compact,
-                                  int sel, size_t smem, int threads) {
-    if (compact) {
-        if (sel == SNP_SELECT_FIRST) return launch_tiled_eb<G, S, true, SNP_SELECT_FIRST>(s, tl, t, st, smem, threads);
-        return launch_tiled_eb<G, S, true, SNP_SELECT_PHILOX>(s, tl, t, st, smem, threads);
+template <int EB>
+static cudaError_t launch_tiled_eb(const DevSys& s, const TiledSys& tl, int kind, int32_t t, cudaStream_t st,
+                                   bool compact, int sel, size_t smem, int threads) {
+    cudaError_t e = cudaSuccess;
+    if (kind != kPullSelectOnly) e = launch_gather_eb<EB>(s, tl, t, st, smem, threads);
+    if (e != cudaSuccess) return e;
+#define SNP_TILED_SEL(G, S)                                                                              \
+    do {                                                                                                 \
+        if (compact)                                                                                     \
+            return sel == SNP_SELECT_FIRST ? launch_select_t<G, S, true, SNP_SELECT_FIRST, EB>(s, tl, t, st) \
+                                           : launch_select_t<G, S, true, SNP_SELECT_PHILOX, EB>(s, tl, t, st); \
+        return sel == SNP_SELECT_FIRST ? launch_select_t<G, S, false, SNP_SELECT_FIRST, EB>(s, tl, t, st)    \
+                                       : launch_select_t<G, S, false, SNP_SELECT_PHILOX, EB>(s, tl, t, st);  \
+    } while (0)
+    switch (kind) {
+        case kPullSelectOnly: SNP_TILED_SEL(false, true);
+        case kPullFused: SNP_TILED_SEL(true, true);
+        case kPullGatherOnly: SNP_TILED_SEL(true, false);
+        default: return cudaErrorInvalidValue;
     }
-    if (sel == SNP_SELECT_FIRST) return launch_tiled_eb<G, S, false, SNP_SELECT_FIRST>(s, tl, t, st, smem, threads);
-    return launch_tiled_eb<G, S, false, SNP_SELECT_PHILOX>(s, tl, t, st, smem, threads);
+#undef SNP_TILED_SEL
 }
 
 cudaError_t launch_tiled(const DevSys& s, const TiledSys& tl, int kind, int32_t t, cudaStream_t st, bool compact,
                          int sel, size_t smem, int threads) {
-    switch (kind) {
-        case kPullSelectOnly: return launch_tiled_k<false, true>(s, tl, t, st, compact, sel, smem, threads);
-        case kPullFused: return launch_tiled_k<true, true>(s, tl, t, st, compact, sel, smem, threads);
-        case kPullGatherOnly: return launch_tiled_k<true, false>(s, tl, t, st, compact, sel, smem, threads);
+    switch (tl.e_bits) {
+        case 2: return launch_tiled_eb<2>(s, tl, kind, t, st, compact, sel, smem, threads);
+        case 4: return launch_tiled_eb<4>(s, tl, kind, t, st, compact, sel, smem, threads);
+        case 8: return launch_tiled_eb<8>(s, tl, kind, t, st, compact, sel, smem, threads);
+        case 16: return launch_tiled_eb<16>(s, tl, kind, t, st, compact, sel, smem, threads);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -223,6 +223,102 @@ int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int 
     return SNP_OK;
 }
 
+int pack_ell(const snp_desc* d, const HostPack& hp, bool want_pull, bool want_push, EllPack* ep) {
+    const int32_t q = hp.q;
+    const int64_t m = hp.m;
+    const int32_t nslices = (q + kSlice - 1) / kSlice;
+    // firing rules (p > 0) of every source slot, as (slot rule id, p)
+    auto rule_id = [&](int32_t i, int64_t r) { return (int32_t)(hp.rule_off[hp.inv[i]] + (r - d->rule_offsets[i])); };
+    std::vector<int32_t> nfire(q, 0);
+    for (int32_t i = 0; i < q; ++i)
+        for (int64_t r = d->rule_offsets[i]; r < d->rule_offsets[i + 1]; ++r) nfire[i] += d->rule_p[r] > 0;
+    if (want_pull) {
+        std::vector<int64_t> len(q, 0);  // pairs per target slot
+        for (int32_t i = 0; i < q; ++i)
+            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e) len[hp.inv[d->syn_targets[e]]] += nfire[i];
+        ep->in_ptr.assign((size_t)nslices + 1, 0);
+        int64_t acc = 0;
+        for (int32_t sl = 0; sl < nslices; ++sl) {
+            int64_t w = 0;
+            for (int l = 0; l < kSlice; ++l) {
+                const int64_t s = (int64_t)sl * kSlice + l;
+                if (s < q) w = std::max(w, len[s]);
+            }
+            ep->in_ptr[sl] = (int32_t)acc;
+            acc += w;
+            if (acc * kSlice * 2 > INT32_MAX) return fail(SNP_ERR_UNSUPPORTED, "ELL in-lists too large");
+        }
+        ep->in_ptr[nslices] = (int32_t)acc;
+        ep->in_ent.assign((size_t)acc * kSlice * 2, 0);
+        for (int64_t x = 0; x < acc * kSlice; ++x) ep->in_ent[2 * x] = (int32_t)m;  // pad (m, 0)
+        std::vector<int32_t> fill(q, 0);
+        for (int32_t i = 0; i < q; ++i)
+            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e) {
+                const int32_t s = hp.inv[d->syn_targets[e]];
+                const int64_t sl = s / kSlice, lane = s % kSlice;
+                for (int64_t r = d->rule_offsets[i]; r < d->rule_offsets[i + 1]; ++r) {
+                    if (d->rule_p[r] <= 0) continue;
+                    const int64_t x = ((int64_t)ep->in_ptr[sl] + fill[s]++) * kSlice + lane;
+                    ep->in_ent[2 * x] = rule_id(i, r);
+                    ep->in_ent[2 * x + 1] = d->rule_p[r];
+                }
+            }
+    }
+    if (want_push) {
+        const int64_t nrs = (m + kSlice - 1) / kSlice;
+        // owner slot of every slot rule id
+        std::vector<int32_t> owner((size_t)m);
+        for (int32_t s = 0; s < q; ++s)
+            for (int32_t r = hp.rule_off[s]; r < hp.rule_off[s + 1]; ++r) owner[r] = s;
+        ep->out_ptr.assign((size_t)nrs + 1, 0);
+        int64_t acc = 0;
+        auto col_len = [&](int64_t r) -> int64_t {
+            const int32_t i = hp.perm[owner[r]];
+            const int64_t rr = d->rule_offsets[i] + (r - hp.rule_off[owner[r]]);
+            return d->rule_p[rr] > 0 ? d->syn_offsets[i + 1] - d->syn_offsets[i] : 0;
+        };
+        for (int64_t rs = 0; rs < nrs; ++rs) {
+            int64_t w = 0;
+            for (int l = 0; l < kSlice; ++l) {
+                const int64_t r = rs * kSlice + l;
+                if (r < m) w = std::max(w, col_len(r));
+            }
+            ep->out_ptr[rs] = (int32_t)acc;
+            acc += w;
+            if (acc * kSlice * 2 > INT32_MAX) return fail(SNP_ERR_UNSUPPORTED, "ELL out-lists too large");
+        }
+        ep->out_ptr[nrs] = (int32_t)acc;
+        ep->out_ent.assign((size_t)acc * kSlice * 2, 0);
+        for (int64_t x = 0; x < acc * kSlice; ++x) ep->out_ent[2 * x] = -1;  // pad (-1, 0)
+        for (int64_t r = 0; r < m; ++r) {
+            const int32_t i = hp.perm[owner[r]];
+            const int64_t rr = d->rule_offsets[i] + (r - hp.rule_off[owner[r]]);
+            if (d->rule_p[rr] <= 0) continue;
+            const int64_t rs = r / kSlice, lane = r % kSlice;
+            int64_t row = 0;
+            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e, ++row) {
+                const int64_t x = ((int64_t)ep->out_ptr[rs] + row) * kSlice + lane;
+                ep->out_ent[2 * x] = hp.inv[d->syn_targets[e]];
+                ep->out_ent[2 * x + 1] = d->rule_p[rr];
+            }
+        }
+    }
+    return SNP_OK;
+}
+
+int pack_dense(const snp_desc* d, const HostPack& hp, std::vector<int32_t>* M) {
+    const int64_t q = hp.q, m = hp.m;
+    if (m * q > ((int64_t)1 << 31)) return fail(SNP_ERR_UNSUPPORTED, "dense matrix too large (m q > 2^31)");
+    M->assign((size_t)(m * q), 0);
+    for (int32_t i = 0; i < hp.q; ++i)
+        for (int64_t r = d->rule_offsets[i]; r < d->rule_offsets[i + 1]; ++r) {
+            const int64_t row = hp.rule_off[hp.inv[i]] + (r - d->rule_offsets[i]);
+            for (int64_t e = d->syn_offsets[i]; e < d->syn_offsets[i + 1]; ++e)
+                (*M)[(size_t)(row * q + hp.inv[d->syn_targets[e]])] = d->rule_p[r];
+        }
+    return SNP_OK;
+}
+
 int tiled_e_bits(int max_p) {
     if (max_p <= 3) return 2;
     if (max_p <= 15) return 4;
@@ -231,8 +327,12 @@ int tiled_e_bits(int max_p) {
 }
 
 size_t tiled_smem_bytes(const TiledPack& tp) {
-    size_t b = (size_t)tp.part_words * 4;
-    if (tp.P > 1) b += (size_t)tp.max_slices * kSlice * 4;
+    return (size_t)tp.part_words * 4 + (size_t)tp.acc_words * 4;
+}
+
+static int bits_for(int64_t n) {  // bits to hold 0..n
+    int b = 0;
+    while (((int64_t)1 << b) <= n) ++b;
     return b;
 }
 
@@ -241,6 +341,7 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     const int32_t nslices = (q + kSlice - 1) / kSlice;
     const int eb = tiled_e_bits(hp.max_p);
     if (G < 1) G = 1;
+    if (G > nslices) G = nslices;
 
     // in-neighbour lists by target slot, sources as slots, sorted
     std::vector<int64_t> ioff((size_t)q + 1, 0);
@@ -276,22 +377,27 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     }
     int32_t max_slices = 0;
     for (int g = 0; g < G; ++g) max_slices = std::max(max_slices, cta_lo[g + 1] - cta_lo[g]);
+    const int64_t max_slots = (int64_t)max_slices * kSlice;  // local slot max_slots is the dummy
+    const int dst_bits = bits_for(max_slots);
+    const int acc_words = (int)((max_slots + 1 + 3) / 4 * 4);
 
-    // partitions: the fewest whose shared memory fits the budget
-    int P = 0, part_size = 0, part_words = 0;
-    for (int p = 1; p <= 64; ++p) {
+    // partitions: the fewest whose shared memory and entry encoding fit
+    int P = 0, part_size = 0, part_words = 0, src_bits = 0;
+    for (int p = 1; p <= 256; ++p) {
         int64_t ps = ((int64_t)q + p - 1) / p;
         ps = (ps + 511) / 512 * 512;
         const int64_t words = ps * eb / 32;
-        size_t need = (size_t)words * 4 + (p > 1 ? (size_t)max_slices * kSlice * 4 : 0);
-        if (need <= smem_budget) {
+        const size_t need = (size_t)words * 4 + (size_t)acc_words * 4;
+        const int sb = bits_for(ps - 1);
+        if (need <= smem_budget && sb + dst_bits <= 32) {
             P = p;
             part_size = (int)ps;
             part_words = (int)words;
+            src_bits = sb;
             break;
         }
     }
-    if (P == 0) return fail(SNP_ERR_UNSUPPORTED, "no source partitioning fits shared memory");
+    if (P == 0) return fail(SNP_ERR_UNSUPPORTED, "no source partitioning fits shared memory and 32-bit entries");
 
     tp->e_bits = eb;
     tp->P = P;
@@ -299,40 +405,45 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     tp->part_words = part_words;
     tp->G = G;
     tp->max_slices = max_slices;
+    tp->acc_words = acc_words;
+    tp->src_bits = src_bits;
     tp->cta_lo = cta_lo;
-    tp->blk.assign((size_t)nslices * P + 1, 0);
-    tp->cnt.assign((size_t)nslices * P * kSlice, 0);
+    tp->grp.assign((size_t)G * P + 1, 0);
     tp->ent.clear();
-    tp->ent.reserve((size_t)hp.nsyn);
-    // per lane and partition: the range of its sorted in-list in that partition
+    tp->ent.reserve((size_t)hp.nsyn + (size_t)G * P * 4);
+    const uint32_t dummy = (uint32_t)max_slots << src_bits;
     std::vector<int64_t> cur(kSlice), end(kSlice);
-    for (int32_t sl = 0; sl < nslices; ++sl) {
+    for (int g = 0; g < G; ++g) {
         for (int h = 0; h < P; ++h) {
-            const int64_t blk_id = (int64_t)sl * P + h;
-            tp->blk[blk_id] = (int32_t)tp->ent.size();
-            const int32_t lo_src = h * part_size, hi_src = (int32_t)std::min<int64_t>(q, (int64_t)(h + 1) * part_size);
-            int32_t maxn = 0;
-            for (int l = 0; l < kSlice; ++l) {
-                const int64_t s = (int64_t)sl * kSlice + l;
-                if (s >= q) {
-                    cur[l] = end[l] = 0;
-                    continue;
+            tp->grp[(size_t)g * P + h] = (int32_t)tp->ent.size();
+            const int32_t lo_src = h * part_size;
+            const int32_t hi_src = (int32_t)std::min<int64_t>(q, (int64_t)(h + 1) * part_size);
+            for (int32_t sl = cta_lo[g]; sl < cta_lo[g + 1]; ++sl) {
+                int64_t maxn = 0;
+                for (int l = 0; l < kSlice; ++l) {
+                    const int64_t s = (int64_t)sl * kSlice + l;
+                    if (s >= q) {
+                        cur[l] = end[l] = 0;
+                        continue;
+                    }
+                    auto b = isrc.begin() + ioff[s], e = isrc.begin() + ioff[s + 1];
+                    cur[l] = std::lower_bound(b, e, lo_src) - isrc.begin();
+                    end[l] = std::lower_bound(b, e, hi_src) - isrc.begin();
+                    maxn = std::max(maxn, end[l] - cur[l]);
                 }
-                auto b = isrc.begin() + ioff[s], e = isrc.begin() + ioff[s + 1];
-                cur[l] = std::lower_bound(b, e, lo_src) - isrc.begin();
-                end[l] = std::lower_bound(b, e, hi_src) - isrc.begin();
-                const int64_t n = end[l] - cur[l];
-                if (n > 255) return fail(SNP_ERR_UNSUPPORTED, "more than 255 in-neighbours of one neuron in one partition");
-                tp->cnt[blk_id * kSlice + l] = (uint8_t)n;
-                maxn = std::max<int32_t>(maxn, (int32_t)n);
+                // column-major inside the slice: consecutive words target distinct lanes
+                const uint32_t local0 = (uint32_t)(sl - cta_lo[g]) * kSlice;
+                for (int64_t t = 0; t < maxn; ++t)
+                    for (int l = 0; l < kSlice; ++l)
+                        if (cur[l] + t < end[l])
+                            tp->ent.push_back(((local0 + (uint32_t)l) << src_bits) |
+                                              (uint32_t)(isrc[(size_t)(cur[l] + t)] - lo_src));
             }
-            for (int32_t t = 0; t < maxn; ++t)
-                for (int l = 0; l < kSlice; ++l)
-                    if (cur[l] + t < end[l]) tp->ent.push_back(isrc[(size_t)(cur[l] + t)] - lo_src);
+            while (tp->ent.size() % 4) tp->ent.push_back(dummy);  // 16-byte groups
             if (tp->ent.size() > (size_t)INT32_MAX) return fail(SNP_ERR_UNSUPPORTED, "too many entries");
         }
     }
-    tp->blk[(size_t)nslices * P] = (int32_t)tp->ent.size();
+    tp->grp[(size_t)G * P] = (int32_t)tp->ent.size();
     return SNP_OK;
 }
 

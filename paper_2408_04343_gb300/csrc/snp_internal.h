@@ -92,12 +92,14 @@ struct HostPack {
 
 // Layout of the tiled engine (shared-memory emissions, source partitions).
 // Sources are cut into P partitions of part_size slots so that one
-// partition's bit-packed emissions fit in shared memory.  For slice s and
-// partition h, the in-neighbours of the 32 lanes that lie in h form one
-// block: lane l has cnt[(s*P+h)*32+l] of them, stored "jagged column-major":
-// column t holds, in lane order, the t-th entry of every lane with more than
-// t entries, so a warp reads each column with one coalesced load and no
-// padding.  Entries are source slots relative to the partition start.
+// partition's bit-packed emissions fit in shared memory.  Every CTA of the
+// launch owns a range of slices; for each partition h its in-edges from h
+// form one contiguous group of 32-bit words (dst_local << src_bits) |
+// src_local, where dst_local is the target slot relative to the CTA's first
+// slot and src_local the source slot relative to the partition start.
+// Groups are padded to 4 words with a dummy target so they load as 16-byte
+// vectors.  Inside a slice the words are column-major (t-th in-neighbour of
+// every lane, then the next t), so neighbouring words target distinct slots.
 struct TiledPack {
     int e_bits = 0;          // bits per emission (2, 4, 8, 16)
     int P = 0;               // partitions
@@ -105,17 +107,38 @@ struct TiledPack {
     int part_words = 0;      // 32-bit words of one partition's emissions
     int G = 0;               // CTAs of a launch (one range of slices each)
     int max_slices = 0;      // most slices given to one CTA
-    std::vector<int32_t> blk;   // [nslices*P + 1] block starts in ent
-    std::vector<uint8_t> cnt;   // [nslices*P*32] entries per lane and block
-    std::vector<int32_t> ent;   // entries
+    int acc_words = 0;       // shared in-flow accumulators per CTA (+ dummy)
+    int src_bits = 0;        // low bits of an entry holding the source
+    std::vector<int32_t> grp;     // [G*P + 1] group starts in ent
+    std::vector<uint32_t> ent;    // entries
     std::vector<int32_t> cta_lo;  // [G + 1] first slice of each CTA
 };
 
+// Layouts of the ELL form (Sec. 3, M^s_Pi: a column per rule of (neuron,
+// value) pairs) and of the uncompressed "Sparse" form (Table 1, M_Pi).
+// Rule ids are slot-order ids (rule_off[slot] + local index).  The
+// consumption pair (-c, own neuron) of M^s_Pi's row 0 is not stored: with
+// delays a rule consumes when it fires and emits d steps later, so the
+// consumption is applied by the select phase in every form.
+//  * in-ELL (pull): per target slot, one (rule, p) pair for every firing
+//    rule of every in-neighbour -- the transpose of the +p rows of M^s_Pi --
+//    as sliced ELL (32 targets per slice, column-major pairs, pad (m, 0));
+//  * out-ELL (push): per rule, its column's +p pairs (target slot, p) as
+//    sliced ELL (32 rules per slice, column-major, pad (-1, 0));
+//  * dense: M_Pi's positive part, m x q int32 row-major in slot order.
+struct EllPack {
+    std::vector<int32_t> in_ptr;   // [nslices+1], units of 32 pairs
+    std::vector<int32_t> in_ent;   // pairs as 2 int32 (rule, p)
+    std::vector<int32_t> out_ptr;  // [ceil(m/32)+1], units of 32 pairs
+    std::vector<int32_t> out_ent;  // pairs as 2 int32 (target, p)
+};
+int pack_ell(const snp_desc* d, const HostPack& hp, bool want_pull, bool want_push, EllPack* out);
+int pack_dense(const snp_desc* d, const HostPack& hp, std::vector<int32_t>* M);
+
 // Bits per packed emission for the largest p of a system.
 int tiled_e_bits(int max_p);
-// Builds the tiled layout; returns SNP_ERR_UNSUPPORTED when the system does
-// not fit it (a lane with more than 255 in-neighbours in one partition, or no
-// partitioning fits the shared-memory budget).
+// Builds the tiled layout; returns SNP_ERR_UNSUPPORTED when no partitioning
+// fits the shared-memory budget and the 32-bit entry encoding.
 int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget, TiledPack* out);
 size_t tiled_smem_bytes(const TiledPack& tp);
 

@@ -48,6 +48,8 @@ struct snp_system {
     size_t tiled_smem = 0;
     int64_t tiled_entries = 0;
     int32_t tiled_threads = 1024;
+    // ELL and dense forms
+    snp::EllSys ell{};
 };
 
 namespace snp {
