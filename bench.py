@@ -210,10 +210,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--engine", default="tiled", choices=["tiled", "launch"],
                     help="tiled: emissions in shared memory (default); launch: emissions gathered from L2")
+    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "skewed"],
+                    help="large: the 1M-neuron headline (default); batch: 8,192 systems in one persistent "
+                         "launch vs the plain per-system loop; serve: Poisson request loop; skewed: the "
+                         "2M-neuron power-law system and its 16,384-neuron dense copy")
+    ap.add_argument("--batch-count", type=int, default=8192)
+    ap.add_argument("--rates", default="10,100,1000,10000")
+    ap.add_argument("--requests", type=int, default=200)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        barrier(ws)
+        return
+    if args.workload != "large":
+        import bench_workloads
+        bench_workloads.run(args, ws, rank, local)
         barrier(ws)
         return
 

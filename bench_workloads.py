@@ -1,0 +1,197 @@
+"""Secondary bench workloads (selected with bench.py --workload ...).
+
+batch  -- 8,192 independent systems (q log-uniform in 64..65,536, out-degree
+          U{4..16}, 3 rules, d in [0,4], 500 steps each, Philox) advanced by
+          the batched form (one persistent launch per round, CTA per system)
+          against the plain per-system loop (each system alone on the
+          grid-wide engine, one launch per step, one system after another);
+          the plain loop is timed on every 16th system and compared bit for
+          bit with the batched result.
+serve  -- Poisson request loop: each request a system of q log-uniform in
+          1e3..1e6 with a log-uniform step count in 10..1e4, out-degree
+          U{2..32}, 2-4 rules, d in [0,5]; admitted by a 150 GB device-memory
+          budget; p50/p99 latency (arrival to completion) and aggregate
+          synaptic updates/s per arrival rate.
+skewed -- the 2,097,152-neuron system with truncated Zipf(2.1) out-degree on
+          [1, 4096], 256 steps, on the tiled, L2-gather and push engines and
+          the ELL form; and its 16,384-neuron copy on the dense M_Pi.
+All inputs are seeded synthetic systems (paper_2408_04343_gb300/synth.py).
+"""
+from __future__ import annotations
+
+import os
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+
+def run(args, ws, rank, local):
+    import json
+    import torch
+    from paper_2408_04343_gb300 import build as B, libsnp, synth
+    if rank == 0:
+        B.build()
+    torch.cuda.set_device(local)
+    fn = {"batch": batch, "serve": serve, "skewed": skewed}[args.workload]
+    line = fn(args, libsnp, synth)
+    line.update({"n_gpus": ws, "data": "synthetic", "dtype": "int32", "higher_is_better": True})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _threads():
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def batch(args, libsnp, synth):
+    import torch
+    descs, nsteps, _ = synth.batch_8k(count=args.batch_count, processes=_threads())
+    sel = libsnp.SNP_SELECT_PHILOX
+    with ThreadPoolExecutor(_threads()) as ex:
+        gs = list(ex.map(lambda d: libsnp.System(d, select=sel, seed=d.seed), descs))
+    torch.cuda.synchronize()
+    b = libsnp.Batch()
+    t0 = time.perf_counter()
+    t = b.submit(gs, [nsteps] * len(gs))
+    done = b.wait(t)
+    t1 = time.perf_counter()
+    work = sum(d.num_syn * n for d, n in zip(descs, done))
+    batched = work / (t1 - t0)
+    info = b.info()
+    sample = list(range(0, len(descs), 16))
+    plain = [libsnp.System(descs[i], select=sel, seed=descs[i].seed, engine=libsnp.SNP_ENGINE_LAUNCH)
+             for i in sample]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    pdone = [g.step(nsteps, wait=False) for g in plain]
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    pdone = [g.get_state()[3] for g in plain]
+    pwork = sum(descs[i].num_syn * n for i, n in zip(sample, pdone))
+    plain_v = pwork / (t3 - t2)
+    same = all((plain[j].config() == gs[i].config()).all() and pdone[j] == done[i] for j, i in enumerate(sample))
+    return {"metric": "synaptic updates/s", "workload": "batch", "value": batched, "unit": "synaptic updates/s",
+            "plain_loop_value": plain_v, "speedup_vs_plain_loop": batched / plain_v,
+            "identical_to_plain_loop": bool(same),
+            "config": {"systems": len(descs), "neurons": int(sum(d.q for d in descs)),
+                       "synapses": int(sum(d.num_syn for d in descs)), "steps_each": nsteps,
+                       "rounds": int(info.rounds), "batched_seconds": t1 - t0,
+                       "plain_loop_sample": f"every 16th system ({len(sample)}), one after another, "
+                                            f"{t3 - t2:.2f} s"}}
+
+
+def _request_pool(synth, n, seed=5005):
+    rng = np.random.default_rng(seed)
+    qs = np.floor(np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=n))).astype(int)
+    rules = rng.integers(2, 5, size=n)
+    work = [(int(q), int(r), 77_000 + i) for i, (q, r) in enumerate(zip(qs, rules))]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(_threads()) as pool:
+        return pool.map(_request_system, work)
+
+
+def _request_system(w):
+    from paper_2408_04343_gb300 import synth
+    q, r, s = w
+    return synth.random_system(q, s, outdeg=(2, 32), rules=(r, r), d_range=(0, 5), spikes=(0, 20))
+
+
+def serve(args, libsnp, synth):
+    rates = [float(x) for x in args.rates.split(",")]
+    n = args.requests
+    pool = _request_pool(synth, min(n, 48))
+    rng = np.random.default_rng(606)
+    steps = np.floor(np.exp(rng.uniform(np.log(10), np.log(1e4), size=n))).astype(int)
+    seeds = rng.integers(1, 2**62, size=n)
+    per_rate = []
+    for lam in rates:
+        with ThreadPoolExecutor(_threads()) as ex:
+            gs = list(ex.map(lambda i: libsnp.System(pool[i % len(pool)], select=libsnp.SNP_SELECT_PHILOX,
+                                                     seed=int(seeds[i]), deferred=True), range(n)))
+        b = libsnp.Batch(mem_budget=150 << 30)
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=n))
+        tickets = [None] * n
+        start = time.perf_counter()
+
+        def submitter():
+            for i in range(n):
+                dt = start + arr[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[i] = b.submit([gs[i]], [int(steps[i])])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, work, left = [0.0] * n, 0, set(range(n))
+        last = start
+        while left:
+            for i in list(left):
+                if tickets[i] is not None and b.poll(tickets[i]):
+                    now = time.perf_counter()
+                    lat[i] = now - (start + arr[i])
+                    done = b.steps_done(tickets[i], 0)
+                    work += pool[i % len(pool)].num_syn * done
+                    gs[i].close()
+                    left.discard(i)
+                    last = now
+            time.sleep(0.0005)
+        th.join()
+        info = b.info()
+        b.close()
+        wall = last - start
+        per_rate.append({"rate_per_s": lam, "requests": n, "p50_latency_s": float(np.percentile(lat, 50)),
+                         "p99_latency_s": float(np.percentile(lat, 99)), "syn_updates_per_s": work / wall,
+                         "wall_s": wall, "rounds": int(info.rounds),
+                         "peak_device_gb": info.peak_resident_bytes / 1e9})
+    best = max(r["syn_updates_per_s"] for r in per_rate)
+    return {"metric": "synaptic updates/s", "workload": "serve", "value": best, "unit": "synaptic updates/s",
+            "per_rate": per_rate,
+            "config": {"q": "log-uniform 1e3..1e6 (48 distinct systems reused)", "steps": "log-uniform 10..1e4",
+                       "budget_gb": 150, "requests_per_rate": n}}
+
+
+def skewed(args, libsnp, synth):
+    import torch
+    d, nsteps, mode = synth.skewed_2m()
+    res = {}
+    for name, kw in [("tiled", dict(engine=libsnp.SNP_ENGINE_TILED)),
+                     ("l2_gather", dict(engine=libsnp.SNP_ENGINE_LAUNCH)),
+                     ("push", dict(prop=libsnp.SNP_PROP_PUSH)),
+                     ("ell_pull", dict(form=libsnp.SNP_FORM_ELL)),
+                     ("ell_push", dict(form=libsnp.SNP_FORM_ELL, prop=libsnp.SNP_PROP_PUSH))]:
+        try:
+            g = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=d.seed, **kw)
+        except libsnp.SnpError as e:
+            res[name] = {"unavailable": str(e)}
+            continue
+        g.step(8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = g.step(nsteps)
+        dt = time.perf_counter() - t0
+        res[name] = {"syn_updates_per_s": d.num_syn * done / dt, "us_per_step": dt / max(done, 1) * 1e6,
+                     "device_mb": g.info().device_bytes / 1e6}
+        g.close()
+    dd, _, _ = synth.skewed_dense_copy()
+    g = libsnp.System(dd, form=libsnp.SNP_FORM_DENSE, select=libsnp.SNP_SELECT_PHILOX, seed=dd.seed)
+    g.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done = g.step(10)
+    dt = time.perf_counter() - t0
+    dense_bytes = dd.m * dd.q * 4
+    res["dense_16k"] = {"us_per_step": dt / max(done, 1) * 1e6, "matrix_gb": dense_bytes / 1e9,
+                        "matrix_gbs": dense_bytes * done / dt / 1e9}
+    g.close()
+    gt = libsnp.System(dd, engine=libsnp.SNP_ENGINE_TILED, select=libsnp.SNP_SELECT_PHILOX, seed=dd.seed)
+    gt.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done = gt.step(10)
+    res["tiled_16k_us_per_step"] = (time.perf_counter() - t0) / max(done, 1) * 1e6
+    gt.close()
+    return {"metric": "synaptic updates/s", "workload": "skewed", "value": res["tiled"].get("syn_updates_per_s"),
+            "unit": "synaptic updates/s", "engines": res,
+            "config": {"q": d.q, "num_syn": d.num_syn, "steps": nsteps, "dense_copy_q": dd.q, "dense_copy_m": dd.m}}

@@ -107,8 +107,13 @@ typedef struct snp_options {
     void* stream;     /* cudaStream_t; NULL = legacy default stream   */
     const snp_allocator* alloc; /* NULL = cudaMalloc/cudaFree         */
     int32_t threads;  /* CTA size hint for the kernels; 0 = default   */
-    int32_t reserved;
+    int32_t flags;    /* SNP_FLAG_* bits                              */
 } snp_options;
+
+/* snp_create packs the system on the host but allocates and uploads nothing
+ * until the system is first stepped, read, or admitted by a batch (which
+ * then counts its memory against the batch budget).                       */
+#define SNP_FLAG_DEFER_UPLOAD 1
 
 /* A system Pi = (O, syn, sigma_1..sigma_q, i_out) (Sec. 2) as the user
  * defines it (Sec. 5, "Initialization").  All arrays are HOST memory.
@@ -221,6 +226,19 @@ int snp_batch_poll(snp_batch* b, int64_t ticket, int* done);
 int snp_batch_wait(snp_batch* b, int64_t ticket);
 /* Executed steps of system `index` of a completed ticket.                 */
 int snp_batch_steps_done(snp_batch* b, int64_t ticket, int32_t index, int64_t* steps_done);
+/* Counters of a batch: device bytes of the systems it holds now and at most
+ * so far, rounds run, systems admitted / finished / waiting / running.    */
+typedef struct snp_batch_info {
+    uint64_t budget_bytes;
+    uint64_t resident_bytes;
+    uint64_t peak_resident_bytes;
+    int64_t rounds;
+    int64_t admitted;
+    int64_t finished;
+    int64_t waiting;
+    int64_t running;
+} snp_batch_info;
+int snp_batch_get_info(snp_batch* b, snp_batch_info* info);
 
 /* ---- paper formats, host only (inspection and memory accounting) -------- */
 /* The paper's matrices for a system, written densely on the host:

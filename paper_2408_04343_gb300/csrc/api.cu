@@ -47,23 +47,124 @@ static void sys_free_all(snp_system* s) {
     s->device_bytes = 0;
 }
 
-template <typename T>
-static T* upload(snp_system* s, const std::vector<T>& v, int* err) {
-    T* p = (T*)sys_alloc(s, v.size() * sizeof(T));
-    if (!p) {
-        *err = fail(SNP_ERR_OOM, "device allocation failed");
-        return nullptr;
-    }
-    if (!v.empty() && cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
-        *err = fail(SNP_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(cudaGetLastError()));
-        return nullptr;
-    }
-    return p;
-}
-
 static int cuda_fail(const char* what) {
     cudaError_t e = cudaGetLastError();
     return fail(SNP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---- one allocation per system ---------------------------------------------
+// Every device buffer of a system is carved from one allocation: the host
+// image is turned into a list of pieces (destination pointer field, source or
+// fill byte, size), the sizes are summed at 256-byte alignment, one block is
+// allocated, and each piece is copied or filled into its place.
+
+size_t plan_bytes(const std::vector<Piece>& plan) {
+    size_t t = 0;
+    for (const Piece& p : plan) t += (p.bytes + 255) & ~(size_t)255;
+    return t;
+}
+
+void build_plan(snp_system* s, std::vector<Piece>& plan) {
+    HostImage& im = *s->img;
+    HostPack& hp = im.hp;
+    DevSys& d = s->dev;
+    const size_t q = (size_t)hp.q;
+    const int32_t nslices = (hp.q + kSlice - 1) / kSlice;
+    auto vec = [&](void* field, const auto& v) {
+        plan.push_back({reinterpret_cast<void**>(field), v.data(), v.size() * sizeof(v[0]), -1});
+    };
+    auto fill = [&](void* field, size_t bytes, int byte) {
+        plan.push_back({reinterpret_cast<void**>(field), nullptr, bytes, byte});
+    };
+    d.q = hp.q;
+    d.nslices = nslices;
+    vec(&d.slice_ptr, hp.slice_ptr);
+    if (s->has_in_lists) vec(&d.in_idx, hp.in_idx);
+    if (s->opt.form == SNP_FORM_OPT && s->opt.prop == SNP_PROP_PUSH) {
+        vec(&d.out_ptr, hp.out_ptr);
+        vec(&d.out_idx, hp.out_idx);
+    }
+    vec(&d.rule_off, hp.rule_off);
+    vec(&d.rules, hp.rules);
+    vec(&d.orig, hp.perm);
+    vec(&s->d_rule_base, hp.rule_base);
+    vec(&d.C, hp.C0);
+    fill(&d.st, q * 4, 0);
+    for (int b = 0; b < 2; ++b) {
+        if (s->opt.form == SNP_FORM_OPT) fill(&d.E[b], (q + 1) * 4, 0);
+        fill(&d.S[b], q * 4, 0xff);  // -1: no rule selected yet
+    }
+    fill(&d.flags, kNumFlags * 4, 0);
+    fill(&d.step, kNumStepWords * 8, 0);
+    fill(&s->scratch, q * 4, 0);
+    fill(&s->d_nsteps, 8, 0);
+    fill(&s->d_work, 4, 0);
+    fill(&s->d_self, sizeof(DevSys), 0);
+    if (s->opt.form != SNP_FORM_OPT) {
+        EllSys& e = s->ell;
+        e.m = hp.m;
+        if (!im.ep.in_ptr.empty()) {
+            vec(&e.in_ptr, im.ep.in_ptr);
+            vec(&e.in_ent, im.ep.in_ent);
+        }
+        if (!im.ep.out_ptr.empty()) {
+            vec(&e.out_ptr, im.ep.out_ptr);
+            vec(&e.out_ent, im.ep.out_ent);
+        }
+        if (s->opt.form == SNP_FORM_DENSE) {
+            vec(&e.dense, im.dense);
+            fill(&e.inflow, q * 4, 0);
+        }
+        for (int b = 0; b < 2; ++b) fill(&e.Em[b], (size_t)hp.m + 1, 0);
+    }
+    if (s->has_tiled) {
+        TiledSys& tl = s->tiled;
+        const TiledPack& tp = im.tp;
+        tl.P = tp.P;
+        tl.part_words = tp.part_words;
+        tl.e_bits = tp.e_bits;
+        tl.G = tp.G;
+        tl.acc_words = tp.acc_words;
+        tl.src_bits = tp.src_bits;
+        vec(&tl.grp, tp.grp);
+        vec(&tl.ent, tp.ent);
+        vec(&tl.cta_lo, tp.cta_lo);
+        fill(&tl.inflow, (size_t)nslices * kSlice * 4, 0);
+        for (int b = 0; b < 2; ++b) fill(&tl.Eg[b], (size_t)tp.P * tp.part_words * 4, 0);
+    }
+}
+
+int materialize(snp_system* s) {
+    if (s->materialized) return SNP_OK;
+    if (!s->img) return fail(SNP_ERR_INVALID, "system has no host image");
+    std::vector<Piece> plan;
+    build_plan(s, plan);
+    const size_t total = plan_bytes(plan);
+    char* base = (char*)sys_alloc(s, total);
+    if (!base) return fail(SNP_ERR_OOM, "device allocation of " + std::to_string(total) + " bytes failed");
+    size_t off = 0;
+    for (const Piece& p : plan) {
+        *p.dst = base + off;
+        cudaError_t e = cudaSuccess;
+        if (p.src && p.bytes)
+            e = cudaMemcpyAsync(base + off, p.src, p.bytes, cudaMemcpyHostToDevice, s->stream);
+        else if (p.fill >= 0 && p.bytes)
+            e = cudaMemsetAsync(base + off, p.fill, p.bytes, s->stream);
+        if (e != cudaSuccess) return cuda_fail("upload");
+        off += (p.bytes + 255) & ~(size_t)255;
+    }
+    DevSys& d = s->dev;
+    d.rules_per_neuron = s->uniform_rules;
+    d.identity = s->identity ? 1 : 0;
+    d.seed = s->opt.seed;
+    d.select = s->opt.select;
+    d.max_p = s->max_p;
+    if (cudaMemcpyAsync(s->d_self, &d, sizeof(DevSys), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        return cuda_fail("descriptor upload");
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return cuda_fail("upload sync");
+    s->img.reset();
+    s->materialized = true;
+    return SNP_OK;
 }
 
 bool is_device_ptr(const void* p) {
@@ -304,23 +405,24 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     s->opt = o;
     s->stream = (cudaStream_t)o.stream;
     if (o.alloc) s->alloc = *o.alloc;
+    s->img.reset(new (std::nothrow) HostImage());
+    if (!s->img) {
+        delete s;
+        return fail(SNP_ERR_OOM, "host allocation failed");
+    }
+    HostImage& im = *s->img;
+    HostPack& hp = im.hp;
     bool want_tiled = false, want_in = false;
     plan_layouts(o, desc->q, &want_tiled, &want_in);
-    HostPack hp;
-    st = pack_system(desc, o.form == SNP_FORM_OPT && o.prop == SNP_PROP_PUSH, false, kSortWindow, &hp);
+    // the tiled layout needs no in-degree order; without it slots are the caller's neurons
+    const int window = (o.form == SNP_FORM_OPT && o.engine == SNP_ENGINE_TILED) ? 0 : kSortWindow;
+    st = pack_system(desc, o.form == SNP_FORM_OPT && o.prop == SNP_PROP_PUSH, false, window, &hp);
+    if (!st && o.form == SNP_FORM_ELL) st = pack_ell(desc, hp, o.prop == SNP_PROP_PULL, o.prop == SNP_PROP_PUSH, &im.ep);
+    if (!st && o.form == SNP_FORM_DENSE) st = pack_dense(desc, hp, &im.dense);
     if (st) {
         delete s;
         return st;
     }
-    EllPack ep;
-    std::vector<int32_t> dense;
-    if (o.form == SNP_FORM_ELL) st = pack_ell(desc, hp, o.prop == SNP_PROP_PULL, o.prop == SNP_PROP_PUSH, &ep);
-    if (o.form == SNP_FORM_DENSE) st = pack_dense(desc, hp, &dense);
-    if (st) {
-        delete s;
-        return st;
-    }
-    TiledPack tp;
     if (want_tiled) {
         int dev = 0, sms = 0, optin = 0;
         cudaGetDevice(&dev);
@@ -329,15 +431,12 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
             delete s;
             return cuda_fail("device query");
         }
-        st = pack_tiled(desc, hp, sms, (size_t)optin - 2048, &tp);
+        st = pack_tiled(desc, hp, sms, (size_t)optin - 2048, &im.tp);
         if (st == SNP_OK) {
             s->has_tiled = true;
             // the resident engine (batches) still needs in-lists when the system fits one CTA
-            if (o.engine == SNP_ENGINE_AUTO && resident_smem_bytes(hp.q, resident_e_bits(hp.max_p)) + 1024 <=
-                                                   (size_t)optin)
-                want_in = true;
-            else if (o.engine == SNP_ENGINE_AUTO)
-                want_in = false;
+            if (o.engine == SNP_ENGINE_AUTO)
+                want_in = resident_smem_bytes(hp.q, resident_e_bits(hp.max_p)) + 1024 <= (size_t)optin;
         } else if (o.engine == SNP_ENGINE_TILED) {
             delete s;
             return st;
@@ -352,109 +451,36 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     s->nsyn = hp.nsyn;
     s->max_p = hp.max_p;
     s->max_rules = hp.max_rules;
+    s->uniform_rules = hp.uniform_rules;
+    s->identity = hp.identity;
     s->compact = hp.compact;
     s->in_entries = (int64_t)hp.in_idx.size();
     s->out_entries = (int64_t)hp.out_idx.size();
+    if (o.form == SNP_FORM_ELL) {
+        s->in_entries = (int64_t)im.ep.in_ent.size() / 2;
+        s->out_entries = (int64_t)im.ep.out_ent.size() / 2;
+    }
+    if (o.form == SNP_FORM_DENSE) s->in_entries = (int64_t)im.dense.size();
     s->rule_words = (int64_t)hp.rules.size();
     s->perm = hp.perm;
     s->rule_offsets.assign(desc->rule_offsets, desc->rule_offsets + (size_t)desc->q + 1);
-
-    int err = SNP_OK;
-    DevSys& d = s->dev;
-    d.q = hp.q;
-    d.nslices = (hp.q + kSlice - 1) / kSlice;
-    d.slice_ptr = upload(s, hp.slice_ptr, &err);
-    if (!err && want_in) d.in_idx = upload(s, hp.in_idx, &err);
-    if (!err && o.form != SNP_FORM_OPT) {
-        EllSys& e = s->ell;
-        e.m = hp.m;
-        if (!ep.in_ptr.empty()) {
-            e.in_ptr = upload(s, ep.in_ptr, &err);
-            if (!err) e.in_ent = reinterpret_cast<const int2*>(upload(s, ep.in_ent, &err));
-            s->in_entries = (int64_t)ep.in_ent.size() / 2;
-        }
-        if (!err && !ep.out_ptr.empty()) {
-            e.out_ptr = upload(s, ep.out_ptr, &err);
-            if (!err) e.out_ent = reinterpret_cast<const int2*>(upload(s, ep.out_ent, &err));
-            s->out_entries = (int64_t)ep.out_ent.size() / 2;
-        }
-        if (!err && o.form == SNP_FORM_DENSE) {
-            e.dense = upload(s, dense, &err);
-            std::vector<int32_t> z((size_t)hp.q, 0);
-            if (!err) e.inflow = upload(s, z, &err);
-            s->in_entries = (int64_t)dense.size();
-        }
-        std::vector<uint8_t> em((size_t)hp.m + 1, 0);
-        for (int b = 0; b < 2 && !err; ++b) e.Em[b] = upload(s, em, &err);
-    }
-    if (!err && s->has_tiled) {
-        TiledSys& tl = s->tiled;
-        tl.P = tp.P;
-        tl.part_words = tp.part_words;
-        tl.e_bits = tp.e_bits;
-        tl.G = tp.G;
-        tl.acc_words = tp.acc_words;
-        tl.src_bits = tp.src_bits;
-        tl.grp = upload(s, tp.grp, &err);
-        if (!err) tl.ent = upload(s, tp.ent, &err);
-        if (!err) {
-            std::vector<int32_t> z((size_t)d.nslices * kSlice, 0);
-            tl.inflow = upload(s, z, &err);
-        }
-        if (!err) tl.cta_lo = upload(s, tp.cta_lo, &err);
-        for (int b = 0; b < 2 && !err; ++b) {
-            std::vector<uint32_t> z((size_t)tp.P * tp.part_words, 0u);
-            tl.Eg[b] = upload(s, z, &err);
-        }
-        s->tiled_smem = tiled_smem_bytes(tp);
-        s->tiled_entries = (int64_t)tp.ent.size();
+    if (s->has_tiled) {
+        s->tiled_smem = tiled_smem_bytes(im.tp);
+        s->tiled_entries = (int64_t)im.tp.ent.size();
         s->tiled_threads = o.threads > 0 ? o.threads : 1024;
     }
-    if (!err && o.prop == SNP_PROP_PUSH) {
-        d.out_ptr = upload(s, hp.out_ptr, &err);
-        if (!err) d.out_idx = upload(s, hp.out_idx, &err);
+    {
+        std::vector<Piece> plan;
+        build_plan(s, plan);
+        s->planned_bytes = plan_bytes(plan);
     }
-    if (!err) d.rule_off = upload(s, hp.rule_off, &err);
-    if (!err) d.rules = upload(s, hp.rules, &err);
-    if (!err) d.orig = upload(s, hp.perm, &err);
-    if (!err) s->d_rule_base = upload(s, hp.rule_base, &err);
-    if (!err) d.C = upload(s, hp.C0, &err);
-    if (!err) {
-        std::vector<uint32_t> zeros((size_t)hp.q, 0u);
-        d.st = upload(s, zeros, &err);
-    }
-    if (!err) {
-        std::vector<int32_t> ez((size_t)hp.q + 1, 0), sm((size_t)hp.q, -1);
-        for (int b = 0; b < 2 && !err; ++b) {
-            d.E[b] = upload(s, ez, &err);
-            if (!err) d.S[b] = upload(s, sm, &err);
+    if (!(o.flags & SNP_FLAG_DEFER_UPLOAD)) {
+        st = materialize(s);
+        if (st) {
+            sys_free_all(s);
+            delete s;
+            return st;
         }
-    }
-    if (!err) {
-        std::vector<uint32_t> fz(kNumFlags, 0u);
-        d.flags = upload(s, fz, &err);
-    }
-    if (!err) {
-        std::vector<unsigned long long> sz(kNumStepWords, 0ull);
-        d.step = upload(s, sz, &err);
-    }
-    if (!err) {
-        s->scratch = (int32_t*)sys_alloc(s, sizeof(int32_t) * (size_t)hp.q);
-        s->d_nsteps = (long long*)sys_alloc(s, sizeof(long long));
-        s->d_work = (unsigned int*)sys_alloc(s, sizeof(unsigned int));
-        s->d_self = (DevSys*)sys_alloc(s, sizeof(DevSys));
-        if (!s->scratch || !s->d_nsteps || !s->d_work || !s->d_self) err = fail(SNP_ERR_OOM, "device allocation failed");
-    }
-    d.seed = o.seed;
-    d.select = o.select;
-    d.max_p = hp.max_p;
-    if (!err && cudaMemcpyAsync(s->d_self, &d, sizeof(DevSys), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
-        err = cuda_fail("descriptor upload");
-    if (!err && cudaStreamSynchronize(s->stream) != cudaSuccess) err = cuda_fail("create sync");
-    if (err) {
-        sys_free_all(s);
-        delete s;
-        return err;
     }
     *out = s;
     return SNP_OK;
@@ -467,7 +493,9 @@ int snp_destroy(snp_system* s) {
     else cudaDeviceSynchronize();
     if (s->chunk_exec) cudaGraphExecDestroy(s->chunk_exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    batch_release(s);
     sys_free_all(s);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
     return SNP_OK;
 }
@@ -475,6 +503,7 @@ int snp_destroy(snp_system* s) {
 int snp_step(snp_system* s, int64_t n, int64_t* steps_done) {
     if (!s) return fail(SNP_ERR_INVALID, "system is NULL");
     if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
+    if (int rc_ = materialize(s)) return rc_;
     if (n < 0) return fail(SNP_ERR_INVALID, "n < 0");
     if (steps_done) *steps_done = 0;
     if (n == 0) return SNP_OK;
@@ -488,6 +517,7 @@ static int export_vec(const snp_system* sc, int what, int32_t* out, int64_t len)
     snp_system* s = const_cast<snp_system*>(sc);
     if (!s || !out) return fail(SNP_ERR_INVALID, "NULL argument");
     if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
+    if (int rc_ = materialize(s)) return rc_;
     if (len < s->q) return fail(SNP_ERR_INVALID, "output shorter than q");
     const bool dev = is_device_ptr(out);
     int32_t* dst = dev ? out : s->scratch;
@@ -507,6 +537,7 @@ int snp_get_pending(const snp_system* s, int32_t* out, int64_t len) { return exp
 
 int snp_get_state(const snp_system* s, int32_t* C, int32_t* D, int32_t* P, int64_t len, uint64_t* step) {
     if (!s) return fail(SNP_ERR_INVALID, "system is NULL");
+    if (int rc_ = materialize(const_cast<snp_system*>(s))) return rc_;
     int rc;
     if (C && (rc = snp_get_config(s, C, len))) return rc;
     if (D && (rc = snp_get_status(s, D, len))) return rc;
@@ -536,6 +567,7 @@ static int fetch_host(const int32_t* src, int64_t q, std::vector<int32_t>& dst, 
 int snp_set_state(snp_system* s, const int32_t* C, const int32_t* D, const int32_t* P, int64_t len, uint64_t step) {
     if (!s || !C || !D || !P) return fail(SNP_ERR_INVALID, "NULL argument");
     if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
+    if (int rc_ = materialize(s)) return rc_;
     if (len < s->q) return fail(SNP_ERR_INVALID, "state shorter than q");
     std::vector<int32_t> hc, hd, hpv;
     int rc;
@@ -586,7 +618,7 @@ int snp_get_info(const snp_system* s, snp_info* info) {
     info->in_entries = info->engine == SNP_ENGINE_TILED ? s->tiled_entries : s->in_entries;
     info->out_entries = s->out_entries;
     info->rule_words = s->rule_words;
-    info->device_bytes = (int64_t)s->device_bytes;
+    info->device_bytes = (int64_t)(s->materialized ? s->device_bytes : s->planned_bytes);
     info->max_rules = s->max_rules;
     info->max_p = s->max_p;
     info->compact_rules = s->compact ? 1 : 0;

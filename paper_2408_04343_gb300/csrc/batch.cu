@@ -1,20 +1,34 @@
-// Batched form: many independent systems advanced by one persistent launch.
+// Batched and served forms: many independent systems advanced together.
 //
-// Submitted tickets are executed by a worker thread in arrival order.  The
-// systems of a ticket that fit the CTA-resident engine are sorted largest
-// first and handed to one persistent launch (grid = SMs x resident CTAs per
-// SM); each CTA takes the next system from a device work counter and runs all
-// its steps, so thousands of systems of uneven size share one launch with
-// per-system offsets (the DevSys table).  Systems too large for one CTA run on
-// the grid-wide engine on their own streams, overlapping with the launch.
+// A batch owns a worker thread that runs continuous batching in rounds:
+//  1. admission -- queued systems are admitted first come first served while
+//     the device memory of the systems the batch holds stays within the
+//     budget; a system created with SNP_FLAG_DEFER_UPLOAD is uploaded only
+//     here, so requests wait on the host until memory frees up (a destroyed
+//     system returns its memory to the batch);
+//  2. one round -- every admitted system advances by up to `round` steps.
+//     Systems small enough for one CTA (the CTA-resident engine, emissions in
+//     shared memory) share ONE persistent launch: each CTA takes the next
+//     system, largest first, from a device work counter and runs all of that
+//     system's steps of the round, with per-system offsets in a table of
+//     system descriptors.  Larger systems run on the grid-wide engines on
+//     their own streams at the same time, so their work overlaps;
+//  3. retirement -- systems that used up their steps or reached a fixed
+//     point leave; a ticket completes when all its systems have.
+// Requests that arrive while a round runs join at the next round, so the
+// device stays busy and new work does not wait for old work to drain.
+// Results depend only on each system's seed and state, never on what it
+// shared a round with (the Philox key is per system).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -25,15 +39,24 @@
 
 namespace snp {
 
+struct Item {
+    int64_t ticket = 0;
+    snp_system* sys = nullptr;
+    int64_t remaining = 0;
+    int64_t done = 0;
+    bool finished = false;
+};
+
 struct Ticket {
-    int64_t id = 0;
-    std::vector<snp_system*> sys;
-    std::vector<int64_t> steps;
-    std::vector<int64_t> done_steps;
-    int state = 0;  // 0 queued, 1 running, 2 done
+    std::vector<std::unique_ptr<Item>> items;
+    int64_t outstanding = 0;
     int status = SNP_OK;
     std::string error;
+    bool complete() const { return outstanding == 0; }
 };
+
+constexpr int64_t kRoundSteps = 64;          // steps per round and system
+constexpr int kBatchResidentMaxQ = 65536;    // larger systems run grid-wide
 
 }  // namespace snp
 
@@ -44,19 +67,25 @@ struct snp_batch {
     bool own_stream = false;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<int64_t> queue;
+    std::deque<snp::Item*> pending;
+    std::vector<snp::Item*> active;
     std::map<int64_t, snp::Ticket> tickets;
+    std::set<snp_system*> owned;   // systems this batch uploaded (memory accounting)
+    size_t resident_bytes = 0;
+    size_t peak_bytes = 0;
+    int64_t rounds = 0, admitted = 0, finished = 0;
     int64_t next_id = 1;
     bool stop = false;
     std::thread worker;
-    // device tables, grown on demand
+    // device tables of the resident launch, grown on demand
     snp::DevSys* d_sys = nullptr;
     long long* d_nsteps = nullptr;
-    unsigned long long* d_exec = nullptr;  // 3 words per system
+    unsigned long long* d_res = nullptr;  // 3 words per system
     unsigned int* d_work = nullptr;
     size_t cap = 0;
     int sms = 0;
-    int threads = 0;   // resident CTA size; 0 = autotune
+    int threads = 0;
+    int64_t round = snp::kRoundSteps;
 };
 
 namespace snp {
@@ -66,13 +95,13 @@ static int grow_tables(snp_batch* b, size_t n) {
     size_t cap = std::max<size_t>(n, 2 * b->cap);
     cudaFree(b->d_sys);
     cudaFree(b->d_nsteps);
-    cudaFree(b->d_exec);
+    cudaFree(b->d_res);
     b->d_sys = nullptr;
     b->d_nsteps = nullptr;
-    b->d_exec = nullptr;
+    b->d_res = nullptr;
     if (cudaMalloc(&b->d_sys, cap * sizeof(DevSys)) != cudaSuccess ||
         cudaMalloc(&b->d_nsteps, cap * sizeof(long long)) != cudaSuccess ||
-        cudaMalloc(&b->d_exec, cap * 3 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&b->d_res, cap * 3 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         b->cap = 0;
         return fail(SNP_ERR_OOM, "batch table allocation failed");
@@ -82,29 +111,30 @@ static int grow_tables(snp_batch* b, size_t n) {
 }
 
 // CTAs of `threads` threads and `smem` bytes that fit on one SM.
-static int ctas_per_sm(int threads, size_t smem, int e_bits, bool compact, int sel) {
-    (void)e_bits;
-    (void)compact;
-    (void)sel;
+static int ctas_per_sm(int threads, size_t smem) {
     int dev = 0, smem_sm = 0, thr_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
-    int by_thr = thr_sm / threads;
-    int by_smem = (int)((size_t)smem_sm / (smem + 1024));
+    const int by_thr = thr_sm / threads;
+    const int by_smem = (int)((size_t)smem_sm / (smem + 1024));
     return std::max(1, std::min(by_thr, by_smem));
 }
 
-int run_resident_group(snp_batch* b, std::vector<snp_system*>& sys, std::vector<int64_t>& steps,
-                       std::vector<int64_t>& exec_out) {
+// One persistent launch over systems that share kernel template parameters;
+// steps[i] each; exec_out receives the executed steps.
+static int run_resident_group(snp_batch* b, std::vector<snp_system*>& sys, std::vector<int64_t>& steps,
+                              std::vector<int64_t>& exec_out) {
     const size_t n = sys.size();
+    exec_out.assign(n, 0);
     if (n == 0) return SNP_OK;
     int rc = grow_tables(b, n);
     if (rc) return rc;
     std::vector<size_t> order(n);
     for (size_t i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](size_t a, size_t c) { return (double)sys[a]->nsyn * steps[a] > (double)sys[c]->nsyn * steps[c]; });
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) {
+        return (double)(sys[a]->nsyn + sys[a]->q) * steps[a] > (double)(sys[c]->nsyn + sys[c]->q) * steps[c];
+    });
     std::vector<DevSys> tab(n);
     std::vector<long long> ns(n);
     int max_q = 0, max_p = 0;
@@ -121,20 +151,19 @@ int run_resident_group(snp_batch* b, std::vector<snp_system*>& sys, std::vector<
     plan.threads = b->threads > 0 ? b->threads : 512;
     const bool compact = sys[0]->compact;
     const int sel = sys[0]->opt.select;
-    plan.ctas = b->sms * ctas_per_sm(plan.threads, plan.smem, plan.e_bits, compact, sel);
+    plan.ctas = b->sms * ctas_per_sm(plan.threads, plan.smem);
     if (cudaMemcpyAsync(b->d_sys, tab.data(), n * sizeof(DevSys), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
         cudaMemcpyAsync(b->d_nsteps, ns.data(), n * sizeof(long long), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
         cudaMemsetAsync(b->d_work, 0, sizeof(unsigned int), b->stream) != cudaSuccess)
         return fail(SNP_ERR_CUDA, "batch table upload");
     if (launch_resident(b->d_sys, b->d_nsteps, (int)n, b->d_work, plan, compact, sel, b->stream) != cudaSuccess)
         return fail(SNP_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(cudaGetLastError()));
-    // executed step counts and overflow flags of every system, in one copy
     std::vector<unsigned long long> ex(n * 3);
-    if (launch_gather_results(b->d_sys, (int)n, b->d_exec, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(ex.data(), b->d_exec, n * 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+    if (launch_gather_results(b->d_sys, (int)n, b->d_res, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(ex.data(), b->d_res, n * 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream) !=
+            cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return fail(SNP_ERR_CUDA, std::string("batch sync: ") + cudaGetErrorString(cudaGetLastError()));
-    exec_out.assign(n, 0);
     bool overflow = false;
     for (size_t r = 0; r < n; ++r) {
         exec_out[order[r]] = (int64_t)ex[3 * r + 1];
@@ -145,73 +174,146 @@ int run_resident_group(snp_batch* b, std::vector<snp_system*>& sys, std::vector<
     return SNP_OK;
 }
 
-static void execute_ticket(snp_batch* b, Ticket& t) {
-    const size_t n = t.sys.size();
-    t.done_steps.assign(n, 0);
-    // group by kernel template: (compact, select); large systems go grid-wide
-    std::map<std::pair<int, int>, std::vector<size_t>> groups;
-    std::vector<size_t> large;
-    for (size_t i = 0; i < n; ++i) {
-        snp_system* s = t.sys[i];
-        if (s->opt.prop == SNP_PROP_PULL && s->opt.engine != SNP_ENGINE_LAUNCH && resident_fits(s, nullptr))
-            groups[{s->compact ? 1 : 0, s->opt.select}].push_back(i);
+static bool batch_resident(const snp_system* s) {
+    return s->opt.form == SNP_FORM_OPT && s->opt.prop == SNP_PROP_PULL && s->opt.engine != SNP_ENGINE_LAUNCH &&
+           s->opt.engine != SNP_ENGINE_TILED && s->q <= kBatchResidentMaxQ && resident_fits(s, nullptr);
+}
+
+// Runs one round over `items`; on return each item's done/remaining/finished is updated.
+static int run_round(snp_batch* b, std::vector<Item*>& items) {
+    std::map<std::pair<int, int>, std::vector<Item*>> groups;
+    std::vector<Item*> large;
+    for (Item* it : items) {
+        if (batch_resident(it->sys))
+            groups[{it->sys->compact ? 1 : 0, it->sys->opt.select}].push_back(it);
         else
-            large.push_back(i);
+            large.push_back(it);
     }
     int rc = SNP_OK;
-    for (size_t i : large) {
-        rc = run_steps(t.sys[i], t.steps[i]);
-        if (rc) break;
+    // grid-wide systems first (asynchronous on their own streams)
+    std::vector<int64_t> large_n(large.size());
+    for (size_t i = 0; i < large.size() && !rc; ++i) {
+        large_n[i] = std::min(large[i]->remaining, b->round);
+        rc = run_steps(large[i]->sys, large_n[i]);
     }
     for (auto& g : groups) {
         if (rc) break;
         std::vector<snp_system*> sys;
         std::vector<int64_t> steps, ex;
-        for (size_t i : g.second) {
-            sys.push_back(t.sys[i]);
-            steps.push_back(t.steps[i]);
+        for (Item* it : g.second) {
+            sys.push_back(it->sys);
+            steps.push_back(std::min(it->remaining, b->round));
         }
         rc = run_resident_group(b, sys, steps, ex);
-        if (!rc)
-            for (size_t r = 0; r < g.second.size(); ++r) t.done_steps[g.second[r]] = ex[r];
+        if (!rc) {
+            for (size_t r = 0; r < g.second.size(); ++r) {
+                Item* it = g.second[r];
+                it->done += ex[r];
+                it->remaining -= steps[r];
+                if (ex[r] < steps[r] || it->remaining <= 0) it->finished = true;
+            }
+        }
     }
-    for (size_t i : large) {
-        if (rc) break;
+    for (size_t i = 0; i < large.size(); ++i) {
         int64_t ex = 0;
-        rc = read_flags(t.sys[i], &ex);
-        t.done_steps[i] = ex;
+        const int r2 = read_flags(large[i]->sys, &ex);
+        if (!rc) rc = r2;
+        large[i]->done += ex;
+        large[i]->remaining -= large_n[i];
+        if (ex < large_n[i] || large[i]->remaining <= 0) large[i]->finished = true;
     }
-    t.status = rc;
-    if (rc) t.error = last_error();
+    return rc;
+}
+
+static void finish_item(snp_batch* b, Item* it, int rc, const std::string& err) {
+    // b->mu held
+    Ticket& t = b->tickets[it->ticket];
+    it->finished = true;
+    if (rc && !t.status) {
+        t.status = rc;
+        t.error = err;
+    }
+    it->sys->busy.store(0);
+    t.outstanding -= 1;
+    b->finished += 1;
 }
 
 static void worker_main(snp_batch* b) {
+    std::unique_lock<std::mutex> lk(b->mu);
     for (;;) {
-        int64_t id;
-        {
-            std::unique_lock<std::mutex> lk(b->mu);
-            b->cv.wait(lk, [&] { return b->stop || !b->queue.empty(); });
-            if (b->queue.empty() && b->stop) return;
-            id = b->queue.front();
-            b->queue.pop_front();
-            b->tickets[id].state = 1;
+        b->cv.wait(lk, [&] { return b->stop || !b->pending.empty() || !b->active.empty(); });
+        if (b->stop && b->pending.empty() && b->active.empty()) return;
+        // admission, first come first served, within the memory budget
+        while (!b->pending.empty()) {
+            Item* it = b->pending.front();
+            snp_system* s = it->sys;
+            const size_t need = s->materialized ? 0 : s->planned_bytes;
+            if (b->budget && b->resident_bytes + need > b->budget && !(b->active.empty())) break;
+            b->pending.pop_front();
+            int rc = SNP_OK;
+            if (!s->stream) {
+                // a stream of its own lets grid-wide systems overlap; a blocking
+                // stream keeps the legacy default stream's ordering
+                cudaStream_t st = nullptr;
+                if (cudaStreamCreate(&st) == cudaSuccess) {
+                    s->stream = st;
+                    s->own_stream = true;
+                } else {
+                    cudaGetLastError();
+                }
+            }
+            if (!s->materialized) {
+                lk.unlock();
+                rc = materialize(s);
+                std::string err = rc ? last_error() : "";
+                lk.lock();
+                if (!rc) {
+                    b->resident_bytes += s->device_bytes;
+                    b->peak_bytes = std::max(b->peak_bytes, b->resident_bytes);
+                    b->owned.insert(s);
+                    s->owner = b;
+                } else {
+                    finish_item(b, it, rc, err);
+                    b->cv.notify_all();
+                    continue;
+                }
+            }
+            if (it->remaining <= 0) {
+                finish_item(b, it, SNP_OK, "");
+                b->cv.notify_all();
+                continue;
+            }
+            b->active.push_back(it);
+            b->admitted += 1;
         }
-        Ticket* t;
-        {
-            std::lock_guard<std::mutex> lk(b->mu);
-            t = &b->tickets[id];
+        if (b->active.empty()) continue;
+        b->rounds += 1;
+        std::vector<Item*> items = b->active;
+        lk.unlock();
+        const int rc = run_round(b, items);
+        const std::string err = rc ? last_error() : "";
+        lk.lock();
+        std::vector<Item*> still;
+        for (Item* it : b->active) {
+            if (rc || it->finished)
+                finish_item(b, it, rc, err);
+            else
+                still.push_back(it);
         }
-        execute_ticket(b, *t);
-        {
-            std::lock_guard<std::mutex> lk(b->mu);
-            for (snp_system* s : t->sys) s->busy.store(0);
-            t->state = 2;
-        }
+        b->active.swap(still);
         b->cv.notify_all();
     }
 }
 
-const char* last_error();
+// Called by snp_destroy: the system's memory returns to its batch's budget.
+void batch_release(snp_system* s) {
+    snp_batch* b = s->owner;
+    if (!b) return;
+    std::lock_guard<std::mutex> lk(b->mu);
+    if (b->owned.erase(s)) b->resident_bytes -= std::min(b->resident_bytes, s->device_bytes);
+    s->owner = nullptr;
+    b->cv.notify_all();
+}
 
 }  // namespace snp
 
@@ -259,9 +361,14 @@ int snp_batch_destroy(snp_batch* b) {
     b->cv.notify_all();
     if (b->worker.joinable()) b->worker.join();
     cudaStreamSynchronize(b->stream);
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        for (snp_system* s : b->owned) s->owner = nullptr;
+        b->owned.clear();
+    }
     cudaFree(b->d_sys);
     cudaFree(b->d_nsteps);
-    cudaFree(b->d_exec);
+    cudaFree(b->d_res);
     cudaFree(b->d_work);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -270,15 +377,14 @@ int snp_batch_destroy(snp_batch* b) {
 
 int snp_batch_submit(snp_batch* b, snp_system* const* sys, const int64_t* steps, int32_t count, int64_t* ticket) {
     if (!b || !sys || !steps || count < 0) return fail(SNP_ERR_INVALID, "bad batch arguments");
-    size_t bytes = 0;
     for (int32_t i = 0; i < count; ++i) {
         if (!sys[i]) return fail(SNP_ERR_INVALID, "NULL system in batch");
         if (steps[i] < 0) return fail(SNP_ERR_INVALID, "negative step count in batch");
-        bytes += sys[i]->device_bytes;
         for (int32_t j = 0; j < i; ++j)
             if (sys[j] == sys[i]) return fail(SNP_ERR_INVALID, "system listed twice in one ticket");
+        const size_t need = sys[i]->materialized ? sys[i]->device_bytes : sys[i]->planned_bytes;
+        if (b->budget && need > b->budget) return fail(SNP_ERR_OOM, "a system is larger than the batch memory budget");
     }
-    if (b->budget && bytes > b->budget) return fail(SNP_ERR_OOM, "ticket exceeds the batch memory budget");
     for (int32_t i = 0; i < count; ++i) {
         int expected = 0;
         if (!sys[i]->busy.compare_exchange_strong(expected, 1)) {
@@ -289,10 +395,15 @@ int snp_batch_submit(snp_batch* b, snp_system* const* sys, const int64_t* steps,
     std::lock_guard<std::mutex> lk(b->mu);
     const int64_t id = b->next_id++;
     Ticket& t = b->tickets[id];
-    t.id = id;
-    t.sys.assign(sys, sys + count);
-    t.steps.assign(steps, steps + count);
-    b->queue.push_back(id);
+    t.outstanding = count;
+    for (int32_t i = 0; i < count; ++i) {
+        t.items.emplace_back(new Item());
+        Item* it = t.items.back().get();
+        it->ticket = id;
+        it->sys = sys[i];
+        it->remaining = steps[i];
+        b->pending.push_back(it);
+    }
     if (ticket) *ticket = id;
     b->cv.notify_all();
     return SNP_OK;
@@ -303,7 +414,7 @@ int snp_batch_poll(snp_batch* b, int64_t ticket, int* done) {
     std::lock_guard<std::mutex> lk(b->mu);
     auto it = b->tickets.find(ticket);
     if (it == b->tickets.end()) return fail(SNP_ERR_INVALID, "unknown ticket");
-    *done = it->second.state == 2;
+    *done = it->second.complete();
     return SNP_OK;
 }
 
@@ -312,7 +423,7 @@ int snp_batch_wait(snp_batch* b, int64_t ticket) {
     std::unique_lock<std::mutex> lk(b->mu);
     auto it = b->tickets.find(ticket);
     if (it == b->tickets.end()) return fail(SNP_ERR_INVALID, "unknown ticket");
-    b->cv.wait(lk, [&] { return it->second.state == 2; });
+    b->cv.wait(lk, [&] { return it->second.complete(); });
     if (it->second.status) return fail(it->second.status, it->second.error);
     return SNP_OK;
 }
@@ -322,9 +433,23 @@ int snp_batch_steps_done(snp_batch* b, int64_t ticket, int32_t index, int64_t* s
     std::lock_guard<std::mutex> lk(b->mu);
     auto it = b->tickets.find(ticket);
     if (it == b->tickets.end()) return fail(SNP_ERR_INVALID, "unknown ticket");
-    if (it->second.state != 2) return fail(SNP_ERR_BUSY, "ticket not finished");
-    if (index < 0 || (size_t)index >= it->second.done_steps.size()) return fail(SNP_ERR_INVALID, "bad index");
-    *steps_done = it->second.done_steps[index];
+    if (!it->second.complete()) return fail(SNP_ERR_BUSY, "ticket not finished");
+    if (index < 0 || (size_t)index >= it->second.items.size()) return fail(SNP_ERR_INVALID, "bad index");
+    *steps_done = it->second.items[index]->done;
+    return SNP_OK;
+}
+
+int snp_batch_get_info(snp_batch* b, snp_batch_info* info) {
+    if (!b || !info) return fail(SNP_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(b->mu);
+    info->budget_bytes = b->budget;
+    info->resident_bytes = b->resident_bytes;
+    info->peak_resident_bytes = b->peak_bytes;
+    info->rounds = b->rounds;
+    info->admitted = b->admitted;
+    info->finished = b->finished;
+    info->waiting = (int64_t)b->pending.size();
+    info->running = (int64_t)b->active.size();
     return SNP_OK;
 }
 

@@ -6,6 +6,11 @@
 
 #include "snp_internal.h"
 
+// One of two buffers by step parity.  A ternary, not arr[k & 1]: indexing a
+// kernel-parameter array with a run-time value makes every thread copy the
+// parameter block into local memory.
+#define SNP_PICK(arr, k) ((((k) & 1ull) != 0ull) ? (arr)[1] : (arr)[0])
+
 namespace snp {
 
 // ---- Philox4x32-10 ------------------------------------------------------
@@ -69,13 +74,44 @@ __device__ __forceinline__ RuleF load_rule(const uint32_t* __restrict__ rules, i
     return f;
 }
 
+// Divisibility by a small j without a division: for 32-bit x and j >= 2,
+// j divides x exactly when x * c <= c - 1 modulo 2^64, c = floor((2^64-1)/j)
+// + 1 (Lemire, Kaser and Kurz, "Faster remainder by direct computation",
+// 2019).  The constants for j < 256 are built at compile time.
+struct DivMagic {
+    unsigned long long c[256];
+    constexpr DivMagic() : c() {
+        for (int j = 2; j < 256; ++j) c[j] = ~0ull / (unsigned long long)j + 1ull;
+    }
+};
+__constant__ DivMagic kDivMagic = DivMagic();
+
+__device__ __forceinline__ bool divides(uint32_t x, uint32_t j) {
+    if ((j & (j - 1u)) == 0u) return (x & (j - 1u)) == 0u;  // j a power of two (incl. 1)
+    if (j < 256u) {
+        const unsigned long long c = kDivMagic.c[j];
+        return (unsigned long long)x * c <= c - 1ull;
+    }
+    return x % j == 0u;
+}
+
 // The regular expression a^k (a^j)* matches n spikes, and n covers c
 // (Sec. 2 types 1-3 and the type-4 form of Sec. 7).
 __device__ __forceinline__ bool rule_applies(int32_t n, const RuleF& f) {
     if (n < f.k || n < f.c) return false;
     if (f.j == 0) return n == f.k;
-    if (f.j == 1) return true;
-    return ((uint32_t)(n - f.k) % (uint32_t)f.j) == 0u;
+    return divides((uint32_t)(n - f.k), (uint32_t)f.j);
+}
+
+// Rule range of a slot and the caller's id of a slot.
+__device__ __forceinline__ int32_t rule_lo(const DevSys& s, int32_t slot) {
+    return s.rules_per_neuron > 0 ? slot * s.rules_per_neuron : __ldg(s.rule_off + slot);
+}
+__device__ __forceinline__ int32_t rule_hi(const DevSys& s, int32_t slot) {
+    return s.rules_per_neuron > 0 ? (slot + 1) * s.rules_per_neuron : __ldg(s.rule_off + slot + 1);
+}
+__device__ __forceinline__ uint32_t neuron_id(const DevSys& s, int32_t slot) {
+    return s.identity ? (uint32_t)slot : (uint32_t)__ldg(s.orig + slot);
 }
 
 // Result of the select phase of one neuron for one step.
@@ -120,6 +156,22 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
                 break;
             }
         }
+    } else if (r1 - r0 <= 32) {
+        // one pass: bit i of `mask` = rule r0 + i applies; the draw picks
+        // the idx-th set bit
+        uint32_t mask = 0u;
+        for (int32_t r = r0; r < r1; ++r)
+            if (rule_applies(n, load_rule<COMPACT>(rules, r))) mask |= 1u << (r - r0);
+        const int32_t cnt = __popc(mask);
+        if (cnt == 1) {
+            pick = r0 + __ffs(mask) - 1;
+        } else if (cnt > 1) {
+            const Philox4 x = philox4x32_10((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
+                                            (uint32_t)(seed >> 32));
+            int32_t idx = (int32_t)(((unsigned long long)x.v[0] * (unsigned long long)cnt) >> 32);
+            for (; idx > 0; --idx) mask &= mask - 1u;  // drop the lowest set bits
+            pick = r0 + __ffs(mask) - 1;
+        }
     } else {
         int32_t cnt = 0, first = -1;
         for (int32_t r = r0; r < r1; ++r) {
@@ -161,6 +213,54 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
     return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// ---- fixed-point protocol of the per-step launches -----------------------
+// Word kFlagAct0 + (k mod 3) is raised by the launch that selects step k when
+// any neuron is pending or selected; the launch that finishes step k reads
+// it, and if it is clear the system is at a fixed point: the step does not
+// run and kFlagHalted stays set for the rest of the call.  The words are
+// read once per CTA by thread 0 through the non-coherent cache and shared
+// with the CTA: every warp reading them would queue tens of thousands of
+// requests on one L2 line.  The activity word of step k is never written by
+// the launch that reads it, and kFlagHalted is written in a launch only when
+// that launch's activity word is clear, so a stale read cannot change what a
+// CTA decides.
+
+// Block-uniform: true if the launch finishing step kg must return at once.
+__device__ __forceinline__ bool step_blocked(uint32_t* fl, unsigned long long* steps, unsigned long long kg) {
+    __shared__ int s_blocked;
+    if (threadIdx.x == 0) {
+        int b = __ldg(fl + kFlagHalted) != 0u;
+        if (!b && __ldg(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
+            b = 1;
+            if (blockIdx.x == 0 && blockIdx.y == 0) {
+                steps[kStepHalt] = kg;
+                __threadfence();
+                atomicExch(fl + kFlagHalted, 1u);
+            }
+        }
+        s_blocked = b;
+    }
+    __syncthreads();
+    return s_blocked != 0;
+}
+
+// Block-uniform: true if an earlier launch of this call found a fixed point.
+__device__ __forceinline__ bool call_halted(const uint32_t* fl) {
+    __shared__ int s_halted;
+    if (threadIdx.x == 0) s_halted = __ldg(fl + kFlagHalted) != 0u;
+    __syncthreads();
+    return s_halted != 0;
+}
+
+// End of a select launch: raise step ks's activity word if this CTA saw a
+// pending or selecting neuron (one store per CTA, skipped once raised).
+__device__ __forceinline__ void raise_step_activity(uint32_t* fl, unsigned long long ks, bool active) {
+    if (__syncthreads_or(active) && threadIdx.x == 0) {
+        uint32_t* a = fl + kFlagAct0 + (int)(ks % 3ull);
+        if (__ldg(a) == 0u) *reinterpret_cast<volatile uint32_t*>(a) = 1u;
+    }
 }
 
 }  // namespace snp

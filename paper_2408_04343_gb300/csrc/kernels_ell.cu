@@ -21,44 +21,22 @@
 
 namespace snp {
 
-// Returns true if the launch for absolute step kg must not run (shared with
-// kernels_step.cu's protocol: activity words by step mod 3, sticky halt).
-__device__ __forceinline__ bool ell_check_halt(uint32_t* fl, unsigned long long* steps, unsigned long long kg) {
-    if (ld_volatile(fl + kFlagHalted)) return true;
-    if (ld_volatile(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
-        if (threadIdx.x == 0) {
-            steps[kStepHalt] = kg;
-            __threadfence();
-            atomicExch(fl + kFlagHalted, 1u);
-        }
-        return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void ell_raise_activity(uint32_t* fl, unsigned long long ks, bool active) {
-    if (__syncthreads_or(active) && threadIdx.x == 0) {
-        uint32_t* a = fl + kFlagAct0 + (int)(ks % 3ull);
-        if (ld_volatile(a) == 0u) atomicExch(a, 1u);
-    }
-}
-
 // Select for step ks on one slot, writing the per-rule emission bytes.
 template <bool COMPACT, int SEL>
 __device__ __forceinline__ bool ell_select_slot(const DevSys& s, const EllSys& e, int32_t slot, int32_t& c,
                                                 unsigned long long ks) {
     const uint32_t st = s.st[slot];
-    const int32_t r0 = __ldg(s.rule_off + slot), r1 = __ldg(s.rule_off + slot + 1);
+    const int32_t r0 = rule_lo(s, slot), r1 = rule_hi(s, slot);
     const SelOut o = select_neuron<COMPACT, SEL>(s.rules, r0, r1, c, st, ks,
-                                                 SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u,
+                                                 SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u,
                                                  s.seed);
     int32_t emitting = -1;  // local index of the rule that emits at ks
     if ((st >> kPendShift) != 0u && (st & kDMask) == 0u) emitting = (int32_t)(st >> kPendShift) - 1;
     else if (o.s >= 0 && o.emit > 0) emitting = o.s;
-    uint8_t* Em = e.Em[ks & 1ull];
+    uint8_t* Em = SNP_PICK(e.Em, ks);
     for (int32_t r = r0; r < r1; ++r) Em[r] = (r - r0) == emitting ? 1 : 0;
     c = o.c_after;
-    s.S[ks & 1ull][slot] = o.s;
+    SNP_PICK(s.S, ks)[slot] = o.s;
     s.st[slot] = o.st;
     return o.active;
 }
@@ -70,7 +48,7 @@ __global__ void __launch_bounds__(256) k_ell_pull(DevSys s, EllSys e, int32_t t)
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
     const unsigned long long ks = GATHER ? kg + 1ull : kg;
     if (GATHER) {
-        if (ell_check_halt(fl, s.step, kg)) return;
+        if (step_blocked(fl, s.step, kg)) return;
         if (SELECT && blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
     }
     const int lane = threadIdx.x & 31;
@@ -81,7 +59,7 @@ __global__ void __launch_bounds__(256) k_ell_pull(DevSys s, EllSys e, int32_t t)
         const bool valid = slot < s.q;
         int32_t c = valid ? s.C[slot] : 0;
         if (GATHER) {
-            const uint8_t* __restrict__ Em = e.Em[kg & 1ull];
+            const uint8_t* __restrict__ Em = SNP_PICK(e.Em, kg);
             const int32_t b = __ldg(e.in_ptr + slice);
             const int32_t w = __ldg(e.in_ptr + slice + 1) - b;
             const int2* __restrict__ p = e.in_ent + (size_t)b * kSlice + lane;
@@ -108,7 +86,7 @@ __global__ void __launch_bounds__(256) k_ell_pull(DevSys s, EllSys e, int32_t t)
         if (SELECT && valid) active = ell_select_slot<COMPACT, SEL>(s, e, slot, c, ks);
         if (valid) s.C[slot] = c;
     }
-    if (SELECT) ell_raise_activity(fl, ks, active);
+    if (SELECT) raise_step_activity(fl, ks, active);
 }
 
 // Select launch of step ks = base + t for the push and dense variants.  With
@@ -119,7 +97,7 @@ template <bool INFLOW, bool SELECT, bool COMPACT, int SEL>
 __global__ void __launch_bounds__(256) k_ell_select(DevSys s, EllSys e, int32_t t) {
     uint32_t* fl = s.flags;
     const unsigned long long ks = s.step[kStepBase] + (unsigned long long)t;
-    if (ld_volatile(fl + kFlagHalted)) return;
+    if (call_halted(fl)) return;
     const int32_t slot = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     bool active = false;
     if (slot < s.q) {
@@ -139,21 +117,21 @@ __global__ void __launch_bounds__(256) k_ell_select(DevSys s, EllSys e, int32_t 
         if (SELECT) active = ell_select_slot<COMPACT, SEL>(s, e, slot, c, ks);
         s.C[slot] = c;
     }
-    if (SELECT) ell_raise_activity(fl, ks, active);
+    if (SELECT) raise_step_activity(fl, ks, active);
 }
 
 // ELL push of step kg = base + t: a warp per 32 consecutive rules.
 __global__ void __launch_bounds__(256) k_ell_push(DevSys s, EllSys e, int32_t t) {
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
-    if (ell_check_halt(fl, s.step, kg)) return;
+    if (step_blocked(fl, s.step, kg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 1ull) % 3ull)] = 0u;
     const int lane = threadIdx.x & 31;
     const int64_t rs = (int64_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int64_t nrs = (e.m + kSlice - 1) / kSlice;
     if (rs >= nrs) return;  // warp-uniform
     const int64_t r = rs * kSlice + lane;
-    const bool on = r < e.m && e.Em[kg & 1ull][r];
+    const bool on = r < e.m && SNP_PICK(e.Em, kg)[r];
     const int32_t b = __ldg(e.out_ptr + rs);
     const int32_t w = __ldg(e.out_ptr + rs + 1) - b;
     const int2* __restrict__ p = e.out_ent + (size_t)b * kSlice + lane;
@@ -175,12 +153,12 @@ __global__ void __launch_bounds__(256) k_ell_push(DevSys s, EllSys e, int32_t t)
 __global__ void __launch_bounds__(256) k_dense_accum(DevSys s, EllSys e, int32_t t, int32_t rows) {
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
-    if (ell_check_halt(fl, s.step, kg)) return;
+    if (step_blocked(fl, s.step, kg)) return;
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.y * rows;
     const int64_t r1 = r0 + rows < e.m ? r0 + rows : e.m;
-    const uint8_t* __restrict__ Em = e.Em[kg & 1ull];
+    const uint8_t* __restrict__ Em = SNP_PICK(e.Em, kg);
     if (j >= s.q) return;
     long long sum = 0;
     const int32_t* __restrict__ col = e.dense + j;

@@ -59,15 +59,15 @@ __device__ void run_resident(const DevSys& s, long long n, uint32_t* esm) {
         int32_t emit = 0;
         if (slot < s.q) {
             const SelOut o = select_neuron<COMPACT, SEL>(
-                s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), s.C[slot], s.st[slot], base,
-                SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
+                s.rules, rule_lo(s, slot), rule_hi(s, slot), s.C[slot], s.st[slot], base,
+                SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
             s.C[slot] = o.c_after;
             s.st[slot] = o.st;
-            s.S[base & 1ull][slot] = o.s;
+            SNP_PICK(s.S, base)[slot] = o.s;
             emit = o.emit;
             act |= o.active;
         }
-        e_put_slice<EB>(Eb[base & 1ull], slice, lane, emit);
+        e_put_slice<EB>(SNP_PICK(Eb, base), slice, lane, emit);
     }
     bool any = __syncthreads_or(act);
 
@@ -80,8 +80,8 @@ __device__ void run_resident(const DevSys& s, long long n, uint32_t* esm) {
         }
         const unsigned long long kg = base + (unsigned long long)t;
         const bool do_sel = (t + 1) < n;
-        const uint32_t* __restrict__ Ek = Eb[kg & 1ull];
-        uint32_t* En = Eb[(kg + 1ull) & 1ull];
+        const uint32_t* __restrict__ Ek = SNP_PICK(Eb, kg);
+        uint32_t* En = SNP_PICK(Eb, kg + 1ull);
         act = false;
         for (int32_t slice = warp; slice < s.nslices; slice += nwarps) {
             const int32_t slot = slice * kSlice + lane;
@@ -116,11 +116,11 @@ __device__ void run_resident(const DevSys& s, long long n, uint32_t* esm) {
             int32_t emit = 0;
             if (do_sel && valid) {
                 const SelOut o = select_neuron<COMPACT, SEL>(
-                    s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), c, st, kg + 1ull,
-                    SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
+                    s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, kg + 1ull,
+                    SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
                 c = o.c_after;
                 s.st[slot] = o.st;
-                s.S[(kg + 1ull) & 1ull][slot] = o.s;
+                SNP_PICK(s.S, kg + 1ull)[slot] = o.s;
                 emit = o.emit;
                 act |= o.active;
             }

@@ -25,27 +25,6 @@
 
 namespace snp {
 
-// Returns true if the launch gathering absolute step kg must not run.
-__device__ __forceinline__ bool check_halt(uint32_t* fl, unsigned long long* steps, unsigned long long kg) {
-    if (ld_volatile(fl + kFlagHalted)) return true;
-    if (ld_volatile(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
-        if (threadIdx.x == 0) {
-            steps[kStepHalt] = kg;
-            __threadfence();
-            atomicExch(fl + kFlagHalted, 1u);
-        }
-        return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void raise_activity(uint32_t* fl, unsigned long long ks, bool active) {
-    if (__syncthreads_or(active) && threadIdx.x == 0) {
-        uint32_t* a = fl + kFlagAct0 + (int)(ks % 3ull);
-        if (ld_volatile(a) == 0u) atomicExch(a, 1u);
-    }
-}
-
 template <bool GATHER, bool SELECT, bool COMPACT, int SEL>
 __global__ void __launch_bounds__(256) k_step_pull(DevSys s, int32_t t) {
     uint32_t* fl = s.flags;
@@ -53,7 +32,7 @@ __global__ void __launch_bounds__(256) k_step_pull(DevSys s, int32_t t) {
     const unsigned long long kg = base + (unsigned long long)t;
     const unsigned long long ks = GATHER ? kg + 1ull : kg;
     if (GATHER) {
-        if (check_halt(fl, s.step, kg)) return;
+        if (step_blocked(fl, s.step, kg)) return;
         if (SELECT && blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
     }
     const int lane = threadIdx.x & 31;
@@ -69,7 +48,7 @@ __global__ void __launch_bounds__(256) k_step_pull(DevSys s, int32_t t) {
             st = s.st[slot];
         }
         if (GATHER) {
-            const int32_t* __restrict__ E = s.E[kg & 1ull];
+            const int32_t* __restrict__ E = SNP_PICK(s.E, kg);
             const int32_t b = __ldg(s.slice_ptr + slice);
             const int32_t w = __ldg(s.slice_ptr + slice + 1) - b;
             const int32_t* __restrict__ p = s.in_idx + (size_t)b * kSlice + lane;
@@ -94,30 +73,30 @@ __global__ void __launch_bounds__(256) k_step_pull(DevSys s, int32_t t) {
         }
         if (SELECT && valid) {
             const SelOut o = select_neuron<COMPACT, SEL>(
-                s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), c, st, ks,
-                SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
+                s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks,
+                SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
             c = o.c_after;
             active = o.active;
-            s.E[ks & 1ull][slot] = o.emit;
-            s.S[ks & 1ull][slot] = o.s;
+            SNP_PICK(s.E, ks)[slot] = o.emit;
+            SNP_PICK(s.S, ks)[slot] = o.s;
             s.st[slot] = o.st;
         }
         if (valid) s.C[slot] = c;
     }
-    if (SELECT) raise_activity(fl, ks, active);
+    if (SELECT) raise_step_activity(fl, ks, active);
 }
 
 // Push propagation of step kg = base + t: select already ran for kg.
 __global__ void __launch_bounds__(256) k_push_scatter(DevSys s, int32_t t) {
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
-    if (check_halt(fl, s.step, kg)) return;
+    if (step_blocked(fl, s.step, kg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 1ull) % 3ull)] = 0u;
     const int lane = threadIdx.x & 31;
     const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (slice >= s.nslices) return;  // warp-uniform
     const int32_t slot = slice * kSlice + lane;
-    const int32_t emit = slot < s.q ? s.E[kg & 1ull][slot] : 0;
+    const int32_t emit = slot < s.q ? SNP_PICK(s.E, kg)[slot] : 0;
     const int32_t b = __ldg(s.out_ptr + slice);
     const int32_t w = __ldg(s.out_ptr + slice + 1) - b;
     const int32_t* __restrict__ p = s.out_idx + (size_t)b * kSlice + lane;
@@ -138,22 +117,22 @@ template <bool COMPACT, int SEL>
 __global__ void __launch_bounds__(256) k_select_push(DevSys s, int32_t t) {
     uint32_t* fl = s.flags;
     const unsigned long long ks = s.step[kStepBase] + (unsigned long long)t;
-    if (ld_volatile(fl + kFlagHalted)) return;
+    if (call_halted(fl)) return;
     const int lane = threadIdx.x & 31;
     const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int32_t slot = slice * kSlice + lane;
     bool active = false;
     if (slice < s.nslices && slot < s.q) {
         const SelOut o = select_neuron<COMPACT, SEL>(
-            s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), s.C[slot], s.st[slot], ks,
-            SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
+            s.rules, rule_lo(s, slot), rule_hi(s, slot), s.C[slot], s.st[slot], ks,
+            SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
         active = o.active;
         s.C[slot] = o.c_after;
-        s.E[ks & 1ull][slot] = o.emit;
-        s.S[ks & 1ull][slot] = o.s;
+        SNP_PICK(s.E, ks)[slot] = o.emit;
+        SNP_PICK(s.S, ks)[slot] = o.s;
         s.st[slot] = o.st;
     }
-    raise_activity(fl, ks, active);
+    raise_step_activity(fl, ks, active);
 }
 
 // Call bookkeeping: remember where the call started and clear its flags.
@@ -269,7 +248,7 @@ __global__ void k_export(const DevSys s, const int32_t* __restrict__ rule_base, 
             // S of the last executed step k-1 (parity < 0: read k on the device)
             const unsigned long long k = s.step[kStepBase];
             const int par = parity >= 0 ? parity : (int)((k + 1ull) & 1ull);
-            const int32_t x = (parity < 0 && k == 0ull) ? -1 : s.S[par][slot];
+            const int32_t x = (parity < 0 && k == 0ull) ? -1 : SNP_PICK(s.S, par)[slot];
             v = x >= 0 ? rule_base[slot] + x : -1;
             break;
         }

@@ -65,19 +65,11 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
     int* acc = reinterpret_cast<int*>(smem + tl.part_words);
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
-    if (ld_volatile(fl + kFlagHalted)) return;
-    if (ld_volatile(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
-        if (threadIdx.x == 0) {
-            s.step[kStepHalt] = kg;
-            __threadfence();
-            atomicExch(fl + kFlagHalted, 1u);
-        }
-        return;
-    }
+    if (step_blocked(fl, s.step, kg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
     const int32_t lo = __ldg(tl.cta_lo + blockIdx.x), hi = __ldg(tl.cta_lo + blockIdx.x + 1);
     for (int i = threadIdx.x; i < tl.acc_words; i += blockDim.x) acc[i] = 0;
-    const uint32_t* Eprev = tl.Eg[kg & 1ull];
+    const uint32_t* Eprev = SNP_PICK(tl.Eg, kg);
     const uint32_t smask = (tl.src_bits >= 32) ? 0xffffffffu : ((1u << tl.src_bits) - 1u);
     const int sbits = tl.src_bits;
     const uint4* ent = reinterpret_cast<const uint4*>(tl.ent);
@@ -123,7 +115,7 @@ __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
     const unsigned long long ks = GATHER ? kg + 1ull : kg;
-    if (ld_volatile(fl + kFlagHalted)) return;
+    if (call_halted(fl)) return;
     const int lane = threadIdx.x & 31;
     const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int32_t slot = slice * kSlice + lane;
@@ -148,23 +140,18 @@ __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int
         uint32_t emit = 0u;
         if (SELECT && valid) {
             const SelOut o = select_neuron<COMPACT, SEL>(
-                s.rules, __ldg(s.rule_off + slot), __ldg(s.rule_off + slot + 1), c, st, ks,
-                SEL == SNP_SELECT_PHILOX ? (uint32_t)__ldg(s.orig + slot) : 0u, s.seed);
+                s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks,
+                SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
             c = o.c_after;
             active = o.active;
             emit = (uint32_t)o.emit;
-            s.S[ks & 1ull][slot] = o.s;
+            SNP_PICK(s.S, ks)[slot] = o.s;
             s.st[slot] = o.st;
         }
         if (valid) s.C[slot] = c;
-        if (SELECT) pk_put_slice<EB>(tl.Eg[ks & 1ull], slice, lane, emit);
+        if (SELECT) pk_put_slice<EB>(SNP_PICK(tl.Eg, ks), slice, lane, emit);
     }
-    if (SELECT) {
-        if (__syncthreads_or(active) && threadIdx.x == 0) {
-            uint32_t* a = fl + kFlagAct0 + (int)(ks % 3ull);
-            if (ld_volatile(a) == 0u) atomicExch(a, 1u);
-        }
-    }
+    if (SELECT) raise_step_activity(fl, ks, active);
 }
 
 template <int EB>

@@ -109,7 +109,8 @@ int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int 
     hp->q = q;
     hp->m = m;
     hp->nsyn = nsyn;
-    if (window < kSlice) window = kSlice;
+    const bool sort_slots = window > 0;
+    if (sort_slots && window < kSlice) window = kSlice;
 
     // in-degrees
     std::vector<int32_t> indeg(q, 0);
@@ -122,7 +123,7 @@ int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int 
     // slot order: stable sort by decreasing in-degree inside windows
     hp->perm.resize(q);
     std::iota(hp->perm.begin(), hp->perm.end(), 0);
-    for (int64_t w0 = 0; w0 < q; w0 += window) {
+    for (int64_t w0 = 0; sort_slots && w0 < q; w0 += window) {
         int64_t w1 = std::min<int64_t>(q, w0 + window);
         std::stable_sort(hp->perm.begin() + w0, hp->perm.begin() + w1,
                          [&](int32_t a, int32_t b) { return indeg[a] > indeg[b]; });
@@ -150,6 +151,13 @@ int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int 
             compact = false;
     }
     hp->max_rules = max_rules;
+    hp->uniform_rules = max_rules;
+    for (int32_t i = 0; i < q; ++i)
+        if (d->rule_offsets[i + 1] - d->rule_offsets[i] != max_rules) {
+            hp->uniform_rules = 0;
+            break;
+        }
+    hp->identity = !sort_slots;
     hp->max_p = max_p;
     hp->max_d = max_d;
     hp->compact = compact;

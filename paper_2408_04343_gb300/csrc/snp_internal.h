@@ -70,6 +70,8 @@ struct DevSys {
     uint64_t seed;
     int32_t select;
     int32_t max_p;
+    int32_t rules_per_neuron;  // > 0: every neuron has this many rules (rule r0 = slot * R)
+    int32_t identity;          // 1: slot order is the caller's order (orig[slot] = slot)
 };
 
 // Host-side packed form of a system (slot order).
@@ -77,6 +79,8 @@ struct HostPack {
     int32_t q = 0;
     int64_t m = 0, nsyn = 0;
     int32_t max_rules = 0, max_p = 0, max_d = 0, max_out = 0, max_in = 0;
+    int32_t uniform_rules = 0;  // > 0: every neuron has this many rules
+    bool identity = false;      // slot order == caller's order
     bool compact = true;
     std::vector<int32_t> perm;        // slot -> neuron
     std::vector<int32_t> inv;         // neuron -> slot

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <memory>
 #include <utility>
 #include <vector>
 
@@ -15,6 +16,23 @@ namespace snp {
 constexpr int kChunk = 48;                 // steps per captured CUDA graph
 constexpr int kSortWindow = 8192;          // in-degree sort window (slots)
 constexpr int kAutoResidentMaxQ = 8192;    // AUTO picks the resident engine up to here
+
+// Host-side layouts of a system kept until they are uploaded.
+struct HostImage {
+    HostPack hp;
+    TiledPack tp;
+    EllPack ep;
+    std::vector<int32_t> dense;
+};
+
+// One device buffer of a system: where its pointer goes, its source (or a
+// fill byte when src is NULL) and its size.
+struct Piece {
+    void** dst;
+    const void* src;
+    size_t bytes;
+    int fill;
+};
 
 }  // namespace snp
 
@@ -36,6 +54,8 @@ struct snp_system {
     int64_t m = 0, nsyn = 0;
     int32_t max_p = 0, max_rules = 0;
     bool compact = true;
+    int32_t uniform_rules = 0;
+    bool identity = false;
     int64_t in_entries = 0, out_entries = 0, rule_words = 0;
     std::vector<int32_t> perm;          // slot -> caller's neuron
     std::vector<int64_t> rule_offsets;  // caller's N_Pi (for set_state checks)
@@ -50,9 +70,19 @@ struct snp_system {
     int32_t tiled_threads = 1024;
     // ELL and dense forms
     snp::EllSys ell{};
+    // deferred upload
+    std::unique_ptr<snp::HostImage> img;  // host layouts until uploaded
+    bool materialized = false;
+    size_t planned_bytes = 0;             // device bytes the upload will take
+    struct snp_batch* owner = nullptr;    // batch that uploaded it (memory accounting)
+    bool own_stream = false;              // stream created by the library
 };
 
 namespace snp {
+size_t plan_bytes(const std::vector<Piece>& plan);
+void build_plan(snp_system* s, std::vector<Piece>& plan);
+int materialize(snp_system* s);
+void batch_release(snp_system* s);
 void* sys_alloc(snp_system* s, size_t bytes);
 bool is_device_ptr(const void* p);
 bool resident_fits(const snp_system* s, ResidentPlan* plan);

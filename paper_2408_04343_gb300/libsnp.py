@@ -40,7 +40,7 @@ class snp_allocator(ct.Structure):
 class snp_options(ct.Structure):
     _fields_ = [("form", ct.c_int32), ("prop", ct.c_int32), ("select", ct.c_int32), ("engine", ct.c_int32),
                 ("seed", ct.c_uint64), ("stream", ct.c_void_p), ("alloc", ct.POINTER(snp_allocator)),
-                ("threads", ct.c_int32), ("reserved", ct.c_int32)]
+                ("threads", ct.c_int32), ("flags", ct.c_int32)]
 
 
 class snp_desc(ct.Structure):
@@ -66,7 +66,14 @@ class snp_device_system(ct.Structure):
                 ("C", ct.c_void_p), ("D", ct.c_void_p), ("P", ct.c_void_p), ("S", ct.c_void_p)]
 
 
+class snp_batch_info(ct.Structure):
+    _fields_ = [("budget_bytes", ct.c_uint64), ("resident_bytes", ct.c_uint64),
+                ("peak_resident_bytes", ct.c_uint64), ("rounds", ct.c_int64), ("admitted", ct.c_int64),
+                ("finished", ct.c_int64), ("waiting", ct.c_int64), ("running", ct.c_int64)]
+
+
 SNP_NOALLOC_MAX_Q = 262144
+SNP_FLAG_DEFER_UPLOAD = 1
 
 _P = ct.c_void_p
 _SIGS = {
@@ -86,6 +93,7 @@ _SIGS = {
     "snp_batch_poll": (ct.c_int, [_P, ct.c_int64, ct.POINTER(ct.c_int)]),
     "snp_batch_wait": (ct.c_int, [_P, ct.c_int64]),
     "snp_batch_steps_done": (ct.c_int, [_P, ct.c_int64, ct.c_int32, ct.POINTER(ct.c_int64)]),
+    "snp_batch_get_info": (ct.c_int, [_P, ct.POINTER(snp_batch_info)]),
     "snp_export_dense": (ct.c_int, [ct.POINTER(snp_desc), _P, ct.c_int64]),
     "snp_export_ell": (ct.c_int, [ct.POINTER(snp_desc), _P, _P, ct.c_int64, ct.POINTER(ct.c_int64)]),
     "snp_export_compressed": (ct.c_int, [ct.POINTER(snp_desc), _P, ct.c_int64, ct.POINTER(ct.c_int64)]),
@@ -161,8 +169,8 @@ class _DescHolder:
 
 
 def make_options(form=SNP_FORM_OPT, prop=SNP_PROP_PULL, select=SNP_SELECT_FIRST, engine=SNP_ENGINE_AUTO,
-                 seed=0, stream=None, threads=0, allocator=None) -> snp_options:
-    o = snp_options(form, prop, select, engine, seed & (2**64 - 1), _stream_handle(stream), None, threads, 0)
+                 seed=0, stream=None, threads=0, allocator=None, flags=0) -> snp_options:
+    o = snp_options(form, prop, select, engine, seed & (2**64 - 1), _stream_handle(stream), None, threads, flags)
     if allocator is not None:
         o.alloc = ct.pointer(allocator)
     return o
@@ -172,7 +180,7 @@ class System:
     """One SNP system on the GPU (snp_create .. snp_destroy)."""
 
     def __init__(self, desc, *, form=SNP_FORM_OPT, prop=SNP_PROP_PULL, select=SNP_SELECT_FIRST,
-                 engine=SNP_ENGINE_AUTO, seed=None, stream=None, threads=0, allocator=None):
+                 engine=SNP_ENGINE_AUTO, seed=None, stream=None, threads=0, allocator=None, deferred=False):
         lib = load()
         self._lib = lib
         self.q = int(desc.q)
@@ -181,7 +189,8 @@ class System:
         h = _DescHolder(desc)
         seed = getattr(desc, "seed", 0) if seed is None else seed
         self._alloc = allocator
-        opts = make_options(form, prop, select, engine, int(seed), stream, threads, allocator)
+        opts = make_options(form, prop, select, engine, int(seed), stream, threads, allocator,
+                            SNP_FLAG_DEFER_UPLOAD if deferred else 0)
         out = ct.c_void_p()
         check(lib.snp_create(ct.byref(h.d), ct.byref(opts), ct.byref(out)))
         self.handle = out.value
@@ -289,6 +298,16 @@ class Batch:
             check(self._lib.snp_batch_steps_done(self.handle, int(ticket), i, ct.byref(v)))
             out.append(int(v.value))
         return out
+
+    def steps_done(self, ticket: int, index: int) -> int:
+        v = ct.c_int64(0)
+        check(self._lib.snp_batch_steps_done(self.handle, int(ticket), int(index), ct.byref(v)))
+        return int(v.value)
+
+    def info(self) -> snp_batch_info:
+        inf = snp_batch_info()
+        check(self._lib.snp_batch_get_info(self.handle, ct.byref(inf)))
+        return inf
 
     def close(self):
         if getattr(self, "handle", None):

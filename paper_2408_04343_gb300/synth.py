@@ -193,16 +193,28 @@ def batch_sizes(rng: np.random.Generator, count: int, lo: int = 64, hi: int = 65
     return np.floor(x).astype(np.int64).clip(lo, hi)
 
 
-def batch_8k(seed: int = 4004, count: int = 8192, lo: int = 64, hi: int = 65536):
+def _batch_member(args):
+    i, qs, sd = args
+    return random_system(int(qs), int(sd), outdeg=(4, 16), rules=(3, 3), d_range=(0, 4), spikes=(0, 10),
+                         name=f"batch-{i}")
+
+
+def batch_8k(seed: int = 4004, count: int = 8192, lo: int = 64, hi: int = 65536, processes: int = 0):
     """8,192 independent systems, q log-uniform in [64, 65536], out-degree
     U{4..16}, 2 firing + 1 forgetting rule, d in [0,4], spikes U[0,10];
-    500 steps each, Philox with a per-system seed."""
+    500 steps each, Philox with a per-system seed.  With processes > 1 the
+    systems are drawn in a spawned process pool (same systems: each is
+    seeded on its own)."""
     rng = np.random.default_rng(seed)
     sizes = batch_sizes(rng, count, lo, hi)
     seeds = rng.integers(1, 2**62, size=count, dtype=np.int64)
-    systems = [random_system(int(qs), int(sd), outdeg=(4, 16), rules=(3, 3), d_range=(0, 4),
-                             spikes=(0, 10), name=f"batch-{i}")
-               for i, (qs, sd) in enumerate(zip(sizes, seeds))]
+    work = [(i, int(qs), int(sd)) for i, (qs, sd) in enumerate(zip(sizes, seeds))]
+    if processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            systems = pool.map(_batch_member, work, chunksize=64)
+    else:
+        systems = [_batch_member(w) for w in work]
     return systems, 500, SEL_PHILOX
 
 

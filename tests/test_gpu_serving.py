@@ -1,0 +1,125 @@
+"""The served form: continuous batching with admission by device memory.
+
+Checks that (1) every request's result is identical alone and in the mix
+(and, for small ones, identical to the oracle); (2) requests that arrive
+while others run are admitted and finish without waiting for the earlier
+long ones; (3) the device memory held by the batch never exceeds its budget
+while requests wait on the host for memory to free up.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_04343_gb300 import libsnp, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_04343_gb300 import build
+    build.build()
+    libsnp.load()
+
+
+def _requests(n, seed, q_range=(500, 120000), steps_range=(5, 300)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        q = int(np.exp(rng.uniform(np.log(q_range[0]), np.log(q_range[1]))))
+        steps = int(np.exp(rng.uniform(np.log(steps_range[0]), np.log(steps_range[1]))))
+        rules = int(rng.integers(2, 5))
+        d = synth.random_system(q, 7000 + 13 * i + seed, outdeg=(2, 32), rules=(rules, rules), d_range=(0, 5),
+                                spikes=(0, 20))
+        out.append((d, steps, int(rng.integers(1, 2**62))))
+    return out
+
+
+def test_mix_equals_alone_and_oracle():
+    reqs = _requests(24, 1)
+    b = libsnp.Batch(mem_budget=8 << 30)
+    systems, tickets = [], []
+    for d, steps, seed in reqs:
+        g = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=seed, deferred=True)
+        systems.append(g)
+        tickets.append(b.submit([g], [steps]))
+        time.sleep(0.002)   # arrivals spread over time, while earlier ones run
+    for (d, steps, seed), g, t in zip(reqs, systems, tickets):
+        done = b.wait(t)[0]
+        alone = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=seed)
+        assert alone.step(steps) == done
+        a = alone.get_state()
+        m = g.get_state()
+        for x, y in zip(a[:3], m[:3]):
+            assert (x == y).all()
+        assert a[3] == m[3]
+        assert (alone.spiking() == g.spiking()).all()
+        if d.q <= 5000:
+            st = oracle.initial_state(d)
+            ex, S = oracle.run(d, st, steps, oracle.PHILOX, seed)
+            assert ex == done and (st[0] == m[0]).all() and (st[1] == m[1]).all() and (st[2] == m[2]).all()
+        alone.close()
+        g.close()
+    inf = b.info()
+    assert inf.finished == len(reqs) and inf.waiting == 0 and inf.running == 0
+    b.close()
+
+
+def test_late_short_request_overtakes_long_one():
+    long_d = synth.random_system(400000, 5, outdeg=(8, 24), rules=(4, 4), d_range=(0, 5), spikes=(0, 20))
+    short_d = synth.random_system(2000, 6, outdeg=(2, 32), rules=(3, 3), d_range=(0, 5), spikes=(0, 20))
+    b = libsnp.Batch()
+    gl = libsnp.System(long_d, select=libsnp.SNP_SELECT_PHILOX, seed=1, deferred=True)
+    gs = libsnp.System(short_d, select=libsnp.SNP_SELECT_PHILOX, seed=2, deferred=True)
+    tl = b.submit([gl], [3000])
+    time.sleep(0.05)
+    ts = b.submit([gs], [20])
+    b.wait(ts)
+    assert not b.poll(tl), "the short request should finish while the long one still runs"
+    b.wait(tl)
+    b.close()
+
+
+def test_admission_respects_memory_budget():
+    reqs = _requests(16, 2, q_range=(20000, 60000), steps_range=(50, 120))
+    sizes = []
+    for d, _, _ in reqs:
+        g = libsnp.System(d, deferred=True)
+        sizes.append(g.info().device_bytes)
+        g.close()
+    budget = int(max(sizes) * 2.5)   # at most two or three requests resident at once
+    b = libsnp.Batch(mem_budget=budget)
+    systems = [libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=s, deferred=True) for d, _, s in reqs]
+    tickets = [b.submit([g], [steps]) for g, (_, steps, _) in zip(systems, reqs)]
+    peak_seen = 0
+    pending = list(zip(tickets, systems))
+    while pending:
+        t, g = pending[0]
+        if b.poll(t):
+            C = g.config()
+            assert C.shape[0] == g.q
+            g.close()          # returns its memory to the batch
+            pending.pop(0)
+        inf = b.info()
+        peak_seen = max(peak_seen, inf.resident_bytes)
+        time.sleep(0.001)
+    inf = b.info()
+    assert inf.peak_resident_bytes <= budget
+    assert peak_seen <= budget
+    assert inf.finished == len(reqs)
+    b.close()
+
+
+def test_request_larger_than_budget_is_refused():
+    d = synth.random_system(50000, 3, outdeg=(4, 16))
+    g = libsnp.System(d, deferred=True)
+    b = libsnp.Batch(mem_budget=1 << 20)
+    with pytest.raises(libsnp.SnpError) as ei:
+        b.submit([g], [10])
+    assert ei.value.status == libsnp.SNP_ERR_OOM
+    b.close()
