@@ -126,10 +126,10 @@ void build_plan(snp_system* s, std::vector<Piece>& plan) {
         tl.G = tp.G;
         tl.acc_words = tp.acc_words;
         tl.src_bits = tp.src_bits;
-        vec(&tl.grp, tp.grp);
+        vec(&tl.sub, tp.sub);
         vec(&tl.ent, tp.ent);
         vec(&tl.cta_lo, tp.cta_lo);
-        fill(&tl.inflow, (size_t)nslices * kSlice * 4, 0);
+        fill(&tl.inflow, (size_t)tp.P * nslices * kSlice * 4, 0);
         for (int b = 0; b < 2; ++b) fill(&tl.Eg[b], (size_t)tp.P * tp.part_words * 4, 0);
     }
 }

@@ -23,6 +23,8 @@
 
 #include <algorithm>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <deque>
 #include <map>
 #include <memory>
@@ -56,6 +58,55 @@ struct Ticket {
 };
 
 constexpr int64_t kRoundSteps = 64;          // steps per round and system
+
+// Online autotuner of the resident launch's CTA size.  Launches are grouped
+// by (bits per emission, log2 of the largest system); for each group every
+// candidate CTA size is tried on one real round (the work is not wasted:
+// results do not depend on the CTA size), then the fastest by measured
+// synaptic updates per second is used.  With SNP_AUTOTUNE_CACHE naming a
+// file, choices are read at batch creation and written back at destroy.
+struct Autotune {
+    static constexpr int kCand[3] = {256, 512, 1024};
+    struct Stat {
+        double work[3] = {0, 0, 0};
+        double secs[3] = {0, 0, 0};
+    };
+    std::map<std::pair<int, int>, Stat> stats;
+    int pick(const std::pair<int, int>& key) {
+        Stat& st = stats[key];
+        for (int c = 0; c < 3; ++c)
+            if (st.secs[c] == 0.0) return c;
+        int best = 0;
+        for (int c = 1; c < 3; ++c)
+            if (st.work[c] / st.secs[c] > st.work[best] / st.secs[best]) best = c;
+        return best;
+    }
+    void record(const std::pair<int, int>& key, int c, double work, double secs) {
+        Stat& st = stats[key];
+        st.work[c] += work;
+        st.secs[c] += secs > 1e-9 ? secs : 1e-9;
+    }
+    void load(const char* path) {
+        FILE* f = path ? fopen(path, "r") : nullptr;
+        if (!f) return;
+        int eb, lq, c;
+        double w, t;
+        while (fscanf(f, "%d %d %d %lf %lf", &eb, &lq, &c, &w, &t) == 5)
+            if (c >= 0 && c < 3) record({eb, lq}, c, w, t);
+        fclose(f);
+    }
+    void save(const char* path) const {
+        FILE* f = path ? fopen(path, "w") : nullptr;
+        if (!f) return;
+        for (const auto& kv : stats)
+            for (int c = 0; c < 3; ++c)
+                if (kv.second.secs[c] > 0.0)
+                    fprintf(f, "%d %d %d %.6g %.6g\n", kv.first.first, kv.first.second, c, kv.second.work[c],
+                            kv.second.secs[c]);
+        fclose(f);
+    }
+};
+constexpr int Autotune::kCand[3];
 constexpr int kBatchResidentMaxQ = 65536;    // larger systems run grid-wide
 
 }  // namespace snp
@@ -86,6 +137,8 @@ struct snp_batch {
     int sms = 0;
     int threads = 0;
     int64_t round = snp::kRoundSteps;
+    snp::Autotune tune;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace snp {
@@ -148,22 +201,34 @@ static int run_resident_group(snp_batch* b, std::vector<snp_system*>& sys, std::
     plan.e_bits = resident_e_bits(max_p);
     plan.max_q = max_q;
     plan.smem = resident_smem_bytes(max_q, plan.e_bits);
-    plan.threads = b->threads > 0 ? b->threads : 512;
+    int lq = 0;
+    while ((1 << lq) < max_q) ++lq;
+    const std::pair<int, int> key{plan.e_bits, lq};
+    const int cand = b->threads > 0 ? -1 : b->tune.pick(key);
+    plan.threads = cand < 0 ? b->threads : Autotune::kCand[cand];
     const bool compact = sys[0]->compact;
     const int sel = sys[0]->opt.select;
     plan.ctas = b->sms * ctas_per_sm(plan.threads, plan.smem);
+    double work = 0.0;
+    for (size_t r = 0; r < n; ++r) work += (double)(sys[order[r]]->nsyn + sys[order[r]]->q) * ns[r];
     if (cudaMemcpyAsync(b->d_sys, tab.data(), n * sizeof(DevSys), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
         cudaMemcpyAsync(b->d_nsteps, ns.data(), n * sizeof(long long), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
         cudaMemsetAsync(b->d_work, 0, sizeof(unsigned int), b->stream) != cudaSuccess)
         return fail(SNP_ERR_CUDA, "batch table upload");
+    cudaEventRecord(b->ev0, b->stream);
     if (launch_resident(b->d_sys, b->d_nsteps, (int)n, b->d_work, plan, compact, sel, b->stream) != cudaSuccess)
         return fail(SNP_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(cudaGetLastError()));
+    cudaEventRecord(b->ev1, b->stream);
     std::vector<unsigned long long> ex(n * 3);
     if (launch_gather_results(b->d_sys, (int)n, b->d_res, b->stream) != cudaSuccess ||
         cudaMemcpyAsync(ex.data(), b->d_res, n * 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream) !=
             cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return fail(SNP_ERR_CUDA, std::string("batch sync: ") + cudaGetErrorString(cudaGetLastError()));
+    if (cand >= 0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->tune.record(key, cand, work, ms * 1e-3);
+    }
     bool overflow = false;
     for (size_t r = 0; r < n; ++r) {
         exec_out[order[r]] = (int64_t)ex[3 * r + 1];
@@ -347,6 +412,9 @@ int snp_batch_create(const snp_options* opts, size_t mem_budget, snp_batch** out
         delete b;
         return fail(SNP_ERR_OOM, "device allocation failed");
     }
+    cudaEventCreate(&b->ev0);
+    cudaEventCreate(&b->ev1);
+    b->tune.load(getenv("SNP_AUTOTUNE_CACHE"));
     b->worker = std::thread(worker_main, b);
     *out = b;
     return SNP_OK;
@@ -366,6 +434,9 @@ int snp_batch_destroy(snp_batch* b) {
         for (snp_system* s : b->owned) s->owner = nullptr;
         b->owned.clear();
     }
+    b->tune.save(getenv("SNP_AUTOTUNE_CACHE"));
+    cudaEventDestroy(b->ev0);
+    cudaEventDestroy(b->ev1);
     cudaFree(b->d_sys);
     cudaFree(b->d_nsteps);
     cudaFree(b->d_res);

@@ -149,6 +149,56 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
     o.st = 0u;
     o.active = false;
     int32_t pick = -1;
+    if (COMPACT && r1 - r0 <= 4) {
+        // up to four one-word rules held in registers (one 16-byte load when
+        // the neuron's four rules are 16-byte aligned); bit t of `mask` =
+        // rule r0 + t applies
+        const int32_t R = r1 - r0;
+        uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+        if (R == 4 && (r0 & 3) == 0) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(rules) + (r0 >> 2));
+            w0 = v.x;
+            w1 = v.y;
+            w2 = v.z;
+            w3 = v.w;
+        } else {
+            if (R > 0) w0 = __ldg(rules + r0);
+            if (R > 1) w1 = __ldg(rules + r0 + 1);
+            if (R > 2) w2 = __ldg(rules + r0 + 2);
+            if (R > 3) w3 = __ldg(rules + r0 + 3);
+        }
+        auto applies_w = [&](uint32_t w) {
+            RuleF f;
+            f.k = (int32_t)(w & 255u);
+            f.j = (int32_t)((w >> 8) & 255u);
+            f.c = (int32_t)((w >> 16) & 255u);
+            return rule_applies(n, f);
+        };
+        uint32_t mask = 0u;
+        if (R > 0 && applies_w(w0)) mask |= 1u;
+        if (R > 1 && applies_w(w1)) mask |= 2u;
+        if (R > 2 && applies_w(w2)) mask |= 4u;
+        if (R > 3 && applies_w(w3)) mask |= 8u;
+        if (mask == 0u) return o;
+        if (SEL == SNP_SELECT_PHILOX && (mask & (mask - 1u)) != 0u) {
+            const int32_t cnt = __popc(mask);
+            const Philox4 x = philox4x32_10((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
+                                            (uint32_t)(seed >> 32));
+            int32_t idx = (int32_t)(((unsigned long long)x.v[0] * (unsigned long long)cnt) >> 32);
+            for (; idx > 0; --idx) mask &= mask - 1u;
+        }
+        const int32_t t = __ffs(mask) - 1;  // FIRST: the lowest applicable rule
+        const uint32_t w = t == 0 ? w0 : t == 1 ? w1 : t == 2 ? w2 : w3;
+        const int32_t c = (int32_t)((w >> 16) & 255u), p = (int32_t)((w >> 24) & 15u), d = (int32_t)(w >> 28);
+        o.active = true;
+        o.s = t;
+        o.c_after = n - c;
+        if (d == 0)
+            o.emit = p;
+        else
+            o.st = ((uint32_t)(t + 1) << kPendShift) | (uint32_t)(d - 1);
+        return o;
+    }
     if (SEL == SNP_SELECT_FIRST) {
         for (int32_t r = r0; r < r1; ++r) {
             if (rule_applies(n, load_rule<COMPACT>(rules, r))) {

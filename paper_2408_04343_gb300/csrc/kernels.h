@@ -38,11 +38,11 @@ int resident_max_smem();
 // Tiled engine (kernels_tiled.cu): device view of a TiledPack.
 struct TiledSys {
     int32_t P, part_words, e_bits, G, acc_words, src_bits;
-    const int32_t* grp;     // [G*P+1] group starts (words, multiples of 4)
+    const int32_t* sub;     // [G][kTiledMaxSub+1] window starts (words, multiples of 4); CTA g*P+h
     const uint32_t* ent;    // (dst_local << src_bits) | src_local
-    const int32_t* cta_lo;  // [G+1] slice ranges
+    const int32_t* cta_lo;  // [G/P+1] slice ranges
     uint32_t* Eg[2];        // packed emissions of step k in Eg[k & 1]
-    int32_t* inflow;        // [nslices*32] in-flow of the step being finished
+    int32_t* inflow;        // [P][nslices*32] in-flow of the step being finished, per partition
 };
 cudaError_t launch_tiled(const DevSys& s, const TiledSys& tl, int kind, int32_t t, cudaStream_t st, bool compact,
                          int sel, size_t smem, int threads);

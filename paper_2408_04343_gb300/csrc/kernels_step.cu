@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_step_pull(DevSys s, int32_t t) {
             active = o.active;
             SNP_PICK(s.E, ks)[slot] = o.emit;
             SNP_PICK(s.S, ks)[slot] = o.s;
-            s.st[slot] = o.st;
+            if (o.st != st) s.st[slot] = o.st;
         }
         if (valid) s.C[slot] = c;
     }

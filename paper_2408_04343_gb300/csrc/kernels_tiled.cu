@@ -8,12 +8,14 @@
 // partition at a time, so the gathers become shared-memory reads.
 //
 // A step is two launches:
-//  * k_tiled_gather -- one CTA per SM, each owning a range of slices.  For
-//    every partition h the CTA loads h's packed emissions and streams its
-//    group of in-edge words edge-parallel (16-byte vector loads, no
+//  * k_tiled_gather -- one CTA per SM.  CTA g*P + h owns slice range g and
+//    source partition h: it loads h's packed emissions once and streams the
+//    group of in-edge words of its range from h edge-parallel (16-byte vector loads, no
 //    per-neuron bookkeeping): each word names a local target slot and a
 //    source, whose emission is added to the target's shared-memory
-//    accumulator.  The accumulators become the in-flow vector of step k.
+//    accumulator (words are sorted by target, so runs of one target within
+//    a load are summed first).  The accumulators become partition h's
+//    in-flow vector of step k; the select launch sums the P of them.
 //  * k_tiled_select -- full occupancy, one warp per slice: finishes step k
 //    (C_{k+1} = C' + [open] * in-flow), selects step k+1 and writes the
 //    packed E_{k+1} that the next gather loads.
@@ -50,62 +52,87 @@ __device__ __forceinline__ void pk_put_slice(uint32_t* e, int32_t slice, int lan
     if (lane % per == 0) e[slice * EB + lane / per] = w;
 }
 
+// Four target-sorted words of one window: the emissions of consecutive words
+// with the same target are summed in registers and added to that target
+// (window base + dst) with one atomic, without branches: r_i is the running
+// sum of the run that ends at word i, flushed when the next word's target
+// differs (or at the last word).
 template <int EB>
-__device__ __forceinline__ void edge(const uint32_t* __restrict__ Esm, int* acc, uint32_t w, uint32_t smask,
-                                     int sbits) {
-    const uint32_t v = pk_get<EB>(Esm, w & smask);
-    if (v) atomicAdd(acc + (w >> sbits), (int)v);
+__device__ __forceinline__ void edges4(const uint32_t* __restrict__ Esm, int* acc, const uint4& q, uint32_t base,
+                                       uint32_t smask, int sbits) {
+    const uint32_t v0 = pk_get<EB>(Esm, q.x & smask), v1 = pk_get<EB>(Esm, q.y & smask);
+    const uint32_t v2 = pk_get<EB>(Esm, q.z & smask), v3 = pk_get<EB>(Esm, q.w & smask);
+    const uint32_t d0 = q.x >> sbits, d1 = q.y >> sbits, d2 = q.z >> sbits, d3 = q.w >> sbits;
+    const bool s1 = d1 == d0, s2 = d2 == d1, s3 = d3 == d2;
+    const uint32_t r0 = v0;
+    const uint32_t r1 = (s1 ? r0 : 0u) + v1;
+    const uint32_t r2 = (s2 ? r1 : 0u) + v2;
+    const uint32_t r3 = (s3 ? r2 : 0u) + v3;
+    if (!s1 && r0) atomicAdd(acc + base + d0, (int)r0);
+    if (!s2 && r1) atomicAdd(acc + base + d1, (int)r1);
+    if (!s3 && r2) atomicAdd(acc + base + d2, (int)r2);
+    if (r3) atomicAdd(acc + base + d3, (int)r3);
 }
 
-// In-flow of step kg = base + t into tl.inflow.
+// Target window of the 16-byte word group at index i (monotone in i).
+__device__ __forceinline__ uint32_t window_of(const int32_t* wb, int32_t i, int& k) {
+    while (k + 1 < kTiledMaxSub && i >= wb[k + 1]) ++k;
+    return (uint32_t)k;
+}
+
+// In-flow of step kg = base + t into tl.inflow (partition h's share).
 template <int EB>
 __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl, int32_t t) {
     extern __shared__ uint32_t smem[];
-    uint32_t* Esm = smem;
-    int* acc = reinterpret_cast<int*>(smem + tl.part_words);
+    __shared__ int32_t wb[kTiledMaxSub + 1];
+    uint32_t* Esm = smem;                                              // part_words + a zero word
+    int* acc = reinterpret_cast<int*>(smem + tl.part_words + 4);
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
     if (step_blocked(fl, s.step, kg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
-    const int32_t lo = __ldg(tl.cta_lo + blockIdx.x), hi = __ldg(tl.cta_lo + blockIdx.x + 1);
+    const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
+    const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
+    if (threadIdx.x <= kTiledMaxSub) wb[threadIdx.x] = __ldg(tl.sub + (size_t)blockIdx.x * (kTiledMaxSub + 1) + threadIdx.x) / 4;
+    if (threadIdx.x < 4) Esm[tl.part_words + threadIdx.x] = 0u;
     for (int i = threadIdx.x; i < tl.acc_words; i += blockDim.x) acc[i] = 0;
-    const uint32_t* Eprev = SNP_PICK(tl.Eg, kg);
-    const uint32_t smask = (tl.src_bits >= 32) ? 0xffffffffu : ((1u << tl.src_bits) - 1u);
+    const uint32_t smask = (1u << tl.src_bits) - 1u;
     const int sbits = tl.src_bits;
+    const int db = 32 - sbits;
     const uint4* ent = reinterpret_cast<const uint4*>(tl.ent);
-    for (int h = 0; h < tl.P; ++h) {
-        const uint4* src = reinterpret_cast<const uint4*>(Eprev + (size_t)h * tl.part_words);
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(SNP_PICK(tl.Eg, kg) + (size_t)h * tl.part_words);
         uint4* dst = reinterpret_cast<uint4*>(Esm);
         for (int i = threadIdx.x; i < tl.part_words / 4; i += blockDim.x) dst[i] = __ldcg(src + i);
         __syncthreads();
-        const int64_t g = (int64_t)blockIdx.x * tl.P + h;
-        const int32_t g0 = __ldg(tl.grp + g) / 4, g1 = __ldg(tl.grp + g + 1) / 4;
+        const int32_t g1 = wb[kTiledMaxSub];
         const int32_t stride = blockDim.x;
-        int32_t i = g0 + threadIdx.x;
-        for (; i + 3 * stride < g1; i += 4 * stride) {
-            const uint4 a = ld_stream_v4(ent + i);
-            const uint4 b = ld_stream_v4(ent + i + stride);
-            const uint4 c = ld_stream_v4(ent + i + 2 * stride);
-            const uint4 d = ld_stream_v4(ent + i + 3 * stride);
-            edge<EB>(Esm, acc, a.x, smask, sbits); edge<EB>(Esm, acc, a.y, smask, sbits);
-            edge<EB>(Esm, acc, a.z, smask, sbits); edge<EB>(Esm, acc, a.w, smask, sbits);
-            edge<EB>(Esm, acc, b.x, smask, sbits); edge<EB>(Esm, acc, b.y, smask, sbits);
-            edge<EB>(Esm, acc, b.z, smask, sbits); edge<EB>(Esm, acc, b.w, smask, sbits);
-            edge<EB>(Esm, acc, c.x, smask, sbits); edge<EB>(Esm, acc, c.y, smask, sbits);
-            edge<EB>(Esm, acc, c.z, smask, sbits); edge<EB>(Esm, acc, c.w, smask, sbits);
-            edge<EB>(Esm, acc, d.x, smask, sbits); edge<EB>(Esm, acc, d.y, smask, sbits);
-            edge<EB>(Esm, acc, d.z, smask, sbits); edge<EB>(Esm, acc, d.w, smask, sbits);
+        int32_t i = wb[0] + threadIdx.x;
+        // eight independent 16-byte loads per thread in flight, then their
+        // shared-memory work; the window index only moves forward
+        int k = 0;
+        for (; i + 7 * stride < g1; i += 8 * stride) {
+            uint4 q[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) q[u] = ld_stream_v4(ent + i + u * stride);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                int ku = k;
+                const uint32_t base = window_of(wb, i + u * stride, ku) << db;
+                edges4<EB>(Esm, acc, q[u], base, smask, sbits);
+            }
+            window_of(wb, i + 7 * stride, k);
         }
         for (; i < g1; i += stride) {
             const uint4 a = ld_stream_v4(ent + i);
-            edge<EB>(Esm, acc, a.x, smask, sbits); edge<EB>(Esm, acc, a.y, smask, sbits);
-            edge<EB>(Esm, acc, a.z, smask, sbits); edge<EB>(Esm, acc, a.w, smask, sbits);
+            edges4<EB>(Esm, acc, a, window_of(wb, i, k) << db, smask, sbits);
         }
         __syncthreads();
     }
     const int32_t slot0 = lo * kSlice;
     const int32_t nloc = (hi - lo) * kSlice;
-    for (int i = threadIdx.x; i < nloc; i += blockDim.x) tl.inflow[slot0 + i] = acc[i];
+    int32_t* out = tl.inflow + (size_t)h * s.nslices * kSlice + slot0;
+    for (int i = threadIdx.x; i < nloc; i += blockDim.x) out[i] = acc[i];
 }
 
 // Finishes step kg (GATHER: adds the in-flow to open neurons) and selects
@@ -129,7 +156,9 @@ __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int
             st = s.st[slot];
         }
         if (GATHER && valid && (st >> kPendShift) == 0u) {
-            const long long nc = (long long)c + tl.inflow[slot];
+            long long in = 0;
+            for (int h = 0; h < tl.P; ++h) in += tl.inflow[(size_t)h * s.nslices * kSlice + slot];
+            const long long nc = (long long)c + in;
             if (nc > 2147483647ll) {
                 atomicOr(fl + kFlagOverflow, 1u);
                 c = 2147483647;
@@ -146,7 +175,7 @@ __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int
             active = o.active;
             emit = (uint32_t)o.emit;
             SNP_PICK(s.S, ks)[slot] = o.s;
-            s.st[slot] = o.st;
+            if (o.st != st) s.st[slot] = o.st;  // most neurons stay open: skip the write
         }
         if (valid) s.C[slot] = c;
         if (SELECT) pk_put_slice<EB>(SNP_PICK(tl.Eg, ks), slice, lane, emit);

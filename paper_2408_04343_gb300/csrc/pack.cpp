@@ -335,7 +335,7 @@ int tiled_e_bits(int max_p) {
 }
 
 size_t tiled_smem_bytes(const TiledPack& tp) {
-    return (size_t)tp.part_words * 4 + (size_t)tp.acc_words * 4;
+    return (size_t)tp.part_words * 4 + 16 + (size_t)tp.acc_words * 4;
 }
 
 static int bits_for(int64_t n) {  // bits to hold 0..n
@@ -366,46 +366,61 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
         for (int32_t s = 0; s < q; ++s) std::sort(isrc.begin() + ioff[s], isrc.begin() + ioff[s + 1]);
     }
 
-    // CTA ranges of slices, balanced by entries plus a per-slice cost
-    std::vector<int32_t> cta_lo((size_t)G + 1, nslices);
-    {
-        std::vector<int64_t> cost((size_t)nslices + 1, 0);
-        for (int32_t sl = 0; sl < nslices; ++sl) {
-            const int64_t a = ioff[std::min<int64_t>(q, (int64_t)sl * kSlice)];
-            const int64_t b = ioff[std::min<int64_t>(q, (int64_t)(sl + 1) * kSlice)];
-            cost[sl + 1] = cost[sl] + (b - a) + 64;
-        }
+    // Slice ranges balanced by entries plus a per-slice cost.  The launch has
+    // one CTA per (range, partition), so a CTA loads one partition's
+    // emissions once; with P partitions there are G / P ranges.
+    std::vector<int64_t> cost((size_t)nslices + 1, 0);
+    for (int32_t sl = 0; sl < nslices; ++sl) {
+        const int64_t a = ioff[std::min<int64_t>(q, (int64_t)sl * kSlice)];
+        const int64_t b = ioff[std::min<int64_t>(q, (int64_t)(sl + 1) * kSlice)];
+        cost[sl + 1] = cost[sl] + (b - a) + 64;
+    }
+    auto split = [&](int nr, std::vector<int32_t>& lo) {
+        lo.assign((size_t)nr + 1, nslices);
         int32_t sl = 0;
-        for (int g = 0; g < G; ++g) {
-            cta_lo[g] = sl;
-            const int64_t target = cost[nslices] * (g + 1) / G;
+        for (int g = 0; g < nr; ++g) {
+            lo[g] = sl;
+            const int64_t target = cost[nslices] * (g + 1) / nr;
             while (sl < nslices && cost[sl + 1] <= target) ++sl;
         }
-        cta_lo[G] = nslices;
-    }
-    int32_t max_slices = 0;
-    for (int g = 0; g < G; ++g) max_slices = std::max(max_slices, cta_lo[g + 1] - cta_lo[g]);
-    const int64_t max_slots = (int64_t)max_slices * kSlice;  // local slot max_slots is the dummy
-    const int dst_bits = bits_for(max_slots);
-    const int acc_words = (int)((max_slots + 1 + 3) / 4 * 4);
-
-    // partitions: the fewest whose shared memory and entry encoding fit
-    int P = 0, part_size = 0, part_words = 0, src_bits = 0;
-    for (int p = 1; p <= 256; ++p) {
+        lo[nr] = nslices;
+    };
+    std::vector<int32_t> cta_lo;
+    int P = 0, NR = 0, part_size = 0, part_words = 0, src_bits = 0, acc_words = 0, max_slices = 0;
+    int64_t max_slots = 0;
+    // one CTA per SM first; more CTAs (several waves) when the accumulators of
+    // fewer, larger ranges would not fit next to a partition's emissions
+    for (int p = 1, gm = 1; gm <= 8 && P == 0; p = (p == 64 ? (++gm, 1) : p + 1)) {
+        const int nr = std::max(1, std::min(nslices, G * gm / p));
+        std::vector<int32_t> lo;
+        split(nr, lo);
+        int32_t ms = 0;
+        for (int g = 0; g < nr; ++g) ms = std::max(ms, lo[g + 1] - lo[g]);
+        const int64_t slots = (int64_t)ms * kSlice;  // local slot `slots` is the dummy
+        const int aw = (int)((slots + 1 + 3) / 4 * 4);
         int64_t ps = ((int64_t)q + p - 1) / p;
         ps = (ps + 511) / 512 * 512;
         const int64_t words = ps * eb / 32;
-        const size_t need = (size_t)words * 4 + (size_t)acc_words * 4;
-        const int sb = bits_for(ps - 1);
-        if (need <= smem_budget && sb + dst_bits <= 32) {
+        const size_t need = (size_t)words * 4 + (size_t)aw * 4;
+        const int sb = bits_for(ps);  // sources 0..part_size; part_size reads a zero word
+        const int db = 32 - sb;
+        const int64_t nsub = (slots + ((int64_t)1 << db) - 1) >> db;
+        if (need + 16 <= smem_budget && db >= 5 && nsub <= kTiledMaxSub) {
             P = p;
+            G = G * gm;
+            NR = nr;
+            cta_lo = lo;
             part_size = (int)ps;
             part_words = (int)words;
             src_bits = sb;
+            acc_words = aw;
+            max_slices = ms;
+            max_slots = slots;
             break;
         }
     }
     if (P == 0) return fail(SNP_ERR_UNSUPPORTED, "no source partitioning fits shared memory and 32-bit entries");
+    G = NR * P;  // CTAs of the launch
 
     tp->e_bits = eb;
     tp->P = P;
@@ -416,14 +431,17 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     tp->acc_words = acc_words;
     tp->src_bits = src_bits;
     tp->cta_lo = cta_lo;
-    tp->grp.assign((size_t)G * P + 1, 0);
+    const int db = 32 - src_bits;
+    tp->sub.assign((size_t)G * (kTiledMaxSub + 1), 0);
     tp->ent.clear();
-    tp->ent.reserve((size_t)hp.nsyn + (size_t)G * P * 4);
-    const uint32_t dummy = (uint32_t)max_slots << src_bits;
+    tp->ent.reserve((size_t)hp.nsyn + (size_t)G * kTiledMaxSub * 4);
+    const uint32_t pad = (uint32_t)part_size;  // target 0 of the window, source = the zero word
     std::vector<int64_t> cur(kSlice), end(kSlice);
-    for (int g = 0; g < G; ++g) {
+    for (int g = 0; g < NR; ++g) {
         for (int h = 0; h < P; ++h) {
-            tp->grp[(size_t)g * P + h] = (int32_t)tp->ent.size();
+            int32_t* sb = tp->sub.data() + (size_t)(g * P + h) * (kTiledMaxSub + 1);
+            int win = 0;  // current target window
+            sb[0] = (int32_t)tp->ent.size();
             const int32_t lo_src = h * part_size;
             const int32_t hi_src = (int32_t)std::min<int64_t>(q, (int64_t)(h + 1) * part_size);
             for (int32_t sl = cta_lo[g]; sl < cta_lo[g + 1]; ++sl) {
@@ -439,19 +457,27 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
                     end[l] = std::lower_bound(b, e, hi_src) - isrc.begin();
                     maxn = std::max(maxn, end[l] - cur[l]);
                 }
-                // column-major inside the slice: consecutive words target distinct lanes
+                // target-major: the words of one target are adjacent, so a
+                // 16-byte load mostly holds one or two targets and the kernel
+                // merges their emissions in registers before one atomic each
+                (void)maxn;
                 const uint32_t local0 = (uint32_t)(sl - cta_lo[g]) * kSlice;
-                for (int64_t t = 0; t < maxn; ++t)
-                    for (int l = 0; l < kSlice; ++l)
-                        if (cur[l] + t < end[l])
-                            tp->ent.push_back(((local0 + (uint32_t)l) << src_bits) |
-                                              (uint32_t)(isrc[(size_t)(cur[l] + t)] - lo_src));
+                for (int l = 0; l < kSlice; ++l) {
+                    const uint32_t local = local0 + (uint32_t)l;
+                    while ((int)(local >> db) > win) {  // close the window: pad to 16 bytes
+                        while (tp->ent.size() % 4) tp->ent.push_back(pad);
+                        sb[++win] = (int32_t)tp->ent.size();
+                    }
+                    const uint32_t dst = local & (((uint32_t)1 << db) - 1u);
+                    for (int64_t x = cur[l]; x < end[l]; ++x)
+                        tp->ent.push_back((dst << src_bits) | (uint32_t)(isrc[(size_t)x] - lo_src));
+                }
             }
-            while (tp->ent.size() % 4) tp->ent.push_back(dummy);  // 16-byte groups
+            while (tp->ent.size() % 4) tp->ent.push_back(pad);
+            while (win < kTiledMaxSub) sb[++win] = (int32_t)tp->ent.size();
             if (tp->ent.size() > (size_t)INT32_MAX) return fail(SNP_ERR_UNSUPPORTED, "too many entries");
         }
     }
-    tp->grp[(size_t)G * P] = (int32_t)tp->ent.size();
     return SNP_OK;
 }
 

@@ -94,28 +94,34 @@ struct HostPack {
     std::vector<int32_t> C0;          // slot order
 };
 
+constexpr int kTiledMaxSub = 8;  // target windows per CTA of the tiled engine
+
 // Layout of the tiled engine (shared-memory emissions, source partitions).
 // Sources are cut into P partitions of part_size slots so that one
-// partition's bit-packed emissions fit in shared memory.  Every CTA of the
-// launch owns a range of slices; for each partition h its in-edges from h
-// form one contiguous group of 32-bit words (dst_local << src_bits) |
-// src_local, where dst_local is the target slot relative to the CTA's first
-// slot and src_local the source slot relative to the partition start.
-// Groups are padded to 4 words with a dummy target so they load as 16-byte
-// vectors.  Inside a slice the words are column-major (t-th in-neighbour of
-// every lane, then the next t), so neighbouring words target distinct slots.
+// partition's bit-packed emissions fit in shared memory.  Slices are cut into
+// G/P ranges; CTA g*P + h owns range g and partition h, and the in-edges of
+// its range that come from partition h form one contiguous group of 32-bit
+// words (dst << src_bits) | src, src the source slot relative to the
+// partition start.  A word has 32 - src_bits bits for the target, too few
+// for a whole range, so the group is cut into up to kTiledMaxSub target
+// windows of 2^(32 - src_bits) slots; dst is relative to its window and the
+// kernel knows the window from the word's position (window boundaries in
+// `sub`).  Windows are padded to 16 bytes with words whose source is
+// part_size, which reads a zero word, so they load as 16-byte vectors.
+// Inside a window the words are sorted by target, so the words of one
+// 16-byte load mostly share a target and can be summed before the add.
 struct TiledPack {
     int e_bits = 0;          // bits per emission (2, 4, 8, 16)
     int P = 0;               // partitions
     int part_size = 0;       // slots per partition (multiple of 512)
     int part_words = 0;      // 32-bit words of one partition's emissions
-    int G = 0;               // CTAs of a launch (one range of slices each)
+    int G = 0;               // CTAs of a launch: one per (slice range, partition)
     int max_slices = 0;      // most slices given to one CTA
     int acc_words = 0;       // shared in-flow accumulators per CTA (+ dummy)
-    int src_bits = 0;        // low bits of an entry holding the source
-    std::vector<int32_t> grp;     // [G*P + 1] group starts in ent
+    int src_bits = 0;        // low bits of an entry holding the source (0..part_size)
+    std::vector<int32_t> sub;     // [G][kTiledMaxSub+1] window starts in ent (CTA g*P+h: range g, partition h)
     std::vector<uint32_t> ent;    // entries
-    std::vector<int32_t> cta_lo;  // [G + 1] first slice of each CTA
+    std::vector<int32_t> cta_lo;  // [G/P + 1] first slice of each range
 };
 
 // Layouts of the ELL form (Sec. 3, M^s_Pi: a column per rule of (neuron,
