@@ -163,6 +163,10 @@ typedef struct snp_info {
     int32_t compact_rules;   /* 1 if rules are stored in one word each     */
     int32_t e_bits;          /* bits per stored emission in shared memory  */
     uint64_t step;           /* absolute step counter k                    */
+    int32_t compiled_rules;  /* 1 if the select phase reads one 16-byte    */
+                             /* applicability record per neuron instead    */
+                             /* of testing each rule (Compressed form with */
+                             /* at most 4 small rules per neuron)          */
 } snp_info;
 
 typedef struct snp_system snp_system;

@@ -86,6 +86,8 @@ void build_plan(snp_system* s, std::vector<Piece>& plan) {
     }
     vec(&d.rule_off, hp.rule_off);
     vec(&d.rules, hp.rules);
+    d.rec = nullptr;
+    if (s->opt.form == SNP_FORM_OPT && !hp.rec.empty()) vec(&d.rec, hp.rec);
     vec(&d.orig, hp.perm);
     vec(&s->d_rule_base, hp.rule_base);
     vec(&d.C, hp.C0);
@@ -454,6 +456,7 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     s->uniform_rules = hp.uniform_rules;
     s->identity = hp.identity;
     s->compact = hp.compact;
+    s->compiled = s->opt.form == SNP_FORM_OPT && !hp.rec.empty();
     s->in_entries = (int64_t)hp.in_idx.size();
     s->out_entries = (int64_t)hp.out_idx.size();
     if (o.form == SNP_FORM_ELL) {
@@ -624,6 +627,7 @@ int snp_get_info(const snp_system* s, snp_info* info) {
     info->compact_rules = s->compact ? 1 : 0;
     info->e_bits = info->engine == SNP_ENGINE_TILED ? s->tiled.e_bits : resident_e_bits(s->max_p);
     info->step = s->host_step;
+    info->compiled_rules = s->compiled ? 1 : 0;
     return SNP_OK;
 }
 

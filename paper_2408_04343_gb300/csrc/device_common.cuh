@@ -261,6 +261,79 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
     return o;
 }
 
+// ---- compiled rule records (see compile_rules) ---------------------------
+// x mod L for L in 1..14 by multiplication (Lemire, Kaser and Kurz 2019):
+// with M = floor((2^64-1)/L) + 1, x mod L = hi64((M * x mod 2^64) * L).
+struct ModMagic {
+    unsigned long long m[16];
+    constexpr ModMagic() : m() {
+        for (int l = 1; l < 16; ++l) m[l] = ~0ull / (unsigned long long)l + 1ull;
+    }
+};
+__constant__ ModMagic kModMagic = ModMagic();
+
+template <int SEL>
+__device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, uint32_t st, unsigned long long k,
+                                                  uint32_t nid, uint64_t seed) {
+    SelOut o;
+    o.c_after = n;
+    o.emit = 0;
+    o.s = -1;
+    const uint32_t pend = st >> kPendShift;
+    if (pend != 0u) {
+        o.active = true;
+        if ((st & kDMask) == 0u) {
+            const uint32_t t = pend - 1u;
+            const uint32_t f = ((t < 2u ? rec.z : rec.w) >> (16u * (t & 1u))) & 0xffffu;
+            o.emit = (int32_t)((f >> 6) & 31u);
+            o.st = 0u;
+        } else {
+            o.st = st - 1u;
+        }
+        return o;
+    }
+    o.st = 0u;
+    o.active = false;
+    const uint32_t K = (rec.y >> 24) & 15u, L = rec.y >> 28;
+    uint32_t e = (uint32_t)n;
+    if (e >= K) {
+        const unsigned long long low = kModMagic.m[L] * (unsigned long long)(e - K);
+        e = K + (uint32_t)__umul64hi(low, (unsigned long long)L);
+    }
+    uint32_t mask = e < 8u ? (rec.x >> (4u * e)) & 15u : (rec.y >> (4u * (e - 8u))) & 15u;
+    if (mask == 0u) return o;
+    if (SEL == SNP_SELECT_PHILOX && (mask & (mask - 1u)) != 0u) {
+        const int32_t cnt = __popc(mask);
+        const Philox4 x = philox4x32_10((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
+                                        (uint32_t)(seed >> 32));
+        int32_t idx = (int32_t)(((unsigned long long)x.v[0] * (unsigned long long)cnt) >> 32);
+        for (; idx > 0; --idx) mask &= mask - 1u;
+    }
+    const uint32_t t = (uint32_t)(__ffs(mask) - 1);
+    const uint32_t f = ((t < 2u ? rec.z : rec.w) >> (16u * (t & 1u))) & 0xffffu;
+    const int32_t c = (int32_t)(f & 63u), p = (int32_t)((f >> 6) & 31u), d = (int32_t)(f >> 11);
+    o.active = true;
+    o.s = (int32_t)t;
+    o.c_after = n - c;
+    if (d == 0)
+        o.emit = p;
+    else
+        o.st = ((t + 1u) << kPendShift) | (uint32_t)(d - 1);
+    return o;
+}
+
+// The select phase of a slot through its compiled record when the system has
+// one, else through its rule table.
+template <bool COMPACT, int SEL>
+__device__ __forceinline__ SelOut select_slot(const DevSys& s, int32_t slot, int32_t n, uint32_t st,
+                                              unsigned long long k) {
+    if (s.rec)
+        return select_compiled<SEL>(__ldg(reinterpret_cast<const uint4*>(s.rec) + slot), n, st, k, neuron_id(s, slot),
+                                    s.seed);
+    return select_neuron<COMPACT, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), n, st, k, neuron_id(s, slot),
+                                       s.seed);
+}
+
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
     return *reinterpret_cast<const volatile uint32_t*>(p);
 }

@@ -27,9 +27,7 @@ __device__ __forceinline__ bool ell_select_slot(const DevSys& s, const EllSys& e
                                                 unsigned long long ks) {
     const uint32_t st = s.st[slot];
     const int32_t r0 = rule_lo(s, slot), r1 = rule_hi(s, slot);
-    const SelOut o = select_neuron<COMPACT, SEL>(s.rules, r0, r1, c, st, ks,
-                                                 SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u,
-                                                 s.seed);
+    const SelOut o = select_slot<COMPACT, SEL>(s, slot, c, st, ks);
     int32_t emitting = -1;  // local index of the rule that emits at ks
     if ((st >> kPendShift) != 0u && (st & kDMask) == 0u) emitting = (int32_t)(st >> kPendShift) - 1;
     else if (o.s >= 0 && o.emit > 0) emitting = o.s;

@@ -58,9 +58,7 @@ __device__ void run_resident(const DevSys& s, long long n, uint32_t* esm) {
         const int32_t slot = slice * kSlice + lane;
         int32_t emit = 0;
         if (slot < s.q) {
-            const SelOut o = select_neuron<COMPACT, SEL>(
-                s.rules, rule_lo(s, slot), rule_hi(s, slot), s.C[slot], s.st[slot], base,
-                SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
+            const SelOut o = select_slot<COMPACT, SEL>(s, slot, s.C[slot], s.st[slot], base);
             s.C[slot] = o.c_after;
             s.st[slot] = o.st;
             SNP_PICK(s.S, base)[slot] = o.s;
@@ -115,9 +113,7 @@ __device__ void run_resident(const DevSys& s, long long n, uint32_t* esm) {
             }
             int32_t emit = 0;
             if (do_sel && valid) {
-                const SelOut o = select_neuron<COMPACT, SEL>(
-                    s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, kg + 1ull,
-                    SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
+                const SelOut o = select_slot<COMPACT, SEL>(s, slot, c, st, kg + 1ull);
                 c = o.c_after;
                 s.st[slot] = o.st;
                 SNP_PICK(s.S, kg + 1ull)[slot] = o.s;

@@ -72,9 +72,7 @@ __global__ void __launch_bounds__(256) k_step_pull(DevSys s, int32_t t) {
             }
         }
         if (SELECT && valid) {
-            const SelOut o = select_neuron<COMPACT, SEL>(
-                s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks,
-                SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
+            const SelOut o = select_slot<COMPACT, SEL>(s, slot, c, st, ks);
             c = o.c_after;
             active = o.active;
             SNP_PICK(s.E, ks)[slot] = o.emit;
@@ -123,9 +121,7 @@ __global__ void __launch_bounds__(256) k_select_push(DevSys s, int32_t t) {
     const int32_t slot = slice * kSlice + lane;
     bool active = false;
     if (slice < s.nslices && slot < s.q) {
-        const SelOut o = select_neuron<COMPACT, SEL>(
-            s.rules, rule_lo(s, slot), rule_hi(s, slot), s.C[slot], s.st[slot], ks,
-            SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
+        const SelOut o = select_slot<COMPACT, SEL>(s, slot, s.C[slot], s.st[slot], ks);
         active = o.active;
         s.C[slot] = o.c_after;
         SNP_PICK(s.E, ks)[slot] = o.emit;

@@ -168,9 +168,7 @@ __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int
         }
         uint32_t emit = 0u;
         if (SELECT && valid) {
-            const SelOut o = select_neuron<COMPACT, SEL>(
-                s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks,
-                SEL == SNP_SELECT_PHILOX ? neuron_id(s, slot) : 0u, s.seed);
+            const SelOut o = select_slot<COMPACT, SEL>(s, slot, c, st, ks);
             c = o.c_after;
             active = o.active;
             emit = (uint32_t)o.emit;

@@ -226,6 +226,8 @@ int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int 
         }
     }
 
+    compile_rules(d, hp);
+
     hp->C0.resize(q);
     for (int32_t s = 0; s < q; ++s) hp->C0[s] = d->init_spikes[hp->perm[s]];
     return SNP_OK;
@@ -325,6 +327,58 @@ int pack_dense(const snp_desc* d, const HostPack& hp, std::vector<int32_t>* M) {
                 (*M)[(size_t)(row * q + hp.inv[d->syn_targets[e]])] = d->rule_p[r];
         }
     return SNP_OK;
+}
+
+static int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+bool compile_rules(const snp_desc* d, HostPack* hp) {
+    const int32_t q = hp->q;
+    hp->rec.clear();
+    if (hp->max_rules > 4) return false;
+    std::vector<uint32_t> rec((size_t)q * 4, 0u);
+    for (int32_t s = 0; s < q; ++s) {
+        const int32_t i = hp->perm[s];
+        const int64_t r0 = d->rule_offsets[i], R = d->rule_offsets[i + 1] - r0;
+        int64_t K = 1, L = 1;
+        for (int64_t t = 0; t < R; ++t) {
+            const int64_t r = r0 + t;
+            if (d->rule_c[r] >= 64 || d->rule_p[r] >= 32 || d->rule_d[r] >= 32) return false;
+            K = std::max<int64_t>(K, 1 + std::max<int64_t>(d->rule_k[r], d->rule_c[r]));
+            if (d->rule_j[r] > 0) {
+                L = L / gcd64(L, d->rule_j[r]) * d->rule_j[r];
+                if (L > 14) return false;
+            }
+        }
+        if (K + L > 14) return false;
+        uint64_t table = 0;
+        for (int64_t e = 0; e < K + L; ++e) {
+            const int64_t n = e;  // entries K.. stand for n = K + (n - K) mod L; n = e is such an n
+            uint32_t mask = 0;
+            for (int64_t t = 0; t < R; ++t) {
+                const int64_t r = r0 + t, k = d->rule_k[r], j = d->rule_j[r], c = d->rule_c[r];
+                const bool ok = n >= k && n >= c && (j == 0 ? n == k : (n - k) % j == 0);
+                if (ok) mask |= 1u << t;
+            }
+            table |= (uint64_t)mask << (4 * e);
+        }
+        uint32_t* w = rec.data() + (size_t)s * 4;
+        w[0] = (uint32_t)table;
+        w[1] = (uint32_t)((table >> 32) & 0xffffffu) | ((uint32_t)K << 24) | ((uint32_t)L << 28);
+        for (int64_t t = 0; t < R; ++t) {
+            const int64_t r = r0 + t;
+            const uint32_t f = (uint32_t)d->rule_c[r] | ((uint32_t)d->rule_p[r] << 6) | ((uint32_t)d->rule_d[r] << 11);
+            w[2 + t / 2] |= f << (16 * (t % 2));
+        }
+    }
+    hp->rec.swap(rec);
+    return true;
 }
 
 int tiled_e_bits(int max_p) {

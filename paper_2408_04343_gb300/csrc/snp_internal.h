@@ -70,6 +70,7 @@ struct DevSys {
     uint64_t seed;
     int32_t select;
     int32_t max_p;
+    const void* rec;           // [q] 16-byte compiled rule records, or NULL (see compile_rules)
     int32_t rules_per_neuron;  // > 0: every neuron has this many rules (rule r0 = slot * R)
     int32_t identity;          // 1: slot order is the caller's order (orig[slot] = slot)
 };
@@ -92,7 +93,23 @@ struct HostPack {
     std::vector<int32_t> out_ptr;     // push only
     std::vector<int32_t> out_idx;
     std::vector<int32_t> C0;          // slot order
+    std::vector<uint32_t> rec;        // compiled rule records, 4 words per slot (empty: not compiled)
 };
+
+// Compiled rule records.  For a neuron with at most four rules, which rules
+// apply depends on n only through min(n, K) and (n - K) mod L once n >= K,
+// with K = 1 + the largest k or c of its rules and L the least common
+// multiple of its nonzero j: above K every exact rule (j = 0) fails and every
+// other rule's test (n - k) mod j = 0 repeats with period L.  When K + L <= 14
+// the whole applicability function fits a table of K + L four-bit masks:
+//   word 0: masks of table entries 0..7 (entry e in bits 4e..4e+3);
+//   word 1: masks of entries 8..13, K in bits 24..27, L in bits 28..31;
+//   words 2-3: per rule t, 16 bits (c: 6, p: 5, d: 5) at bits 16(t mod 2) of
+//   word 2 + t/2.
+// Entry e is the mask for n = e when e < K and for n = K + ((n - K) mod L)
+// otherwise.  A system is compiled only if every neuron fits (c < 64,
+// p < 32, d < 32); then one 16-byte load replaces the per-rule tests.
+bool compile_rules(const snp_desc* d, HostPack* hp);
 
 constexpr int kTiledMaxSub = 8;  // target windows per CTA of the tiled engine
 

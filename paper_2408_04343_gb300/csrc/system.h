@@ -54,6 +54,7 @@ struct snp_system {
     int64_t m = 0, nsyn = 0;
     int32_t max_p = 0, max_rules = 0;
     bool compact = true;
+    bool compiled = false;     // compiled rule records uploaded (OPT form)
     int32_t uniform_rules = 0;
     bool identity = false;
     int64_t in_entries = 0, out_entries = 0, rule_words = 0;

@@ -55,7 +55,8 @@ class snp_info(ct.Structure):
                 ("engine", ct.c_int32), ("m", ct.c_int64), ("num_syn", ct.c_int64),
                 ("in_entries", ct.c_int64), ("out_entries", ct.c_int64), ("rule_words", ct.c_int64),
                 ("device_bytes", ct.c_int64), ("max_rules", ct.c_int32), ("max_p", ct.c_int32),
-                ("compact_rules", ct.c_int32), ("e_bits", ct.c_int32), ("step", ct.c_uint64)]
+                ("compact_rules", ct.c_int32), ("e_bits", ct.c_int32), ("step", ct.c_uint64),
+                ("compiled_rules", ct.c_int32)]
 
 
 class snp_device_system(ct.Structure):

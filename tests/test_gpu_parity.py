@@ -76,6 +76,38 @@ def test_small_1k_push_every_step():
     compare(d, 60, oracle.PHILOX, 5, prop=libsnp.SNP_PROP_PUSH)
 
 
+def _rule_shape(name):
+    """Rule tables on both sides of the compiled-record limits (at most four
+    rules per neuron, K + L <= 14, c < 64, p < 32, d < 32)."""
+    if name == "compiled_edge":
+        # k <= 5 and j in {0, 1, 2, 4, 8}: K <= 6, L <= 8, K + L up to 14
+        d = synth.random_system(6000, 11, outdeg=(2, 12), rules=(2, 4), k_range=(1, 5), d_range=(0, 6),
+                                spikes=(0, 3000))
+        fire = d.rule_j > 0
+        rng = np.random.default_rng(12)
+        d.rule_j[:] = np.where(fire | (d.rule_p > 0), rng.choice([0, 1, 2, 4, 8], size=d.rule_j.size), 0)
+        return d, True
+    if name == "wide_k":
+        return synth.random_system(6000, 13, outdeg=(2, 12), rules=(2, 4), k_range=(1, 12), j_range=(0, 7),
+                                   d_range=(0, 6), spikes=(0, 3000)), False
+    if name == "many_rules":
+        return synth.random_system(6000, 14, outdeg=(2, 12), rules=(5, 6), d_range=(0, 4), spikes=(0, 40)), False
+    if name == "long_delay":
+        return synth.random_system(6000, 15, outdeg=(2, 12), rules=(3, 4), d_range=(0, 40), spikes=(0, 40)), False
+    raise ValueError(name)
+
+
+@pytest.mark.parametrize("engine", ["launch", "resident", "tiled"])
+@pytest.mark.parametrize("shape", ["compiled_edge", "wide_k", "many_rules", "long_delay"])
+def test_compiled_rule_records_and_fallback(engine, shape):
+    d, compiled = _rule_shape(shape)
+    gs = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, engine=ENGINES[engine])
+    assert gs.info().compiled_rules == int(compiled)
+    gs.close()
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        compare(d, 48, mode, 31 + len(shape), engine=engine, check_every=False, chunks=(7, 13))
+
+
 @pytest.mark.parametrize("engine", ["launch", "resident", "tiled"])
 def test_chunked_calls_and_graphs(engine):
     """Calls of many sizes (crossing the captured-graph chunk length)."""
