@@ -128,6 +128,7 @@ void build_plan(snp_system* s, std::vector<Piece>& plan) {
         tl.G = tp.G;
         tl.acc_words = tp.acc_words;
         tl.src_bits = tp.src_bits;
+        tl.pairs = tp.pairs;
         vec(&tl.sub, tp.sub);
         vec(&tl.ent, tp.ent);
         vec(&tl.cta_lo, tp.cta_lo);

@@ -334,6 +334,17 @@ __device__ __forceinline__ SelOut select_slot(const DevSys& s, int32_t slot, int
                                        s.seed);
 }
 
+// Programmatic dependent launch: wait until the grids this launch depends on
+// have finished and their writes are visible; let the next launch on the
+// stream start its own prologue.  Without the launch attribute both are
+// no-ops.
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
     return *reinterpret_cast<const volatile uint32_t*>(p);
 }

@@ -37,7 +37,7 @@ int resident_max_smem();
 
 // Tiled engine (kernels_tiled.cu): device view of a TiledPack.
 struct TiledSys {
-    int32_t P, part_words, e_bits, G, acc_words, src_bits;
+    int32_t P, part_words, e_bits, G, acc_words, src_bits, pairs;
     const int32_t* sub;     // [G][kTiledMaxSub+1] window starts (words, multiples of 4); CTA g*P+h
     const uint32_t* ent;    // (dst_local << src_bits) | src_local
     const int32_t* cta_lo;  // [G/P+1] slice ranges

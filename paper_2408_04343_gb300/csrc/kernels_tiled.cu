@@ -13,8 +13,9 @@
 //    group of in-edge words of its range from h edge-parallel (16-byte vector loads, no
 //    per-neuron bookkeeping): each word names a local target slot and a
 //    source, whose emission is added to the target's shared-memory
-//    accumulator (words are sorted by target, so runs of one target within
-//    a load are summed first).  The accumulators become partition h's
+//    accumulator (words are sorted by target; one reduction per aligned pair
+//    of words in the paired layout, per run of equal targets within a load
+//    otherwise).  The accumulators become partition h's
 //    in-flow vector of step k; the select launch sums the P of them.
 //  * k_tiled_select -- full occupancy, one warp per slice: finishes step k
 //    (C_{k+1} = C' + [open] * in-flow), selects step k+1 and writes the
@@ -52,103 +53,243 @@ __device__ __forceinline__ void pk_put_slice(uint32_t* e, int32_t slice, int lan
     if (lane % per == 0) e[slice * EB + lane / per] = w;
 }
 
-// Four target-sorted words of one window: the emissions of consecutive words
-// with the same target are summed in registers and added to that target
-// (window base + dst) with one atomic, without branches: r_i is the running
-// sum of the run that ends at word i, flushed when the next word's target
-// differs (or at the last word).
-template <int EB>
-__device__ __forceinline__ void edges4(const uint32_t* __restrict__ Esm, int* acc, const uint4& q, uint32_t base,
-                                       uint32_t smask, int sbits) {
-    const uint32_t v0 = pk_get<EB>(Esm, q.x & smask), v1 = pk_get<EB>(Esm, q.y & smask);
-    const uint32_t v2 = pk_get<EB>(Esm, q.z & smask), v3 = pk_get<EB>(Esm, q.w & smask);
-    const uint32_t d0 = q.x >> sbits, d1 = q.y >> sbits, d2 = q.z >> sbits, d3 = q.w >> sbits;
-    const bool s1 = d1 == d0, s2 = d2 == d1, s3 = d3 == d2;
-    const uint32_t r0 = v0;
-    const uint32_t r1 = (s1 ? r0 : 0u) + v1;
-    const uint32_t r2 = (s2 ? r1 : 0u) + v2;
-    const uint32_t r3 = (s3 ? r2 : 0u) + v3;
-    if (!s1 && r0) atomicAdd(acc + base + d0, (int)r0);
-    if (!s2 && r1) atomicAdd(acc + base + d1, (int)r1);
-    if (!s3 && r2) atomicAdd(acc + base + d2, (int)r2);
-    if (r3) atomicAdd(acc + base + d3, (int)r3);
+// ---- shared-memory access by 32-bit shared addresses ----------------------
+// The gather's inner loop is issue-bound, so its shared-memory reads and
+// reductions are written with 32-bit shared-window addresses (no generic
+// 64-bit address arithmetic) and conditional reductions are predicated
+// rather than branched around.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void red_add(uint32_t a, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
+__device__ __forceinline__ void red_add_if(uint32_t a, uint32_t v, bool p) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.u32 q, %2, 0;\n\t"
+        "@q red.shared.add.u32 [%0], %1;\n\t}"
+        :
+        : "r"(a), "r"(v), "r"((uint32_t)p));
 }
 
-// Target window of the 16-byte word group at index i (monotone in i).
-__device__ __forceinline__ uint32_t window_of(const int32_t* wb, int32_t i, int& k) {
-    while (k + 1 < kTiledMaxSub && i >= wb[k + 1]) ++k;
-    return (uint32_t)k;
+// Emission of the source named by the low bits of entry word w (the bits
+// above the source field do not disturb it): word (src / per) of the packed
+// vector at shared address esm, field src mod per.  `amask` keeps the
+// source's word index, already scaled to a byte offset.
+template <int EB>
+__device__ __forceinline__ uint32_t emission_of(uint32_t esm, uint32_t w, uint32_t amask) {
+    constexpr uint32_t per = 32u / EB;  // emissions per 32-bit word
+    uint32_t off;
+    if constexpr (per >= 4) {
+        off = (w >> (__builtin_ctz(per) - 2)) & amask;
+    } else {
+        off = (w << (2 - __builtin_ctz(per))) & amask;
+    }
+    const uint32_t word = lds_u32(esm + off);
+    // rotate by (src mod per) * EB: the shift count is taken mod 32
+    return __funnelshift_r(word, word, w * (uint32_t)EB) & ((1u << EB) - 1u);
+}
+
+// One 16-byte load of a window, four words sorted by target; abase =
+// shared address of the window's first accumulator.
+//  PAIRS: two pairs of words, each pair one target (its window-relative slot
+//  in the high bits of both words) and two sources; each pair's emissions
+//  are added to its target with one shared-memory reduction.
+//  Otherwise: the emissions of consecutive words with the same target are
+//  summed in registers, without branches (r_i is the running sum of the run
+//  that ends at word i), and a run is added when the next word's target
+//  differs or at the last word.
+template <int EB, bool PAIRS>
+__device__ __forceinline__ void edges4(uint32_t esm, uint32_t abase, const uint4& q, uint32_t amask, int sbits) {
+    const uint32_t v0 = emission_of<EB>(esm, q.x, amask), v1 = emission_of<EB>(esm, q.y, amask);
+    const uint32_t v2 = emission_of<EB>(esm, q.z, amask), v3 = emission_of<EB>(esm, q.w, amask);
+    if constexpr (PAIRS) {
+        red_add(abase + (q.x >> sbits) * 4u, v0 + v1);
+        red_add(abase + (q.z >> sbits) * 4u, v2 + v3);
+    } else {
+        const uint32_t d0 = q.x >> sbits, d1 = q.y >> sbits, d2 = q.z >> sbits, d3 = q.w >> sbits;
+        const bool s1 = d1 == d0, s2 = d2 == d1, s3 = d3 == d2;
+        const uint32_t r0 = v0;
+        const uint32_t r1 = (s1 ? r0 : 0u) + v1;
+        const uint32_t r2 = (s2 ? r1 : 0u) + v2;
+        const uint32_t r3 = (s3 ? r2 : 0u) + v3;
+        red_add_if(abase + d0 * 4u, r0, !s1);
+        red_add_if(abase + d1 * 4u, r1, !s2);
+        red_add_if(abase + d2 * 4u, r2, !s3);
+        red_add(abase + d3 * 4u, r3);
+    }
+}
+
+// ---- bulk copy of a partition's emissions into shared memory -------------
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Waits for phase 0 of the barrier, at most `limit` polls; true when it completed.
+__device__ __forceinline__ bool mbar_wait0(uint32_t bar, int limit) {
+    for (int it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+constexpr int kBulkChunk = 32768;       // bytes per bulk copy instruction
+constexpr int kWaitPolls = 1 << 20;     // each poll may suspend for a while; ~seconds in all
+
+// One batch of D 16-byte loads of a thread (vector i0 + u * stride for u <
+// D, those below g1).  The window index k only moves forward; a batch inside
+// one window (the common case) takes its base once.
+template <int EB, bool PAIRS, int D>
+__device__ __forceinline__ void gather_batch(const uint4 (&x)[D], int32_t i0, int32_t stride, int32_t g1,
+                                             const int32_t* wb, int& k, uint32_t esm, uint32_t acc0, int db,
+                                             uint32_t amask, int sbits) {
+    const int32_t last = i0 + (D - 1) * stride;
+    if (last < g1 && last < wb[k + 1]) {  // k <= kTiledMaxSub - 1 and wb[kTiledMaxSub] = g1
+        const uint32_t abase = acc0 + ((uint32_t)k << db) * 4u;
+#pragma unroll
+        for (int u = 0; u < D; ++u) edges4<EB, PAIRS>(esm, abase, x[u], amask, sbits);
+    } else {
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+            const int32_t iu = i0 + u * stride;
+            if (iu < g1) {
+                int ku = k;
+                while (ku + 1 < kTiledMaxSub && iu >= wb[ku + 1]) ++ku;
+                edges4<EB, PAIRS>(esm, acc0 + ((uint32_t)ku << db) * 4u, x[u], amask, sbits);
+            }
+        }
+    }
+    const int32_t inext = i0 + D * stride;
+    while (k + 1 < kTiledMaxSub && inext >= wb[k + 1]) ++k;
+}
+
+template <int D>
+__device__ __forceinline__ void load_batch(uint4 (&x)[D], const uint4* ent, int32_t i0, int32_t stride, int32_t g1) {
+#pragma unroll
+    for (int u = 0; u < D; ++u)
+        if (i0 + u * stride < g1) x[u] = ld_stream_v4(ent + i0 + u * stride);
 }
 
 // In-flow of step kg = base + t into tl.inflow (partition h's share).
-template <int EB>
+// Launched as a programmatic dependent of the select launch before it: the
+// part before grid_dependency_wait touches only the constant layout (window
+// bounds, the first entry vectors) and the CTA's own shared memory, so it
+// overlaps the end of that launch.
+template <int EB, bool PAIRS>
 __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl, int32_t t) {
-    extern __shared__ uint32_t smem[];
+    constexpr int D = 4;  // vectors per batch; two batches in registers
+    extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int32_t wb[kTiledMaxSub + 1];
+    __shared__ __align__(8) unsigned long long bar;
     uint32_t* Esm = smem;                                              // part_words + a zero word
     int* acc = reinterpret_cast<int*>(smem + tl.part_words + 4);
+    const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
+    const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
+    const uint32_t ebar = smem_u32(&bar);
+    if (threadIdx.x <= kTiledMaxSub)
+        wb[threadIdx.x] = __ldg(tl.sub + (size_t)blockIdx.x * (kTiledMaxSub + 1) + threadIdx.x) / 4;
+    if (threadIdx.x < 4) Esm[tl.part_words + threadIdx.x] = 0u;
+    if (threadIdx.x == 0) mbar_init(ebar);
+    for (int i = threadIdx.x; i < tl.acc_words; i += blockDim.x) acc[i] = 0;
+    __syncthreads();
+    const int sbits = tl.src_bits;
+    const int db = 32 - sbits;
+    constexpr uint32_t per = 32u / EB;
+    const uint32_t smask = (1u << sbits) - 1u;
+    const uint32_t amask = (per >= 4 ? (smask >> (__builtin_ctz(per) - 2)) : (smask << (2 - __builtin_ctz(per)))) & ~3u;
+    const uint32_t esm = smem_u32(Esm);
+    const uint32_t acc0 = smem_u32(acc);
+    const uint4* ent = reinterpret_cast<const uint4*>(tl.ent);
+    const int32_t g1 = wb[kTiledMaxSub];
+    const int32_t stride = blockDim.x;
+    int32_t i = wb[0] + threadIdx.x;
+    uint4 qa[D], qb[D];
+    load_batch(qa, ent, i, stride, g1);
+
+    grid_dependency_wait();  // the select launch that wrote E_k has finished
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
     if (step_blocked(fl, s.step, kg)) return;
+    allow_dependents();
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
-    const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
-    const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
-    if (threadIdx.x <= kTiledMaxSub) wb[threadIdx.x] = __ldg(tl.sub + (size_t)blockIdx.x * (kTiledMaxSub + 1) + threadIdx.x) / 4;
-    if (threadIdx.x < 4) Esm[tl.part_words + threadIdx.x] = 0u;
-    for (int i = threadIdx.x; i < tl.acc_words; i += blockDim.x) acc[i] = 0;
-    const uint32_t smask = (1u << tl.src_bits) - 1u;
-    const int sbits = tl.src_bits;
-    const int db = 32 - sbits;
-    const uint4* ent = reinterpret_cast<const uint4*>(tl.ent);
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(SNP_PICK(tl.Eg, kg) + (size_t)h * tl.part_words);
-        uint4* dst = reinterpret_cast<uint4*>(Esm);
-        for (int i = threadIdx.x; i < tl.part_words / 4; i += blockDim.x) dst[i] = __ldcg(src + i);
-        __syncthreads();
-        const int32_t g1 = wb[kTiledMaxSub];
-        const int32_t stride = blockDim.x;
-        int32_t i = wb[0] + threadIdx.x;
-        // eight independent 16-byte loads per thread in flight, then their
-        // shared-memory work; the window index only moves forward
-        int k = 0;
-        for (; i + 7 * stride < g1; i += 8 * stride) {
-            uint4 q[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) q[u] = ld_stream_v4(ent + i + u * stride);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                int ku = k;
-                const uint32_t base = window_of(wb, i + u * stride, ku) << db;
-                edges4<EB>(Esm, acc, q[u], base, smask, sbits);
-            }
-            window_of(wb, i + 7 * stride, k);
-        }
-        for (; i < g1; i += stride) {
-            const uint4 a = ld_stream_v4(ent + i);
-            edges4<EB>(Esm, acc, a, window_of(wb, i, k) << db, smask, sbits);
-        }
-        __syncthreads();
+    const uint32_t ebytes = (uint32_t)tl.part_words * 4u;
+    if (threadIdx.x == 0) {
+        const char* src = reinterpret_cast<const char*>(SNP_PICK(tl.Eg, kg) + (size_t)h * tl.part_words);
+        mbar_expect_tx(ebar, ebytes);
+        for (uint32_t o = 0; o < ebytes; o += kBulkChunk)
+            bulk_g2s(esm + o, src + o, min((uint32_t)kBulkChunk, ebytes - o), ebar);
     }
+    if (!mbar_wait0(ebar, kWaitPolls)) {
+        atomicOr(fl + kFlagTimeout, 1u);
+        mbar_wait0(ebar, kWaitPolls);  // let the copy land before the CTA's shared memory goes away
+        return;
+    }
+    // two batches in flight: the next batch loads while this one is added
+    int k = 0;
+    while (k + 1 < kTiledMaxSub && i >= wb[k + 1]) ++k;
+    for (;;) {
+        int32_t inext = i + D * stride;
+        load_batch(qb, ent, inext, stride, g1);
+        gather_batch<EB, PAIRS, D>(qa, i, stride, g1, wb, k, esm, acc0, db, amask, sbits);
+        if (inext >= g1) break;
+        i = inext;
+        inext = i + D * stride;
+        load_batch(qa, ent, inext, stride, g1);
+        gather_batch<EB, PAIRS, D>(qb, i, stride, g1, wb, k, esm, acc0, db, amask, sbits);
+        if (inext >= g1) break;
+        i = inext;
+    }
+    __syncthreads();
     const int32_t slot0 = lo * kSlice;
-    const int32_t nloc = (hi - lo) * kSlice;
-    int32_t* out = tl.inflow + (size_t)h * s.nslices * kSlice + slot0;
-    for (int i = threadIdx.x; i < nloc; i += blockDim.x) out[i] = acc[i];
+    const int32_t nloc = (hi - lo) * kSlice;  // a multiple of 32
+    uint4* out = reinterpret_cast<uint4*>(tl.inflow + (size_t)h * s.nslices * kSlice + slot0);
+    const uint4* a4 = reinterpret_cast<const uint4*>(acc);
+    for (int j = threadIdx.x; j < nloc / 4; j += blockDim.x) out[j] = a4[j];
 }
 
 // Finishes step kg (GATHER: adds the in-flow to open neurons) and selects
-// step ks (SELECT), one warp per slice.
+// step ks (SELECT), one warp per slice.  Launched as a programmatic
+// dependent of the launch before it: the compiled rule record (constant) is
+// loaded before grid_dependency_wait.
 template <bool GATHER, bool SELECT, bool COMPACT, int SEL, int EB>
 __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int32_t t) {
-    uint32_t* fl = s.flags;
-    const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
-    const unsigned long long ks = GATHER ? kg + 1ull : kg;
-    if (call_halted(fl)) return;
     const int lane = threadIdx.x & 31;
     const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int32_t slot = slice * kSlice + lane;
+    const bool valid = slice < s.nslices && slot < s.q;
+    const bool has_rec = s.rec != nullptr;
+    uint4 rec = make_uint4(0u, 0u, 0u, 0u);
+    if (SELECT && valid && has_rec) rec = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
+
+    grid_dependency_wait();
+    uint32_t* fl = s.flags;
+    if (call_halted(fl)) return;
+    allow_dependents();
+    const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
+    const unsigned long long ks = GATHER ? kg + 1ull : kg;
     bool active = false;
     if (slice < s.nslices) {
-        const bool valid = slot < s.q;
         int32_t c = 0;
         uint32_t st = 0u;
         if (valid) {
@@ -168,7 +309,9 @@ __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int
         }
         uint32_t emit = 0u;
         if (SELECT && valid) {
-            const SelOut o = select_slot<COMPACT, SEL>(s, slot, c, st, ks);
+            const SelOut o = has_rec ? select_compiled<SEL>(rec, c, st, ks, neuron_id(s, slot), s.seed)
+                                     : select_neuron<COMPACT, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c,
+                                                                   st, ks, neuron_id(s, slot), s.seed);
             c = o.c_after;
             active = o.active;
             emit = (uint32_t)o.emit;
@@ -181,21 +324,37 @@ __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int
     if (SELECT) raise_step_activity(fl, ks, active);
 }
 
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous launch on the stream is finishing, and waits for it with
+// grid_dependency_wait before touching anything that launch writes.
+template <typename... P, typename... A>
+static cudaError_t launch_dependent(void (*fn)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                                    A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, args...);
+}
+
 template <int EB>
 static cudaError_t launch_gather_eb(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st, size_t smem,
                                     int threads) {
-    auto fn = k_tiled_gather<EB>;
+    auto fn = tl.pairs ? k_tiled_gather<EB, true> : k_tiled_gather<EB, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<tl.G, threads, smem, st>>>(s, tl, t);
-    return cudaGetLastError();
+    return launch_dependent(fn, (unsigned)tl.G, (unsigned)threads, smem, st, s, tl, t);
 }
 
 template <bool G, bool S, bool C, int SEL, int EB>
 static cudaError_t launch_select_t(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st) {
-    const dim3 grid((unsigned)((s.nslices + 7) / 8));
-    k_tiled_select<G, S, C, SEL, EB><<<grid, 256, 0, st>>>(s, tl, t);
-    return cudaGetLastError();
+    return launch_dependent(k_tiled_select<G, S, C, SEL, EB>, (unsigned)((s.nslices + 7) / 8), 256u, 0, st, s, tl, t);
 }
 
 template <int EB>

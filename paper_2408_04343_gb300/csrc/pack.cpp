@@ -486,9 +486,23 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     tp->src_bits = src_bits;
     tp->cta_lo = cta_lo;
     const int db = 32 - src_bits;
+    // paired layout unless too many (target, partition) groups have an odd
+    // number of words
+    {
+        int64_t odd = 0;
+        for (int32_t s = 0; s < q; ++s) {
+            auto b = isrc.begin() + ioff[s], e = isrc.begin() + ioff[s + 1];
+            for (int h = 0; h < P && b != e; ++h) {
+                auto m = std::lower_bound(b, e, (int32_t)std::min<int64_t>(q, (int64_t)(h + 1) * part_size));
+                odd += (m - b) & 1;
+                b = m;
+            }
+        }
+        tp->pairs = (double)odd <= kTiledPairSlack * (double)std::max<int64_t>(1, hp.nsyn) ? 1 : 0;
+    }
     tp->sub.assign((size_t)G * (kTiledMaxSub + 1), 0);
     tp->ent.clear();
-    tp->ent.reserve((size_t)hp.nsyn + (size_t)G * kTiledMaxSub * 4);
+    tp->ent.reserve((size_t)hp.nsyn + (size_t)q + (size_t)G * kTiledMaxSub * 4);
     const uint32_t pad = (uint32_t)part_size;  // target 0 of the window, source = the zero word
     std::vector<int64_t> cur(kSlice), end(kSlice);
     for (int g = 0; g < NR; ++g) {
@@ -511,9 +525,9 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
                     end[l] = std::lower_bound(b, e, hi_src) - isrc.begin();
                     maxn = std::max(maxn, end[l] - cur[l]);
                 }
-                // target-major: the words of one target are adjacent, so a
-                // 16-byte load mostly holds one or two targets and the kernel
-                // merges their emissions in registers before one atomic each
+                // target-major; in the paired layout each target's words are
+                // padded to an even count, so a 16-byte load holds two
+                // (target, two sources) pairs
                 (void)maxn;
                 const uint32_t local0 = (uint32_t)(sl - cta_lo[g]) * kSlice;
                 for (int l = 0; l < kSlice; ++l) {
@@ -525,6 +539,7 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
                     const uint32_t dst = local & (((uint32_t)1 << db) - 1u);
                     for (int64_t x = cur[l]; x < end[l]; ++x)
                         tp->ent.push_back((dst << src_bits) | (uint32_t)(isrc[(size_t)x] - lo_src));
+                    if (tp->pairs && ((end[l] - cur[l]) & 1)) tp->ent.push_back((dst << src_bits) | pad);  // complete the pair
                 }
             }
             while (tp->ent.size() % 4) tp->ent.push_back(pad);

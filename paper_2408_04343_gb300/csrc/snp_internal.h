@@ -112,6 +112,7 @@ struct HostPack {
 bool compile_rules(const snp_desc* d, HostPack* hp);
 
 constexpr int kTiledMaxSub = 8;  // target windows per CTA of the tiled engine
+constexpr double kTiledPairSlack = 0.125;  // largest padding of the paired layout
 
 // Layout of the tiled engine (shared-memory emissions, source partitions).
 // Sources are cut into P partitions of part_size slots so that one
@@ -123,10 +124,16 @@ constexpr int kTiledMaxSub = 8;  // target windows per CTA of the tiled engine
 // for a whole range, so the group is cut into up to kTiledMaxSub target
 // windows of 2^(32 - src_bits) slots; dst is relative to its window and the
 // kernel knows the window from the word's position (window boundaries in
-// `sub`).  Windows are padded to 16 bytes with words whose source is
-// part_size, which reads a zero word, so they load as 16-byte vectors.
-// Inside a window the words are sorted by target, so the words of one
-// 16-byte load mostly share a target and can be summed before the add.
+// `sub`).  Inside a window the words are sorted by target.  In the paired
+// layout each target's words are padded to an even count, so every aligned
+// pair of words shares one target and the kernel adds the pair's two
+// emissions with one reduction; it is used when the padding adds at most
+// kTiledPairSlack of the words (systems whose targets mostly have one
+// in-edge per partition would nearly double).  Otherwise the words of one
+// target are merely adjacent and the kernel merges runs of equal targets
+// within a 16-byte load.  Pad words have source part_size, which reads a
+// zero word; windows are padded to 16 bytes with them so they load as
+// 16-byte vectors.
 struct TiledPack {
     int e_bits = 0;          // bits per emission (2, 4, 8, 16)
     int P = 0;               // partitions
@@ -136,6 +143,7 @@ struct TiledPack {
     int max_slices = 0;      // most slices given to one CTA
     int acc_words = 0;       // shared in-flow accumulators per CTA (+ dummy)
     int src_bits = 0;        // low bits of an entry holding the source (0..part_size)
+    int pairs = 0;           // 1: paired layout (every aligned word pair has one target)
     std::vector<int32_t> sub;     // [G][kTiledMaxSub+1] window starts in ent (CTA g*P+h: range g, partition h)
     std::vector<uint32_t> ent;    // entries
     std::vector<int32_t> cta_lo;  // [G/P + 1] first slice of each range

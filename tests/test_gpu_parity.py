@@ -108,6 +108,19 @@ def test_compiled_rule_records_and_fallback(engine, shape):
         compare(d, 48, mode, 31 + len(shape), engine=engine, check_every=False, chunks=(7, 13))
 
 
+@pytest.mark.parametrize("outdeg,paired", [((1, 2), False), ((12, 24), True)])
+def test_tiled_paired_and_run_layouts(outdeg, paired):
+    """The tiled gather pads each target's in-edges to pairs only when that
+    adds at most 1/8 of the words; low in-degree systems keep the run-merging
+    layout.  One system of each kind (one source partition at this size)."""
+    d = synth.random_system(50000, 21 + outdeg[0], outdeg=outdeg, rules=(3, 4), d_range=(0, 5), spikes=(0, 20))
+    indeg = np.bincount(d.syn_targets, minlength=d.q)
+    odd_frac = float((indeg & 1).sum()) / d.num_syn
+    assert (odd_frac <= 0.125) == paired
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        compare(d, 40, mode, 5 + outdeg[0], engine="tiled", check_every=False, chunks=(9, 31))
+
+
 @pytest.mark.parametrize("engine", ["launch", "resident", "tiled"])
 def test_chunked_calls_and_graphs(engine):
     """Calls of many sizes (crossing the captured-graph chunk length)."""
