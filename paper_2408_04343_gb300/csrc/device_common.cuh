@@ -29,8 +29,10 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
     constexpr uint32_t kBumpA = 0x9E3779B9u, kBumpB = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hiA = __umulhi(kMulA, c0), loA = kMulA * c0;
-        const uint32_t hiB = __umulhi(kMulB, c2), loB = kMulB * c2;
+        const unsigned long long pA = (unsigned long long)kMulA * c0;  // one wide multiply each
+        const unsigned long long pB = (unsigned long long)kMulB * c2;
+        const uint32_t hiA = (uint32_t)(pA >> 32), loA = (uint32_t)pA;
+        const uint32_t hiB = (uint32_t)(pB >> 32), loB = (uint32_t)pB;
         const uint32_t n0 = hiB ^ c1 ^ key0;
         const uint32_t n2 = hiA ^ c3 ^ key1;
         c0 = n0;
@@ -359,14 +361,15 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
 // requests on one L2 line.  The activity word of step k is never written by
 // the launch that reads it, and kFlagHalted is written in a launch only when
 // that launch's activity word is clear, so a stale read cannot change what a
-// CTA decides.
+// CTA decides.  The reads go to L2 (ld.global.cg): launches may overlap the
+// end of the launch before them, and L2 is where its writes are visible.
 
 // Block-uniform: true if the launch finishing step kg must return at once.
 __device__ __forceinline__ bool step_blocked(uint32_t* fl, unsigned long long* steps, unsigned long long kg) {
     __shared__ int s_blocked;
     if (threadIdx.x == 0) {
-        int b = __ldg(fl + kFlagHalted) != 0u;
-        if (!b && __ldg(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
+        int b = __ldcg(fl + kFlagHalted) != 0u;
+        if (!b && __ldcg(fl + kFlagAct0 + (int)(kg % 3ull)) == 0u) {
             b = 1;
             if (blockIdx.x == 0 && blockIdx.y == 0) {
                 steps[kStepHalt] = kg;
@@ -383,7 +386,7 @@ __device__ __forceinline__ bool step_blocked(uint32_t* fl, unsigned long long* s
 // Block-uniform: true if an earlier launch of this call found a fixed point.
 __device__ __forceinline__ bool call_halted(const uint32_t* fl) {
     __shared__ int s_halted;
-    if (threadIdx.x == 0) s_halted = __ldg(fl + kFlagHalted) != 0u;
+    if (threadIdx.x == 0) s_halted = __ldcg(fl + kFlagHalted) != 0u;
     __syncthreads();
     return s_halted != 0;
 }
@@ -393,7 +396,7 @@ __device__ __forceinline__ bool call_halted(const uint32_t* fl) {
 __device__ __forceinline__ void raise_step_activity(uint32_t* fl, unsigned long long ks, bool active) {
     if (__syncthreads_or(active) && threadIdx.x == 0) {
         uint32_t* a = fl + kFlagAct0 + (int)(ks % 3ull);
-        if (__ldg(a) == 0u) *reinterpret_cast<volatile uint32_t*>(a) = 1u;
+        if (__ldcg(a) == 0u) *reinterpret_cast<volatile uint32_t*>(a) = 1u;
     }
 }
 

@@ -269,56 +269,85 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
 }
 
 // Finishes step kg (GATHER: adds the in-flow to open neurons) and selects
-// step ks (SELECT), one warp per slice.  Launched as a programmatic
-// dependent of the launch before it: the compiled rule record (constant) is
-// loaded before grid_dependency_wait.
-template <bool GATHER, bool SELECT, bool COMPACT, int SEL, int EB>
+// step ks (SELECT); one warp per NS consecutive slices.  Launched as a
+// programmatic dependent of the launch before it: the compiled rule records
+// (constant) are loaded before grid_dependency_wait, and every load of the
+// step is issued before the fixed-point test, whose flag read would
+// otherwise add a round trip to memory in front of them.
+template <bool GATHER, bool SELECT, bool COMPACT, int SEL, int EB, int NS>
 __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int32_t t) {
     const int lane = threadIdx.x & 31;
-    const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int32_t slot = slice * kSlice + lane;
-    const bool valid = slice < s.nslices && slot < s.q;
+    const int32_t sl0 = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * NS;
     const bool has_rec = s.rec != nullptr;
-    uint4 rec = make_uint4(0u, 0u, 0u, 0u);
-    if (SELECT && valid && has_rec) rec = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
+    uint4 rec[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const int32_t slot = (sl0 + j) * kSlice + lane;
+        rec[j] = make_uint4(0u, 0u, 0u, 0u);
+        if (SELECT && has_rec && sl0 + j < s.nslices && slot < s.q)
+            rec[j] = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
+    }
 
     grid_dependency_wait();
     uint32_t* fl = s.flags;
-    if (call_halted(fl)) return;
-    allow_dependents();
+    const size_t pstride = (size_t)s.nslices * kSlice;
+    int32_t c[NS];
+    uint32_t st[NS];
+    long long in[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const int32_t slot = (sl0 + j) * kSlice + lane;
+        const bool valid = sl0 + j < s.nslices && slot < s.q;
+        c[j] = valid ? s.C[slot] : 0;
+        st[j] = valid ? s.st[slot] : 0u;
+        in[j] = 0;
+        if (GATHER && valid) {
+            in[j] = tl.inflow[slot];
+            if (tl.P > 1) in[j] += tl.inflow[pstride + slot];
+        }
+    }
+    if (GATHER && tl.P > 2) {
+        for (int h = 2; h < tl.P; ++h) {
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                const int32_t slot = (sl0 + j) * kSlice + lane;
+                if (sl0 + j < s.nslices && slot < s.q) in[j] += tl.inflow[(size_t)h * pstride + slot];
+            }
+        }
+    }
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
     const unsigned long long ks = GATHER ? kg + 1ull : kg;
+    if (call_halted(fl)) return;
+    allow_dependents();
     bool active = false;
-    if (slice < s.nslices) {
-        int32_t c = 0;
-        uint32_t st = 0u;
-        if (valid) {
-            c = s.C[slot];
-            st = s.st[slot];
-        }
-        if (GATHER && valid && (st >> kPendShift) == 0u) {
-            long long in = 0;
-            for (int h = 0; h < tl.P; ++h) in += tl.inflow[(size_t)h * s.nslices * kSlice + slot];
-            const long long nc = (long long)c + in;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const int32_t slice = sl0 + j;
+        if (slice >= s.nslices) break;  // warp-uniform
+        const int32_t slot = slice * kSlice + lane;
+        const bool valid = slot < s.q;
+        int32_t cj = c[j];
+        if (GATHER && valid && (st[j] >> kPendShift) == 0u) {
+            const long long nc = (long long)cj + in[j];
             if (nc > 2147483647ll) {
                 atomicOr(fl + kFlagOverflow, 1u);
-                c = 2147483647;
+                cj = 2147483647;
             } else {
-                c = (int32_t)nc;
+                cj = (int32_t)nc;
             }
         }
         uint32_t emit = 0u;
         if (SELECT && valid) {
-            const SelOut o = has_rec ? select_compiled<SEL>(rec, c, st, ks, neuron_id(s, slot), s.seed)
-                                     : select_neuron<COMPACT, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c,
-                                                                   st, ks, neuron_id(s, slot), s.seed);
-            c = o.c_after;
-            active = o.active;
+            const SelOut o = has_rec ? select_compiled<SEL>(rec[j], cj, st[j], ks, neuron_id(s, slot), s.seed)
+                                     : select_neuron<COMPACT, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), cj,
+                                                                   st[j], ks, neuron_id(s, slot), s.seed);
+            cj = o.c_after;
+            active |= o.active;
             emit = (uint32_t)o.emit;
             SNP_PICK(s.S, ks)[slot] = o.s;
-            if (o.st != st) s.st[slot] = o.st;  // most neurons stay open: skip the write
+            if (o.st != st[j]) s.st[slot] = o.st;  // most neurons stay open: skip the write
         }
-        if (valid) s.C[slot] = c;
+        if (valid) s.C[slot] = cj;
         if (SELECT) pk_put_slice<EB>(SNP_PICK(tl.Eg, ks), slice, lane, emit);
     }
     if (SELECT) raise_step_activity(fl, ks, active);
@@ -352,9 +381,13 @@ static cudaError_t launch_gather_eb(const DevSys& s, const TiledSys& tl, int32_t
     return launch_dependent(fn, (unsigned)tl.G, (unsigned)threads, smem, st, s, tl, t);
 }
 
+// One slice per warp: several slices per warp (more loads in flight per
+// warp) measured slower on the 1M-neuron workload, as the registers they need
+// lower the occupancy more than they add parallelism.
 template <bool G, bool S, bool C, int SEL, int EB>
 static cudaError_t launch_select_t(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st) {
-    return launch_dependent(k_tiled_select<G, S, C, SEL, EB>, (unsigned)((s.nslices + 7) / 8), 256u, 0, st, s, tl, t);
+    return launch_dependent(k_tiled_select<G, S, C, SEL, EB, 1>, (unsigned)((s.nslices + 7) / 8), 256u, 0, st, s, tl,
+                            t);
 }
 
 template <int EB>
