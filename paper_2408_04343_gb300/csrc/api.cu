@@ -129,6 +129,7 @@ void build_plan(snp_system* s, std::vector<Piece>& plan) {
         tl.acc_words = tp.acc_words;
         tl.src_bits = tp.src_bits;
         tl.pairs = tp.pairs;
+        tl.ent_words = (int64_t)tp.ent.size();
         vec(&tl.sub, tp.sub);
         vec(&tl.ent, tp.ent);
         vec(&tl.cta_lo, tp.cta_lo);
@@ -471,7 +472,7 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     if (s->has_tiled) {
         s->tiled_smem = tiled_smem_bytes(im.tp);
         s->tiled_entries = (int64_t)im.tp.ent.size();
-        s->tiled_threads = o.threads > 0 ? o.threads : 1024;
+        s->tiled_threads = kTiledThreads;  // fixed: the entry layout is dealt to this many threads
     }
     {
         std::vector<Piece> plan;

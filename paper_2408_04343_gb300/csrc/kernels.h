@@ -40,6 +40,7 @@ struct TiledSys {
     int32_t P, part_words, e_bits, G, acc_words, src_bits, pairs;
     const int32_t* sub;     // [G][kTiledMaxSub+1] window starts (words, multiples of 4); CTA g*P+h
     const uint32_t* ent;    // (dst_local << src_bits) | src_local
+    int64_t ent_words;      // words of ent
     const int32_t* cta_lo;  // [G/P+1] slice ranges
     uint32_t* Eg[2];        // packed emissions of step k in Eg[k & 1]
     int32_t* inflow;        // [P][nslices*32] in-flow of the step being finished, per partition

@@ -54,17 +54,11 @@ __device__ __forceinline__ void pk_put_slice(uint32_t* e, int32_t slice, int lan
 }
 
 // ---- shared-memory access by 32-bit shared addresses ----------------------
-// The gather's inner loop is issue-bound, so its shared-memory reads and
-// reductions are written with 32-bit shared-window addresses (no generic
-// 64-bit address arithmetic) and conditional reductions are predicated
-// rather than branched around.
+// The gather's reductions are written with 32-bit shared-window addresses
+// (no generic 64-bit address arithmetic), and conditional reductions are
+// predicated rather than branched around.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
 }
 __device__ __forceinline__ void red_add(uint32_t a, uint32_t v) {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
@@ -79,19 +73,15 @@ __device__ __forceinline__ void red_add_if(uint32_t a, uint32_t v, bool p) {
 }
 
 // Emission of the source named by the low bits of entry word w (the bits
-// above the source field do not disturb it): word (src / per) of the packed
-// vector at shared address esm, field src mod per.  `amask` keeps the
-// source's word index, already scaled to a byte offset.
+// above the source field do not disturb it): word src / per of the packed
+// vector Esm in shared memory, field src mod per.  `wmask` keeps the
+// source's word index.  A plain shared-memory load, so the compiler may
+// issue the lookups of a whole batch ahead of the reductions (which touch
+// only the accumulators).
 template <int EB>
-__device__ __forceinline__ uint32_t emission_of(uint32_t esm, uint32_t w, uint32_t amask) {
+__device__ __forceinline__ uint32_t emission_of(const uint32_t* __restrict__ Esm, uint32_t w, uint32_t wmask) {
     constexpr uint32_t per = 32u / EB;  // emissions per 32-bit word
-    uint32_t off;
-    if constexpr (per >= 4) {
-        off = (w >> (__builtin_ctz(per) - 2)) & amask;
-    } else {
-        off = (w << (2 - __builtin_ctz(per))) & amask;
-    }
-    const uint32_t word = lds_u32(esm + off);
+    const uint32_t word = Esm[(w >> __builtin_ctz(per)) & wmask];
     // rotate by (src mod per) * EB: the shift count is taken mod 32
     return __funnelshift_r(word, word, w * (uint32_t)EB) & ((1u << EB) - 1u);
 }
@@ -106,9 +96,10 @@ __device__ __forceinline__ uint32_t emission_of(uint32_t esm, uint32_t w, uint32
 //  that ends at word i), and a run is added when the next word's target
 //  differs or at the last word.
 template <int EB, bool PAIRS>
-__device__ __forceinline__ void edges4(uint32_t esm, uint32_t abase, const uint4& q, uint32_t amask, int sbits) {
-    const uint32_t v0 = emission_of<EB>(esm, q.x, amask), v1 = emission_of<EB>(esm, q.y, amask);
-    const uint32_t v2 = emission_of<EB>(esm, q.z, amask), v3 = emission_of<EB>(esm, q.w, amask);
+__device__ __forceinline__ void edges4(const uint32_t* __restrict__ Esm, uint32_t abase, const uint4& q,
+                                       uint32_t wmask, int sbits) {
+    const uint32_t v0 = emission_of<EB>(Esm, q.x, wmask), v1 = emission_of<EB>(Esm, q.y, wmask);
+    const uint32_t v2 = emission_of<EB>(Esm, q.z, wmask), v3 = emission_of<EB>(Esm, q.w, wmask);
     if constexpr (PAIRS) {
         red_add(abase + (q.x >> sbits) * 4u, v0 + v1);
         red_add(abase + (q.z >> sbits) * 4u, v2 + v3);
@@ -139,6 +130,14 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+// Asks L2 to fetch [p, p + bytes) from memory (16-byte aligned, a multiple
+// of 16 bytes); nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2_range(const char* p, uint64_t bytes) {
+    for (uint64_t o = 0; o < bytes; o += 32768) prefetch_l2(p + o, (uint32_t)min((uint64_t)32768, bytes - o));
+}
 // Waits for phase 0 of the barrier, at most `limit` polls; true when it completed.
 __device__ __forceinline__ bool mbar_wait0(uint32_t bar, int limit) {
     for (int it = 0; it < limit; ++it) {
@@ -157,38 +156,38 @@ __device__ __forceinline__ bool mbar_wait0(uint32_t bar, int limit) {
 constexpr int kBulkChunk = 32768;       // bytes per bulk copy instruction
 constexpr int kWaitPolls = 1 << 20;     // each poll may suspend for a while; ~seconds in all
 
-// One batch of D 16-byte loads of a thread (vector i0 + u * stride for u <
-// D, those below g1).  The window index k only moves forward; a batch inside
-// one window (the common case) takes its base once.
+// One batch of D 16-byte loads of a thread: its vectors u0 .. u0+D-1 (those
+// below nt), sorted indices s0 + u.  The window index k only moves forward;
+// a batch inside one window (the common case) takes its base once.
 template <int EB, bool PAIRS, int D>
-__device__ __forceinline__ void gather_batch(const uint4 (&x)[D], int32_t i0, int32_t stride, int32_t g1,
-                                             const int32_t* wb, int& k, uint32_t esm, uint32_t acc0, int db,
-                                             uint32_t amask, int sbits) {
-    const int32_t last = i0 + (D - 1) * stride;
-    if (last < g1 && last < wb[k + 1]) {  // k <= kTiledMaxSub - 1 and wb[kTiledMaxSub] = g1
+__device__ __forceinline__ void gather_batch(const uint4 (&x)[D], int32_t u0, int32_t nt, int32_t s0,
+                                             const int32_t* wb, int& k, const uint32_t* __restrict__ Esm,
+                                             uint32_t acc0, int db, uint32_t wmask, int sbits) {
+    if (u0 + D <= nt && s0 + u0 + D - 1 < wb[k + 1]) {  // k <= kTiledMaxSub - 1; wb[kTiledMaxSub] = group end
         const uint32_t abase = acc0 + ((uint32_t)k << db) * 4u;
 #pragma unroll
-        for (int u = 0; u < D; ++u) edges4<EB, PAIRS>(esm, abase, x[u], amask, sbits);
+        for (int u = 0; u < D; ++u) edges4<EB, PAIRS>(Esm, abase, x[u], wmask, sbits);
     } else {
 #pragma unroll
         for (int u = 0; u < D; ++u) {
-            const int32_t iu = i0 + u * stride;
-            if (iu < g1) {
+            if (u0 + u < nt) {
+                const int32_t su = s0 + u0 + u;
                 int ku = k;
-                while (ku + 1 < kTiledMaxSub && iu >= wb[ku + 1]) ++ku;
-                edges4<EB, PAIRS>(esm, acc0 + ((uint32_t)ku << db) * 4u, x[u], amask, sbits);
+                while (ku + 1 < kTiledMaxSub && su >= wb[ku + 1]) ++ku;
+                edges4<EB, PAIRS>(Esm, acc0 + ((uint32_t)ku << db) * 4u, x[u], wmask, sbits);
             }
         }
     }
-    const int32_t inext = i0 + D * stride;
-    while (k + 1 < kTiledMaxSub && inext >= wb[k + 1]) ++k;
+    const int32_t snext = s0 + u0 + D;
+    while (k + 1 < kTiledMaxSub && snext >= wb[k + 1]) ++k;
 }
 
+// Vectors u0 .. u0+D-1 of a thread (those below nt); vector u is at col[u * T].
 template <int D>
-__device__ __forceinline__ void load_batch(uint4 (&x)[D], const uint4* ent, int32_t i0, int32_t stride, int32_t g1) {
+__device__ __forceinline__ void load_batch(uint4 (&x)[D], const uint4* col, int32_t u0, int32_t nt) {
 #pragma unroll
     for (int u = 0; u < D; ++u)
-        if (i0 + u * stride < g1) x[u] = ld_stream_v4(ent + i0 + u * stride);
+        if (u0 + u < nt) x[u] = ld_stream_v4(col + (size_t)(u0 + u) * kTiledThreads);
 }
 
 // In-flow of step kg = base + t into tl.inflow (partition h's share).
@@ -207,30 +206,36 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
     const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
     const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
     const uint32_t ebar = smem_u32(&bar);
-    if (threadIdx.x <= kTiledMaxSub)
-        wb[threadIdx.x] = __ldg(tl.sub + (size_t)blockIdx.x * (kTiledMaxSub + 1) + threadIdx.x) / 4;
+    // every thread reads its own bounds (one broadcast line), so the first
+    // entry loads do not wait for a barrier; the shared copy of the window
+    // bounds is published by the barrier after grid_dependency_wait.  Thread
+    // t streams its own run of the group's vectors (see TiledPack).
+    const int32_t* subg = tl.sub + (size_t)blockIdx.x * (kTiledMaxSub + 1);
+    if (threadIdx.x <= kTiledMaxSub) wb[threadIdx.x] = __ldg(subg + threadIdx.x) / 4;
+    const int32_t base = __ldg(subg) / 4;
+    const int32_t N = __ldg(subg + kTiledMaxSub) / 4 - base;
+    const int32_t tid = (int32_t)threadIdx.x;
+    const int32_t n = (N + kTiledThreads - 1) / kTiledThreads;
+    const int32_t r = N - (n - 1) * kTiledThreads;
+    const int32_t nt = tid < r ? n : n - 1;                       // this thread's vectors
+    const int32_t s0 = base + tid * n - max(0, tid - r);          // sorted index of the first
+    const uint4* col = reinterpret_cast<const uint4*>(tl.ent) + base + tid;
+    uint4 qa[D], qb[D];
+    load_batch(qa, col, 0, nt);
     if (threadIdx.x < 4) Esm[tl.part_words + threadIdx.x] = 0u;
     if (threadIdx.x == 0) mbar_init(ebar);
-    for (int i = threadIdx.x; i < tl.acc_words; i += blockDim.x) acc[i] = 0;
-    __syncthreads();
+    for (int j = threadIdx.x; j < tl.acc_words; j += blockDim.x) acc[j] = 0;
     const int sbits = tl.src_bits;
     const int db = 32 - sbits;
     constexpr uint32_t per = 32u / EB;
-    const uint32_t smask = (1u << sbits) - 1u;
-    const uint32_t amask = (per >= 4 ? (smask >> (__builtin_ctz(per) - 2)) : (smask << (2 - __builtin_ctz(per)))) & ~3u;
+    const uint32_t wmask = ((1u << sbits) - 1u) >> __builtin_ctz(per);
     const uint32_t esm = smem_u32(Esm);
     const uint32_t acc0 = smem_u32(acc);
-    const uint4* ent = reinterpret_cast<const uint4*>(tl.ent);
-    const int32_t g1 = wb[kTiledMaxSub];
-    const int32_t stride = blockDim.x;
-    int32_t i = wb[0] + threadIdx.x;
-    uint4 qa[D], qb[D];
-    load_batch(qa, ent, i, stride, g1);
 
     grid_dependency_wait();  // the select launch that wrote E_k has finished
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
-    if (step_blocked(fl, s.step, kg)) return;
+    if (step_blocked(fl, s.step, kg)) return;  // its barrier also publishes wb, acc and the mbarrier
     allow_dependents();
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
     const uint32_t ebytes = (uint32_t)tl.part_words * 4u;
@@ -247,18 +252,16 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
     }
     // two batches in flight: the next batch loads while this one is added
     int k = 0;
-    while (k + 1 < kTiledMaxSub && i >= wb[k + 1]) ++k;
-    for (;;) {
-        int32_t inext = i + D * stride;
-        load_batch(qb, ent, inext, stride, g1);
-        gather_batch<EB, PAIRS, D>(qa, i, stride, g1, wb, k, esm, acc0, db, amask, sbits);
-        if (inext >= g1) break;
-        i = inext;
-        inext = i + D * stride;
-        load_batch(qa, ent, inext, stride, g1);
-        gather_batch<EB, PAIRS, D>(qb, i, stride, g1, wb, k, esm, acc0, db, amask, sbits);
-        if (inext >= g1) break;
-        i = inext;
+    while (k + 1 < kTiledMaxSub && s0 >= wb[k + 1]) ++k;
+    for (int32_t u = 0;;) {
+        load_batch(qb, col, u + D, nt);
+        gather_batch<EB, PAIRS, D>(qa, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits);
+        u += D;
+        if (u >= nt) break;
+        load_batch(qa, col, u + D, nt);
+        gather_batch<EB, PAIRS, D>(qb, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits);
+        u += D;
+        if (u >= nt) break;
     }
     __syncthreads();
     const int32_t slot0 = lo * kSlice;
@@ -286,6 +289,16 @@ __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int
         rec[j] = make_uint4(0u, 0u, 0u, 0u);
         if (SELECT && has_rec && sl0 + j < s.nslices && slot < s.q)
             rec[j] = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
+    }
+
+    if (SELECT && threadIdx.x == 0 && tl.ent_words > 0) {
+        // the gather launch after this one streams the whole entry array;
+        // this launch leaves memory bandwidth idle, so each CTA asks L2 for
+        // a slice of it
+        const uint64_t total = (uint64_t)tl.ent_words * 4u;
+        const uint64_t per = (total / gridDim.x + 15u) & ~(uint64_t)15u;
+        const uint64_t a = min(total, (uint64_t)blockIdx.x * per), b = min(total, a + per);
+        if (b > a) prefetch_l2_range(reinterpret_cast<const char*>(tl.ent) + a, b - a);
     }
 
     grid_dependency_wait();
@@ -378,7 +391,8 @@ static cudaError_t launch_gather_eb(const DevSys& s, const TiledSys& tl, int32_t
     auto fn = tl.pairs ? k_tiled_gather<EB, true> : k_tiled_gather<EB, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_dependent(fn, (unsigned)tl.G, (unsigned)threads, smem, st, s, tl, t);
+    (void)threads;
+    return launch_dependent(fn, (unsigned)tl.G, (unsigned)kTiledThreads, smem, st, s, tl, t);
 }
 
 // One slice per warp: several slices per warp (more loads in flight per

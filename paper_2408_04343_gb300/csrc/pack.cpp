@@ -545,6 +545,17 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
             while (tp->ent.size() % 4) tp->ent.push_back(pad);
             while (win < kTiledMaxSub) sb[++win] = (int32_t)tp->ent.size();
             if (tp->ent.size() > (size_t)INT32_MAX) return fail(SNP_ERR_UNSUPPORTED, "too many entries");
+            // thread-contiguous storage order of the group's vectors
+            const int64_t base = sb[0] / 4, N = (int64_t)tp->ent.size() / 4 - base;
+            if (N > 0) {
+                const int64_t T = kTiledThreads, n = (N + T - 1) / T, r = N - (n - 1) * T;
+                std::vector<uint32_t> srt(tp->ent.begin() + base * 4, tp->ent.end());
+                for (int64_t t = 0; t < T; ++t) {
+                    const int64_t s0 = t * n - std::max<int64_t>(0, t - r), nt = t < r ? n : n - 1;
+                    for (int64_t u = 0; u < nt; ++u)
+                        std::copy_n(srt.begin() + (s0 + u) * 4, 4, tp->ent.begin() + (base + u * T + t) * 4);
+                }
+            }
         }
     }
     return SNP_OK;

@@ -112,6 +112,7 @@ struct HostPack {
 bool compile_rules(const snp_desc* d, HostPack* hp);
 
 constexpr int kTiledMaxSub = 8;  // target windows per CTA of the tiled engine
+constexpr int kTiledThreads = 1024;  // threads of a tiled gather CTA (the entry layout depends on it)
 constexpr double kTiledPairSlack = 0.125;  // largest padding of the paired layout
 
 // Layout of the tiled engine (shared-memory emissions, source partitions).
@@ -134,6 +135,14 @@ constexpr double kTiledPairSlack = 0.125;  // largest padding of the paired layo
 // within a 16-byte load.  Pad words have source part_size, which reads a
 // zero word; windows are padded to 16 bytes with them so they load as
 // 16-byte vectors.
+// Storage order: the N 16-byte vectors of a CTA's group, in the sorted order
+// above (window bounds in `sub` count in that order), are dealt out to the
+// kTiledThreads threads of the CTA in contiguous runs -- thread t takes n or
+// n - 1 consecutive vectors, n = ceil(N / T), the first r = N - (n-1)T
+// threads n -- and stored so that the u-th vector of every thread is
+// adjacent: vector u of thread t sits at group offset u*T + t.  A warp's
+// load is then one contiguous 512-byte line set, while its lanes work on
+// targets far apart (no two lanes reducing into one accumulator).
 struct TiledPack {
     int e_bits = 0;          // bits per emission (2, 4, 8, 16)
     int P = 0;               // partitions
