@@ -319,6 +319,20 @@ typedef struct snp_device_system {
 int snp_step_noalloc(const snp_device_system* sys, int32_t select, uint64_t seed, uint64_t step, int64_t n,
                      void* stream, int64_t* steps_done);
 
+/* ---- diagnostic of the device-side wait limit --------------------------
+ * No counterpart in the paper.  Every wait inside the library's kernels
+ * (the tiled engine waits on a shared-memory barrier for the bulk copy of an
+ * emission partition) gives up after a bounded number of polls, records the
+ * fact in the system's timeout flag and returns, so that a lost completion
+ * surfaces as SNP_ERR_TIMEOUT with the CUDA context still usable instead of
+ * a hung GPU.  This call runs one CTA that performs the same bounded wait,
+ * for at most `polls` polls (1 .. 1,000,000), on a barrier that nothing
+ * completes, on the current device and a private stream.
+ * Returns SNP_ERR_TIMEOUT when the wait gave up (the expected outcome),
+ * SNP_OK if it completed, SNP_ERR_INVALID for polls out of range,
+ * SNP_ERR_CUDA on a launch or copy failure.                               */
+int snp_check_bounded_wait(int32_t polls);
+
 const char* snp_strerror(int status);
 const char* snp_last_error(void);
 

@@ -610,6 +610,27 @@ int snp_set_state(snp_system* s, const int32_t* C, const int32_t* D, const int32
     return SNP_OK;
 }
 
+int snp_check_bounded_wait(int32_t polls) {
+    if (polls < 1 || polls > 1000000) return fail(SNP_ERR_INVALID, "polls must be in 1..1000000");
+    cudaStream_t st = nullptr;
+    uint32_t* d_out = nullptr;
+    uint32_t h_out = 0;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail("stream");
+    int rc = SNP_OK;
+    if (cudaMalloc(&d_out, sizeof(uint32_t)) != cudaSuccess || cudaMemsetAsync(d_out, 0, 4, st) != cudaSuccess ||
+        launch_wait_check(polls, d_out, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h_out, d_out, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        rc = cuda_fail("bounded wait check");
+    else if (h_out == 2u)
+        rc = fail(SNP_ERR_TIMEOUT, "the bounded wait gave up after " + std::to_string(polls) + " polls");
+    else if (h_out != 1u)
+        rc = fail(SNP_ERR_CUDA, "the wait check did not report");
+    if (d_out) cudaFree(d_out);
+    cudaStreamDestroy(st);
+    return rc;
+}
+
 int snp_get_info(const snp_system* s, snp_info* info) {
     if (!s || !info) return fail(SNP_ERR_INVALID, "NULL argument");
     std::memset(info, 0, sizeof(*info));

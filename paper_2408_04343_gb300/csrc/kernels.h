@@ -47,6 +47,9 @@ struct TiledSys {
 };
 cudaError_t launch_tiled(const DevSys& s, const TiledSys& tl, int kind, int32_t t, cudaStream_t st, bool compact,
                          int sel, size_t smem, int threads);
+// One CTA waits at most `polls` polls on a barrier nothing completes; *out = 1
+// if the wait completed, 2 if it gave up.
+cudaError_t launch_wait_check(int polls, uint32_t* out, cudaStream_t st);
 cudaError_t launch_gather_results(const DevSys* d_systems, int nsys, unsigned long long* d_out, cudaStream_t st);
 
 // ELL and dense forms (kernels_ell.cu).

@@ -153,6 +153,23 @@ __device__ __forceinline__ bool mbar_wait0(uint32_t bar, int limit) {
     }
     return false;
 }
+__global__ void k_wait_check(int polls, uint32_t* out) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b);
+        mbar_expect_tx(b, 16u);  // sixteen bytes that no copy will deliver
+    }
+    __syncthreads();
+    const bool done = mbar_wait0(b, polls);
+    if (threadIdx.x == 0) *out = done ? 1u : 2u;
+}
+
+cudaError_t launch_wait_check(int polls, uint32_t* out, cudaStream_t st) {
+    k_wait_check<<<1, 32, 0, st>>>(polls, out);
+    return cudaGetLastError();
+}
+
 constexpr int kBulkChunk = 32768;       // bytes per bulk copy instruction
 constexpr int kWaitPolls = 1 << 20;     // each poll may suspend for a while; ~seconds in all
 

@@ -101,6 +101,7 @@ _SIGS = {
     "snp_paper_format_elements": (ct.c_int64, [ct.c_int32, ct.c_int64, ct.c_int64, ct.c_int64]),
     "snp_step_noalloc": (ct.c_int, [ct.POINTER(snp_device_system), ct.c_int32, ct.c_uint64, ct.c_uint64,
                                      ct.c_int64, _P, ct.POINTER(ct.c_int64)]),
+    "snp_check_bounded_wait": (ct.c_int, [ct.c_int32]),
     "snp_strerror": (ct.c_char_p, [ct.c_int]),
     "snp_last_error": (ct.c_char_p, []),
 }

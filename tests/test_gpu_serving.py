@@ -76,7 +76,7 @@ def test_late_short_request_overtakes_long_one():
     b = libsnp.Batch()
     gl = libsnp.System(long_d, select=libsnp.SNP_SELECT_PHILOX, seed=1, deferred=True)
     gs = libsnp.System(short_d, select=libsnp.SNP_SELECT_PHILOX, seed=2, deferred=True)
-    tl = b.submit([gl], [3000])
+    tl = b.submit([gl], [40000])  # about half a second of device time
     time.sleep(0.05)
     ts = b.submit([gs], [20])
     b.wait(ts)
