@@ -317,7 +317,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "engine": {"tiled": "tiled pull (emissions in shared memory), one fused launch per SNP step",
+            "config": {"workload": WORKLOAD, "engine": {"tiled": "tiled pull (emissions in shared memory): a gather and a select launch per SNP step, programmatic dependent launches replayed from CUDA graphs",
                                                      "launch": "grid-wide pull, emissions gathered from L2, one fused launch per SNP step"}[args.engine],
                        "snp_steps_per_bench_step": T, "replicas_round_robin": len(systems),
                        "l2": f"inputs larger than L2: {len(systems)} replicas, {foot / 1e6:.0f} MB on the device, "
@@ -325,7 +325,8 @@ def main():
                        "q": desc.q, "num_syn": desc.num_syn, "snp_steps_timed": int(executed)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": {"tiled": "k_tiled (fused gather + select)", "launch": "k_step_pull (fused gather + select)"}[args.engine],
+                         "kernel": {"tiled": "k_tiled_gather + k_tiled_select (one launch of each per SNP step; achieved = the step's algorithmic bytes / the step's live device time)",
+                                    "launch": "k_step_pull (fused gather + select, one launch per SNP step)"}[args.engine],
                          "algorithmic_bytes_per_snp_step": alg},
             "e2e": {"value": e2e_value, "unit": "synaptic updates/s", "h2d_bytes_per_step": 3 * 4 * q,
                     "d2h_bytes_per_step": 4 * q,
