@@ -436,6 +436,19 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
             return cuda_fail("device query");
         }
         st = pack_tiled(desc, hp, sms, (size_t)optin - 2048, &im.tp);
+        // Under AUTO the tiled engine must pay for itself: every CTA copies a
+        // whole emission partition into shared memory each step.  With one
+        // wave of CTAs that copy overlaps the entry stream; with several
+        // waves (large, low-degree systems: many partitions) it can move more
+        // bytes than the gathers it replaces (2M-neuron Zipf(2.1) system:
+        // 60 MB of copies for 34 MB of entries, slower than the L2 gather).
+        // Keep it when it is one wave or the copies stay under half the
+        // entry stream.
+        if (st == SNP_OK && o.engine == SNP_ENGINE_AUTO && im.tp.G > sms &&
+            (double)im.tp.G * im.tp.part_words * 4.0 > 0.5 * 4.0 * (double)im.tp.ent.size()) {
+            im.tp = TiledPack();
+            st = SNP_ERR_UNSUPPORTED;
+        }
         if (st == SNP_OK) {
             s->has_tiled = true;
             // the resident engine (batches) still needs in-lists when the system fits one CTA

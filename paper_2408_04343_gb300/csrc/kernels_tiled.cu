@@ -86,35 +86,49 @@ __device__ __forceinline__ uint32_t emission_of(const uint32_t* __restrict__ Esm
     return __funnelshift_r(word, word, w * (uint32_t)EB) & ((1u << EB) - 1u);
 }
 
-// One 16-byte load of a window, four words sorted by target; abase =
-// shared address of the window's first accumulator.
-//  PAIRS: two pairs of words, each pair one target (its window-relative slot
-//  in the high bits of both words) and two sources; each pair's emissions
-//  are added to its target with one shared-memory reduction.
-//  Otherwise: the emissions of consecutive words with the same target are
-//  summed in registers, without branches (r_i is the running sum of the run
-//  that ends at word i), and a run is added when the next word's target
-//  differs or at the last word.
-template <int EB, bool PAIRS>
+// Run layout, one 16-byte load of a window: four words sorted by target
+// (abase = shared address of the window's first accumulator).  The
+// emissions of consecutive words with the same target are summed in
+// registers, without branches (r_i is the running sum of the run that ends
+// at word i), and a run is added when the next word's target differs or at
+// the last word.
+template <int EB>
 __device__ __forceinline__ void edges4(const uint32_t* __restrict__ Esm, uint32_t abase, const uint4& q,
                                        uint32_t wmask, int sbits) {
     const uint32_t v0 = emission_of<EB>(Esm, q.x, wmask), v1 = emission_of<EB>(Esm, q.y, wmask);
     const uint32_t v2 = emission_of<EB>(Esm, q.z, wmask), v3 = emission_of<EB>(Esm, q.w, wmask);
-    if constexpr (PAIRS) {
-        red_add(abase + (q.x >> sbits) * 4u, v0 + v1);
-        red_add(abase + (q.z >> sbits) * 4u, v2 + v3);
-    } else {
-        const uint32_t d0 = q.x >> sbits, d1 = q.y >> sbits, d2 = q.z >> sbits, d3 = q.w >> sbits;
-        const bool s1 = d1 == d0, s2 = d2 == d1, s3 = d3 == d2;
-        const uint32_t r0 = v0;
-        const uint32_t r1 = (s1 ? r0 : 0u) + v1;
-        const uint32_t r2 = (s2 ? r1 : 0u) + v2;
-        const uint32_t r3 = (s3 ? r2 : 0u) + v3;
-        red_add_if(abase + d0 * 4u, r0, !s1);
-        red_add_if(abase + d1 * 4u, r1, !s2);
-        red_add_if(abase + d2 * 4u, r2, !s3);
-        red_add(abase + d3 * 4u, r3);
-    }
+    const uint32_t d0 = q.x >> sbits, d1 = q.y >> sbits, d2 = q.z >> sbits, d3 = q.w >> sbits;
+    const bool s1 = d1 == d0, s2 = d2 == d1, s3 = d3 == d2;
+    const uint32_t r0 = v0;
+    const uint32_t r1 = (s1 ? r0 : 0u) + v1;
+    const uint32_t r2 = (s2 ? r1 : 0u) + v2;
+    const uint32_t r3 = (s3 ? r2 : 0u) + v3;
+    red_add_if(abase + d0 * 4u, r0, !s1);
+    red_add_if(abase + d1 * 4u, r1, !s2);
+    red_add_if(abase + d2 * 4u, r2, !s3);
+    red_add(abase + d3 * 4u, r3);
+}
+
+// Paired layout, one 16-byte load (two pairs) of a thread's contiguous run:
+// runs of pairs with the same target are summed in `run` and added to the
+// accumulator at `cur` (a shared address) only when the target changes, so
+// a target costs one reduction however many pairs it has.  The first and
+// last target of a thread's run may be shared with the neighbouring thread;
+// the reduction is atomic.
+template <int EB>
+__device__ __forceinline__ void pairs_merge(const uint32_t* __restrict__ Esm, uint32_t abase, const uint4& q,
+                                            uint32_t wmask, int sbits, uint32_t& cur, uint32_t& run) {
+    const uint32_t v01 = emission_of<EB>(Esm, q.x, wmask) + emission_of<EB>(Esm, q.y, wmask);
+    const uint32_t v23 = emission_of<EB>(Esm, q.z, wmask) + emission_of<EB>(Esm, q.w, wmask);
+    const uint32_t a0 = abase + (q.x >> sbits) * 4u, a1 = abase + (q.z >> sbits) * 4u;
+    bool f = a0 != cur;
+    red_add_if(cur, run, f);
+    run = (f ? 0u : run) + v01;
+    cur = a0;
+    f = a1 != cur;
+    red_add_if(cur, run, f);
+    run = (f ? 0u : run) + v23;
+    cur = a1;
 }
 
 // ---- bulk copy of a partition's emissions into shared memory -------------
@@ -179,11 +193,17 @@ constexpr int kWaitPolls = 1 << 20;     // each poll may suspend for a while; ~s
 template <int EB, bool PAIRS, int D>
 __device__ __forceinline__ void gather_batch(const uint4 (&x)[D], int32_t u0, int32_t nt, int32_t s0,
                                              const int32_t* wb, int& k, const uint32_t* __restrict__ Esm,
-                                             uint32_t acc0, int db, uint32_t wmask, int sbits) {
+                                             uint32_t acc0, int db, uint32_t wmask, int sbits, uint32_t& cur,
+                                             uint32_t& run) {
     if (u0 + D <= nt && s0 + u0 + D - 1 < wb[k + 1]) {  // k <= kTiledMaxSub - 1; wb[kTiledMaxSub] = group end
         const uint32_t abase = acc0 + ((uint32_t)k << db) * 4u;
 #pragma unroll
-        for (int u = 0; u < D; ++u) edges4<EB, PAIRS>(Esm, abase, x[u], wmask, sbits);
+        for (int u = 0; u < D; ++u) {
+            if constexpr (PAIRS)
+                pairs_merge<EB>(Esm, abase, x[u], wmask, sbits, cur, run);
+            else
+                edges4<EB>(Esm, abase, x[u], wmask, sbits);
+        }
     } else {
 #pragma unroll
         for (int u = 0; u < D; ++u) {
@@ -191,7 +211,11 @@ __device__ __forceinline__ void gather_batch(const uint4 (&x)[D], int32_t u0, in
                 const int32_t su = s0 + u0 + u;
                 int ku = k;
                 while (ku + 1 < kTiledMaxSub && su >= wb[ku + 1]) ++ku;
-                edges4<EB, PAIRS>(Esm, acc0 + ((uint32_t)ku << db) * 4u, x[u], wmask, sbits);
+                const uint32_t abase = acc0 + ((uint32_t)ku << db) * 4u;
+                if constexpr (PAIRS)
+                    pairs_merge<EB>(Esm, abase, x[u], wmask, sbits, cur, run);
+                else
+                    edges4<EB>(Esm, abase, x[u], wmask, sbits);
             }
         }
     }
@@ -270,16 +294,18 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
     // two batches in flight: the next batch loads while this one is added
     int k = 0;
     while (k + 1 < kTiledMaxSub && s0 >= wb[k + 1]) ++k;
+    uint32_t cur = acc0, run = 0u;  // paired layout: the target being summed and its sum so far
     for (int32_t u = 0;;) {
         load_batch(qb, col, u + D, nt);
-        gather_batch<EB, PAIRS, D>(qa, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits);
+        gather_batch<EB, PAIRS, D>(qa, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits, cur, run);
         u += D;
         if (u >= nt) break;
         load_batch(qa, col, u + D, nt);
-        gather_batch<EB, PAIRS, D>(qb, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits);
+        gather_batch<EB, PAIRS, D>(qb, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits, cur, run);
         u += D;
         if (u >= nt) break;
     }
+    if (PAIRS) red_add_if(cur, run, run != 0u);
     __syncthreads();
     const int32_t slot0 = lo * kSlice;
     const int32_t nloc = (hi - lo) * kSlice;  // a multiple of 32

@@ -121,6 +121,27 @@ def test_tiled_paired_and_run_layouts(outdeg, paired):
         compare(d, 40, mode, 5 + outdeg[0], engine="tiled", check_every=False, chunks=(9, 31))
 
 
+def test_auto_engine_choice():
+    """AUTO: CTA-resident for small systems, tiled for one wave of tiled
+    CTAs, the L2 gather for large low-degree systems whose emission copies
+    would outweigh the entry stream; every choice matches the oracle."""
+    cases = [(synth.random_system(3000, 61, outdeg=(4, 16), rules=(3, 4), d_range=(0, 5), spikes=(0, 20)),
+              libsnp.SNP_ENGINE_RESIDENT),
+             (synth.random_system(200000, 62, outdeg=(8, 24), rules=(3, 4), d_range=(0, 5), spikes=(0, 20)),
+              libsnp.SNP_ENGINE_TILED),
+             (synth.random_system(1 << 21, 63, zipf=(2.1, 1, 4096), rules=(3, 3), d_range=(0, 3), spikes=(0, 20)),
+              libsnp.SNP_ENGINE_LAUNCH)]
+    for d, want in cases:
+        gs = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=3)
+        assert gs.info().engine == want, (d.q, gs.info().engine)
+        done = gs.step(6)
+        st = oracle.initial_state(d)
+        ex, _ = oracle.run(d, st, 6, oracle.PHILOX, 3)
+        C, D, P, _ = gs.get_state()
+        assert done == ex and (C == st[0]).all() and (D == st[1]).all() and (P == st[2]).all()
+        gs.close()
+
+
 @pytest.mark.parametrize("engine", ["launch", "resident", "tiled"])
 def test_chunked_calls_and_graphs(engine):
     """Calls of many sizes (crossing the captured-graph chunk length)."""
