@@ -133,7 +133,8 @@ void build_plan(snp_system* s, std::vector<Piece>& plan) {
         vec(&tl.sub, tp.sub);
         vec(&tl.ent, tp.ent);
         vec(&tl.cta_lo, tp.cta_lo);
-        fill(&tl.inflow, (size_t)tp.P * nslices * kSlice * 4, 0);
+        tl.inflow = nullptr;  // the fused step sums the partitions' in-flows in distributed shared memory
+        if (tp.P > kTiledMaxCluster) fill(&tl.inflow, (size_t)tp.P * nslices * kSlice * 4, 0);
         for (int b = 0; b < 2; ++b) fill(&tl.Eg[b], (size_t)tp.P * tp.part_words * 4, 0);
     }
 }

@@ -7,7 +7,11 @@
 // is at most 3) and every CTA copies it into its shared memory, one source
 // partition at a time, so the gathers become shared-memory reads.
 //
-// A step is two launches:
+// A step is one launch, k_tiled_step, when the P partitions of a slice range
+// fit one thread-block cluster (P <= kTiledMaxCluster): the gather below,
+// then the select of the next step in the same CTAs, the in-flow summed
+// across the cluster through distributed shared memory.  Otherwise a step is
+// two launches:
 //  * k_tiled_gather -- one CTA per SM.  CTA g*P + h owns slice range g and
 //    source partition h: it loads h's packed emissions once and streams the
 //    group of in-edge words of its range from h edge-parallel (16-byte vector loads, no
@@ -231,22 +235,24 @@ __device__ __forceinline__ void load_batch(uint4 (&x)[D], const uint4* col, int3
         if (u0 + u < nt) x[u] = ld_stream_v4(col + (size_t)(u0 + u) * kTiledThreads);
 }
 
-// In-flow of step kg = base + t into tl.inflow (partition h's share).
-// Launched as a programmatic dependent of the select launch before it: the
-// part before grid_dependency_wait touches only the constant layout (window
-// bounds, the first entry vectors) and the CTA's own shared memory, so it
-// overlaps the end of that launch.
+// Gather phase of step kg = base + t, shared by both launch forms: CTA
+// g*P + h adds the emissions of partition h along the in-edges of range g
+// into its shared accumulators.  The part before grid_dependency_wait
+// touches only the constant layout (window bounds, the first entry vectors)
+// and the CTA's own shared memory, so it overlaps the end of the launch
+// before.  Returns kPhaseBlocked when the step is not executed (a fixed
+// point; the same answer in every CTA), kPhaseTimeout when the bulk copy's
+// wait gave up (the timeout flag is set; the accumulators are incomplete),
+// else kPhaseOk.  On return the accumulators are complete in this CTA.
+enum : int { kPhaseOk = 0, kPhaseBlocked = 1, kPhaseTimeout = 2 };
+
 template <int EB, bool PAIRS>
-__global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl, int32_t t) {
+__device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSys& tl, int32_t t, uint32_t* Esm,
+                                                  int* acc, int32_t* wb, unsigned long long* bar,
+                                                  unsigned long long& kg_out) {
     constexpr int D = 4;  // vectors per batch; two batches in registers
-    extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ int32_t wb[kTiledMaxSub + 1];
-    __shared__ __align__(8) unsigned long long bar;
-    uint32_t* Esm = smem;                                              // part_words + a zero word
-    int* acc = reinterpret_cast<int*>(smem + tl.part_words + 4);
-    const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
-    const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
-    const uint32_t ebar = smem_u32(&bar);
+    const int h = blockIdx.x % tl.P;
+    const uint32_t ebar = smem_u32(bar);
     // every thread reads its own bounds (one broadcast line), so the first
     // entry loads do not wait for a barrier; the shared copy of the window
     // bounds is published by the barrier after grid_dependency_wait.  Thread
@@ -273,10 +279,11 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
     const uint32_t esm = smem_u32(Esm);
     const uint32_t acc0 = smem_u32(acc);
 
-    grid_dependency_wait();  // the select launch that wrote E_k has finished
+    grid_dependency_wait();  // the launch that wrote E_k has finished
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
-    if (step_blocked(fl, s.step, kg)) return;  // its barrier also publishes wb, acc and the mbarrier
+    kg_out = kg;
+    if (step_blocked(fl, s.step, kg)) return kPhaseBlocked;  // its barrier also publishes wb, acc, the mbarrier
     allow_dependents();
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
     const uint32_t ebytes = (uint32_t)tl.part_words * 4u;
@@ -286,10 +293,11 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
         for (uint32_t o = 0; o < ebytes; o += kBulkChunk)
             bulk_g2s(esm + o, src + o, min((uint32_t)kBulkChunk, ebytes - o), ebar);
     }
-    if (!mbar_wait0(ebar, kWaitPolls)) {
-        atomicOr(fl + kFlagTimeout, 1u);
-        mbar_wait0(ebar, kWaitPolls);  // let the copy land before the CTA's shared memory goes away
-        return;
+    const bool landed = mbar_wait0(ebar, kWaitPolls);
+    if (!__syncthreads_and(landed)) {  // the same answer in every thread of the CTA
+        if (threadIdx.x == 0) atomicOr(fl + kFlagTimeout, 1u);
+        if (!landed) mbar_wait0(ebar, kWaitPolls);  // let the copy land before the shared memory goes away
+        return kPhaseTimeout;
     }
     // two batches in flight: the next batch loads while this one is added
     int k = 0;
@@ -307,11 +315,156 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
     }
     if (PAIRS) red_add_if(cur, run, run != 0u);
     __syncthreads();
+    return kPhaseOk;
+}
+
+// Two-launch form (partitions P > kTiledMaxCluster): the gather writes
+// partition h's in-flow of step kg to tl.inflow; k_tiled_select sums them.
+template <int EB, bool PAIRS>
+__global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl, int32_t t) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int32_t wb[kTiledMaxSub + 1];
+    __shared__ __align__(8) unsigned long long bar;
+    uint32_t* Esm = smem;                                              // part_words + a zero word
+    int* acc = reinterpret_cast<int*>(smem + tl.part_words + 4);
+    unsigned long long kg;
+    if (tiled_gather_phase<EB, PAIRS>(s, tl, t, Esm, acc, wb, &bar, kg) != kPhaseOk) return;
+    const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
+    const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
     const int32_t slot0 = lo * kSlice;
     const int32_t nloc = (hi - lo) * kSlice;  // a multiple of 32
     uint4* out = reinterpret_cast<uint4*>(tl.inflow + (size_t)h * s.nslices * kSlice + slot0);
     const uint4* a4 = reinterpret_cast<const uint4*>(acc);
     for (int j = threadIdx.x; j < nloc / 4; j += blockDim.x) out[j] = a4[j];
+}
+
+// ---- thread-block clusters ----------------------------------------------
+// All threads of every CTA of the cluster arrive; writes to shared memory
+// before it are visible to every CTA of the cluster after it.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+// Finish of step kg and select of step kg+1 for one slice, from its in-flow.
+template <int SEL, int EB>
+__device__ __forceinline__ void finish_select_slice(const DevSys& s, const TiledSys& tl, bool select, bool compact,
+                                                    int32_t slice, int lane, int32_t c, uint32_t st, const uint4& rec,
+                                                    long long in, unsigned long long ks, bool& active) {
+    const int32_t slot = slice * kSlice + lane;
+    const bool valid = slot < s.q;
+    if (valid && (st >> kPendShift) == 0u) {
+        const long long nc = (long long)c + in;
+        if (nc > 2147483647ll) {
+            atomicOr(s.flags + kFlagOverflow, 1u);
+            c = 2147483647;
+        } else {
+            c = (int32_t)nc;
+        }
+    }
+    uint32_t emit = 0u;
+    if (select && valid) {
+        const uint32_t nid = neuron_id(s, slot);
+        SelOut o;
+        if (s.rec)
+            o = select_compiled<SEL>(rec, c, st, ks, nid, s.seed);
+        else if (compact)
+            o = select_neuron<true, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks, nid, s.seed);
+        else
+            o = select_neuron<false, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks, nid, s.seed);
+        c = o.c_after;
+        active |= o.active;
+        emit = (uint32_t)o.emit;
+        SNP_PICK(s.S, ks)[slot] = o.s;
+        if (o.st != st) s.st[slot] = o.st;  // most neurons stay open: skip the write
+    }
+    if (valid) s.C[slot] = c;
+    if (select) pk_put_slice<EB>(SNP_PICK(tl.Eg, ks), slice, lane, emit);
+}
+
+// One SNP step in one launch (partitions P <= kTiledMaxCluster): the P CTAs
+// of a slice range form a thread-block cluster.  Each gathers its partition
+// into its shared accumulators; after a cluster barrier every CTA finishes
+// step kg and selects step kg+1 (SELECT) for its share of the range, reading
+// the in-flow of a slot as the sum of the P accumulators through distributed
+// shared memory; a second cluster barrier keeps every accumulator alive until
+// the other CTAs have read it.  Each warp loads the next slice's state while
+// it works on the current one.
+template <int EB, bool PAIRS, int SEL>
+__global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, int32_t t, int select, int compact) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int32_t wb[kTiledMaxSub + 1];
+    __shared__ __align__(8) unsigned long long bar;
+    uint32_t* Esm = smem;
+    int* acc = reinterpret_cast<int*>(smem + tl.part_words + 4);
+    const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
+    const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
+    const int32_t share = (hi - lo + tl.P - 1) / tl.P;
+    const int32_t my_lo = min(hi, lo + h * share), my_hi = min(hi, lo + (h + 1) * share);
+    if (threadIdx.x == 32) {
+        // the select phase reads C, the status words and the compiled records
+        // of this CTA's share: ask L2 for them now, while the gather runs
+        const int32_t a = my_lo * kSlice, b = min(s.q, my_hi * kSlice);
+        const uint64_t nb = b > a ? (uint64_t)(b - a) * 4u & ~(uint64_t)15 : 0u;
+        if (nb) {
+            prefetch_l2_range(reinterpret_cast<const char*>(s.C + a), nb);
+            prefetch_l2_range(reinterpret_cast<const char*>(s.st + a), nb);
+            if (s.rec) prefetch_l2_range(reinterpret_cast<const char*>(s.rec) + (size_t)a * 16u, nb * 4u);
+        }
+    }
+    unsigned long long kg;
+    const int ph = tiled_gather_phase<EB, PAIRS>(s, tl, t, Esm, acc, wb, &bar, kg);
+    if (ph == kPhaseBlocked) return;  // every CTA of the cluster returns here, before any cluster barrier
+    cluster_sync();
+    const unsigned long long ks = kg + 1ull;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t acc0 = smem_u32(acc);
+    const bool has_rec = s.rec != nullptr;
+    bool active = false;
+    if (ph == kPhaseOk) {
+        if (threadIdx.x == 32) {
+            // this CTA's entry words are read again by the next step: ask L2
+            // for them while the select phase leaves memory bandwidth idle
+            const int32_t* subg = tl.sub + (size_t)blockIdx.x * (kTiledMaxSub + 1);
+            const int64_t b0 = __ldg(subg) / 4, b1 = __ldg(subg + kTiledMaxSub) / 4;
+            if (b1 > b0) prefetch_l2_range(reinterpret_cast<const char*>(tl.ent) + b0 * 16, (uint64_t)(b1 - b0) * 16);
+        }
+        int32_t sl = my_lo + warp;
+        int32_t c = 0, cn = 0;
+        uint32_t st = 0u, stn = 0u;
+        uint4 rec = make_uint4(0u, 0u, 0u, 0u), recn = rec;
+        auto load = [&](int32_t slc, int32_t& cc, uint32_t& ss, uint4& rr) {
+            const int32_t slot = slc * kSlice + lane;
+            if (slc < my_hi && slot < s.q) {
+                cc = s.C[slot];
+                ss = s.st[slot];
+                if (select && has_rec) rr = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
+            }
+        };
+        load(sl, c, st, rec);
+        for (; sl < my_hi; sl += nw) {
+            load(sl + nw, cn, stn, recn);
+            const uint32_t la = acc0 + (uint32_t)((sl - lo) * kSlice + lane) * 4u;
+            long long in = 0;
+            for (int r = 0; r < tl.P; ++r) in += (int32_t)ld_cluster_u32(cluster_map(la, (uint32_t)r));
+            finish_select_slice<SEL, EB>(s, tl, select != 0, compact != 0, sl, lane, c, st, rec, in, ks, active);
+            c = cn;
+            st = stn;
+            rec = recn;
+        }
+    }
+    if (select) raise_step_activity(s.flags, ks, active);
+    cluster_sync();
 }
 
 // Finishes step kg (GATHER: adds the in-flow to open neurons) and selects
@@ -447,9 +600,38 @@ static cudaError_t launch_select_t(const DevSys& s, const TiledSys& tl, int32_t 
                             t);
 }
 
+// One fused step launch: clusters of P CTAs, programmatic dependent.
+template <int EB, int SEL>
+static cudaError_t launch_step_eb(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st, size_t smem,
+                                  bool select, bool compact) {
+    auto fn = tl.pairs ? k_tiled_step<EB, true, SEL> : k_tiled_step<EB, false, SEL>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)tl.G);
+    cfg.blockDim = dim3((unsigned)kTiledThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = (unsigned)tl.P;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, fn, s, tl, t, select ? 1 : 0, compact ? 1 : 0);
+}
+
 template <int EB>
 static cudaError_t launch_tiled_eb(const DevSys& s, const TiledSys& tl, int kind, int32_t t, cudaStream_t st,
                                    bool compact, int sel, size_t smem, int threads) {
+    if (kind != kPullSelectOnly && tl.P <= kTiledMaxCluster) {
+        const bool select = kind == kPullFused;
+        return sel == SNP_SELECT_FIRST ? launch_step_eb<EB, SNP_SELECT_FIRST>(s, tl, t, st, smem, select, compact)
+                                       : launch_step_eb<EB, SNP_SELECT_PHILOX>(s, tl, t, st, smem, select, compact);
+    }
     cudaError_t e = cudaSuccess;
     if (kind != kPullSelectOnly) e = launch_gather_eb<EB>(s, tl, t, st, smem, threads);
     if (e != cudaSuccess) return e;

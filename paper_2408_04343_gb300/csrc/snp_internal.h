@@ -113,6 +113,7 @@ bool compile_rules(const snp_desc* d, HostPack* hp);
 
 constexpr int kTiledMaxSub = 8;  // target windows per CTA of the tiled engine
 constexpr int kTiledThreads = 1024;  // threads of a tiled gather CTA (the entry layout depends on it)
+constexpr int kTiledMaxCluster = 8;  // up to this many partitions: one fused launch per step (a cluster per range)
 constexpr double kTiledPairSlack = 0.125;  // largest padding of the paired layout
 
 // Layout of the tiled engine (shared-memory emissions, source partitions).

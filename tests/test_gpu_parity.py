@@ -121,6 +121,18 @@ def test_tiled_paired_and_run_layouts(outdeg, paired):
         compare(d, 40, mode, 5 + outdeg[0], engine="tiled", check_every=False, chunks=(9, 31))
 
 
+@pytest.mark.parametrize("q,outdeg", [(400000, (4, 8)), (1 << 20, (2, 6))])
+def test_tiled_cluster_sizes_and_two_launch_form(q, outdeg):
+    """16-bit emissions (p up to 1000) cut the sources into several
+    partitions: 400k neurons -> a cluster of several CTAs per range (one
+    launch per step); 1M neurons -> more partitions than a cluster holds,
+    the two-launch form with in-flow arrays."""
+    d = synth.random_system(q, 90 + outdeg[1], outdeg=outdeg, rules=(3, 4), p_range=(1, 1000), d_range=(0, 5),
+                            spikes=(0, 20))
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        compare(d, 8, mode, 17, engine="tiled", check_every=False, chunks=(3, 5))
+
+
 def test_auto_engine_choice():
     """AUTO: CTA-resident for small systems, tiled for one wave of tiled
     CTAs, the L2 gather for large low-degree systems whose emission copies
