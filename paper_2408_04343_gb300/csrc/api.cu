@@ -162,6 +162,7 @@ int materialize(snp_system* s) {
     d.rules_per_neuron = s->uniform_rules;
     d.identity = s->identity ? 1 : 0;
     d.seed = s->opt.seed;
+    philox_round_keys(d.seed, d.philox_rk);
     d.select = s->opt.select;
     d.max_p = s->max_p;
     if (cudaMemcpyAsync(s->d_self, &d, sizeof(DevSys), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)

@@ -50,6 +50,31 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
     return out;
 }
 
+// The same generator with the ten round keys given (rk[2r], rk[2r+1] = the
+// key after r Weyl increments, see philox_round_keys): kernels that take the
+// keys from their parameter block read them as constant operands.
+__device__ __forceinline__ Philox4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                    const uint32_t* rk) {
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long pA = (unsigned long long)kMulA * c0;
+        const unsigned long long pB = (unsigned long long)kMulB * c2;
+        const uint32_t n0 = (uint32_t)(pB >> 32) ^ c1 ^ rk[2 * r];
+        const uint32_t n2 = (uint32_t)(pA >> 32) ^ c3 ^ rk[2 * r + 1];
+        c0 = n0;
+        c1 = (uint32_t)pB;
+        c2 = n2;
+        c3 = (uint32_t)pA;
+    }
+    Philox4 out;
+    out.v[0] = c0;
+    out.v[1] = c1;
+    out.v[2] = c2;
+    out.v[3] = c3;
+    return out;
+}
+
 // ---- rules ----------------------------------------------------------------
 struct RuleF {
     int32_t k, j, c, p, d;
@@ -274,9 +299,10 @@ struct ModMagic {
 };
 __constant__ ModMagic kModMagic = ModMagic();
 
-template <int SEL>
+// RK: take the Philox round keys from rk (else derive them from seed).
+template <int SEL, bool RK = false>
 __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, uint32_t st, unsigned long long k,
-                                                  uint32_t nid, uint64_t seed) {
+                                                  uint32_t nid, uint64_t seed, const uint32_t* rk = nullptr) {
     SelOut o;
     o.c_after = n;
     o.emit = 0;
@@ -305,11 +331,15 @@ __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, ui
     uint32_t mask = e < 8u ? (rec.x >> (4u * e)) & 15u : (rec.y >> (4u * (e - 8u))) & 15u;
     if (mask == 0u) return o;
     if (SEL == SNP_SELECT_PHILOX && (mask & (mask - 1u)) != 0u) {
-        const int32_t cnt = __popc(mask);
-        const Philox4 x = philox4x32_10((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
-                                        (uint32_t)(seed >> 32));
-        int32_t idx = (int32_t)(((unsigned long long)x.v[0] * (unsigned long long)cnt) >> 32);
-        for (; idx > 0; --idx) mask &= mask - 1u;
+        const uint32_t cnt = (uint32_t)__popc(mask);
+        const Philox4 x = RK ? philox4x32_10_rk((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, rk)
+                             : philox4x32_10((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
+                                             (uint32_t)(seed >> 32));
+        const uint32_t idx = (uint32_t)(((unsigned long long)x.v[0] * cnt) >> 32);  // < cnt <= 4
+        // drop the idx lowest set bits, without a loop
+        mask = idx > 0u ? mask & (mask - 1u) : mask;
+        mask = idx > 1u ? mask & (mask - 1u) : mask;
+        mask = idx > 2u ? mask & (mask - 1u) : mask;
     }
     const uint32_t t = (uint32_t)(__ffs(mask) - 1);
     const uint32_t f = ((t < 2u ? rec.z : rec.w) >> (16u * (t & 1u))) & 0xffffu;

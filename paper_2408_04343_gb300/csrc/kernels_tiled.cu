@@ -377,7 +377,7 @@ __device__ __forceinline__ void finish_select_slice(const DevSys& s, const Tiled
         const uint32_t nid = neuron_id(s, slot);
         SelOut o;
         if (s.rec)
-            o = select_compiled<SEL>(rec, c, st, ks, nid, s.seed);
+            o = select_compiled<SEL, true>(rec, c, st, ks, nid, s.seed, s.philox_rk);
         else if (compact)
             o = select_neuron<true, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks, nid, s.seed);
         else
@@ -442,25 +442,28 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
         int32_t sl = my_lo + warp;
         int32_t c = 0, cn = 0;
         uint32_t st = 0u, stn = 0u;
+        long long in = 0, inn = 0;
         uint4 rec = make_uint4(0u, 0u, 0u, 0u), recn = rec;
-        auto load = [&](int32_t slc, int32_t& cc, uint32_t& ss, uint4& rr) {
+        // the state and the in-flow (summed over the cluster) of slice slc
+        auto load = [&](int32_t slc, int32_t& cc, uint32_t& ss, uint4& rr, long long& ii) {
             const int32_t slot = slc * kSlice + lane;
             if (slc < my_hi && slot < s.q) {
                 cc = s.C[slot];
                 ss = s.st[slot];
                 if (select && has_rec) rr = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
+                const uint32_t la = acc0 + (uint32_t)((slc - lo) * kSlice + lane) * 4u;
+                ii = 0;
+                for (int r = 0; r < tl.P; ++r) ii += (int32_t)ld_cluster_u32(cluster_map(la, (uint32_t)r));
             }
         };
-        load(sl, c, st, rec);
+        load(sl, c, st, rec, in);
         for (; sl < my_hi; sl += nw) {
-            load(sl + nw, cn, stn, recn);
-            const uint32_t la = acc0 + (uint32_t)((sl - lo) * kSlice + lane) * 4u;
-            long long in = 0;
-            for (int r = 0; r < tl.P; ++r) in += (int32_t)ld_cluster_u32(cluster_map(la, (uint32_t)r));
+            load(sl + nw, cn, stn, recn, inn);
             finish_select_slice<SEL, EB>(s, tl, select != 0, compact != 0, sl, lane, c, st, rec, in, ks, active);
             c = cn;
             st = stn;
             rec = recn;
+            in = inn;
         }
     }
     if (select) raise_step_activity(s.flags, ks, active);

@@ -71,6 +71,7 @@ struct DevSys {
     int32_t select;
     int32_t max_p;
     const void* rec;           // [q] 16-byte compiled rule records, or NULL (see compile_rules)
+    uint32_t philox_rk[20];    // Philox4x32-10 round keys of seed (philox_round_keys)
     int32_t rules_per_neuron;  // > 0: every neuron has this many rules (rule r0 = slot * R)
     int32_t identity;          // 1: slot order is the caller's order (orig[slot] = slot)
 };
@@ -110,6 +111,19 @@ struct HostPack {
 // otherwise.  A system is compiled only if every neuron fits (c < 64,
 // p < 32, d < 32); then one 16-byte load replaces the per-rule tests.
 bool compile_rules(const snp_desc* d, HostPack* hp);
+
+// The ten round keys of Philox4x32-10 for key (seed mod 2^32, seed >> 32):
+// round r uses the key advanced by r Weyl increments (0x9E3779B9,
+// 0xBB67AE85), as the generator's definition (Salmon et al., SC'11) gives.
+inline void philox_round_keys(uint64_t seed, uint32_t rk[20]) {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0;
+        rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 constexpr int kTiledMaxSub = 8;  // target windows per CTA of the tiled engine
 constexpr int kTiledThreads = 1024;  // threads of a tiled gather CTA (the entry layout depends on it)
