@@ -70,6 +70,38 @@ def test_mix_equals_alone_and_oracle():
     b.close()
 
 
+def test_200_requests_against_oracle_and_alone():
+    """A fixed subset of 200 served requests (q log-uniform in 300..20,000,
+    3..120 steps, arrivals spread while earlier ones run): every request's
+    result equals the oracle's and the same system stepped alone."""
+    reqs = _requests(200, 9, q_range=(300, 20000), steps_range=(3, 120))
+    b = libsnp.Batch(mem_budget=4 << 30)
+    systems, tickets = [], []
+    for d, steps, seed in reqs:
+        g = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=seed, deferred=True)
+        systems.append(g)
+        tickets.append(b.submit([g], [steps]))
+        time.sleep(0.0005)
+    for (d, steps, seed), g, t in zip(reqs, systems, tickets):
+        done = b.wait(t)[0]
+        m = g.get_state()
+        st = oracle.initial_state(d)
+        ex, S = oracle.run(d, st, steps, oracle.PHILOX, seed)
+        assert ex == done and m[3] == ex
+        assert (st[0] == m[0]).all() and (st[1] == m[1]).all() and (st[2] == m[2]).all()
+        if ex:
+            assert (g.spiking() == S).all()
+        alone = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=seed)
+        assert alone.step(steps) == done
+        a = alone.get_state()
+        assert all((x == y).all() for x, y in zip(a[:3], m[:3]))
+        alone.close()
+        g.close()
+    inf = b.info()
+    assert inf.finished == len(reqs) and inf.waiting == 0 and inf.running == 0
+    b.close()
+
+
 def test_late_short_request_overtakes_long_one():
     long_d = synth.random_system(400000, 5, outdeg=(8, 24), rules=(4, 4), d_range=(0, 5), spikes=(0, 20))
     short_d = synth.random_system(2000, 6, outdeg=(2, 32), rules=(3, 3), d_range=(0, 5), spikes=(0, 20))
