@@ -344,23 +344,35 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-// Address of the same shared-memory location in CTA `rank` of the cluster.
+// Address of the same shared-memory location in CTA `rank` of the cluster
+// (a pure function of its operands: offsets within a CTA's shared memory are
+// kept, so one mapped base serves a whole array).
 __device__ __forceinline__ uint32_t cluster_map(uint32_t a, uint32_t rank) {
     uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
     return r;
 }
+// This CTA's rank in its cluster.
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Volatile, so it stays after the cluster barrier (also volatile) that
+// publishes what it reads; no memory clobber, so ordinary loads and stores
+// around it are scheduled freely.
 __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t a) {
     uint32_t v;
-    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 
 // Finish of step kg and select of step kg+1 for one slice, from its in-flow.
 template <int SEL, int EB>
-__device__ __forceinline__ void finish_select_slice(const DevSys& s, const TiledSys& tl, bool select, bool compact,
-                                                    int32_t slice, int lane, int32_t c, uint32_t st, const uint4& rec,
-                                                    long long in, unsigned long long ks, bool& active) {
+__device__ __forceinline__ void finish_select_slice(const DevSys& s, bool select, bool compact, int32_t* Sk,
+                                                    uint32_t* Ek, int32_t slice, int lane, int32_t c, uint32_t st,
+                                                    const uint4& rec, long long in, unsigned long long ks,
+                                                    bool& active) {
     const int32_t slot = slice * kSlice + lane;
     const bool valid = slot < s.q;
     if (valid && (st >> kPendShift) == 0u) {
@@ -385,11 +397,11 @@ __device__ __forceinline__ void finish_select_slice(const DevSys& s, const Tiled
         c = o.c_after;
         active |= o.active;
         emit = (uint32_t)o.emit;
-        SNP_PICK(s.S, ks)[slot] = o.s;
+        Sk[slot] = o.s;
         if (o.st != st) s.st[slot] = o.st;  // most neurons stay open: skip the write
     }
     if (valid) s.C[slot] = c;
-    if (select) pk_put_slice<EB>(SNP_PICK(tl.Eg, ks), slice, lane, emit);
+    if (select) pk_put_slice<EB>(Ek, slice, lane, emit);
 }
 
 // One SNP step in one launch (partitions P <= kTiledMaxCluster): the P CTAs
@@ -439,31 +451,47 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
             const int64_t b0 = __ldg(subg) / 4, b1 = __ldg(subg + kTiledMaxSub) / 4;
             if (b1 > b0) prefetch_l2_range(reinterpret_cast<const char*>(tl.ent) + b0 * 16, (uint64_t)(b1 - b0) * 16);
         }
-        int32_t sl = my_lo + warp;
-        int32_t c = 0, cn = 0;
-        uint32_t st = 0u, stn = 0u;
-        long long in = 0, inn = 0;
-        uint4 rec = make_uint4(0u, 0u, 0u, 0u), recn = rec;
+        int32_t* const Sk = SNP_PICK(s.S, ks);
+        uint32_t* const Ek = SNP_PICK(tl.Eg, ks);
+        // the partner's accumulators when the cluster has two CTAs (the
+        // common case), mapped once
+        const uint32_t me = cluster_rank();
+        const uint32_t pbase = tl.P == 2 ? cluster_map(acc0, me ^ 1u) : 0u;
+        struct Stage {
+            int32_t c;
+            uint32_t st;
+            long long in;
+            uint4 rec;
+        };
         // the state and the in-flow (summed over the cluster) of slice slc
-        auto load = [&](int32_t slc, int32_t& cc, uint32_t& ss, uint4& rr, long long& ii) {
+        auto load = [&](int32_t slc, Stage& g) {
             const int32_t slot = slc * kSlice + lane;
             if (slc < my_hi && slot < s.q) {
-                cc = s.C[slot];
-                ss = s.st[slot];
-                if (select && has_rec) rr = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
-                const uint32_t la = acc0 + (uint32_t)((slc - lo) * kSlice + lane) * 4u;
-                ii = 0;
-                for (int r = 0; r < tl.P; ++r) ii += (int32_t)ld_cluster_u32(cluster_map(la, (uint32_t)r));
+                g.c = s.C[slot];
+                g.st = s.st[slot];
+                if (select && has_rec) g.rec = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
+                const int32_t li = (slc - lo) * kSlice + lane;
+                g.in = acc[li];
+                if (tl.P == 2) {
+                    g.in += (int32_t)ld_cluster_u32(pbase + (uint32_t)li * 4u);
+                } else {
+                    for (int r = 0; r < tl.P; ++r)
+                        if ((uint32_t)r != me)
+                            g.in += (int32_t)ld_cluster_u32(cluster_map(acc0 + (uint32_t)li * 4u, (uint32_t)r));
+                }
             }
         };
-        load(sl, c, st, rec, in);
-        for (; sl < my_hi; sl += nw) {
-            load(sl + nw, cn, stn, recn, inn);
-            finish_select_slice<SEL, EB>(s, tl, select != 0, compact != 0, sl, lane, c, st, rec, in, ks, active);
-            c = cn;
-            st = stn;
-            rec = recn;
-            in = inn;
+        Stage a = {0, 0u, 0, make_uint4(0u, 0u, 0u, 0u)}, b = a;
+        int32_t sl = my_lo + warp;
+        load(sl, a);
+        for (; sl < my_hi; sl += 2 * nw) {  // two stages, alternating roles
+            load(sl + nw, b);
+            finish_select_slice<SEL, EB>(s, select != 0, compact != 0, Sk, Ek, sl, lane, a.c, a.st, a.rec, a.in, ks,
+                                         active);
+            if (sl + nw >= my_hi) break;
+            load(sl + 2 * nw, a);
+            finish_select_slice<SEL, EB>(s, select != 0, compact != 0, Sk, Ek, sl + nw, lane, b.c, b.st, b.rec, b.in,
+                                         ks, active);
         }
     }
     if (select) raise_step_activity(s.flags, ks, active);
