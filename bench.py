@@ -151,49 +151,68 @@ def sum_over_ranks(ws, x: float) -> float:
     return float(t.item())
 
 
-def oracle_cpu_baseline(desc, mode, seed, budget_s=15.0):
-    """The oracle as it stands on a bounded sample: the first steps of the same system."""
+def oracle_cpu_baseline(desc, mode, seed, budget_s=12.0):
+    """The oracle as it stands on a bounded sample (the first steps of the same
+    system): its parallel pull form on every host core (the figure reported),
+    and its neuron-by-neuron form on one thread beside it."""
     import oracle
     oracle.build()
+    pr = oracle.PullRunner(desc)                       # in-lists: built once, not timed
     st = oracle.initial_state(desc)
     t0 = time.perf_counter()
-    ex, _ = oracle.run(desc, st, 1, mode, seed)
+    ex, _ = pr.run(st, 1, mode, seed)
     one = time.perf_counter() - t0
-    n = max(1, min(400, int(budget_s / max(one, 1e-6)) - 1))
+    n = max(1, min(2000, int(budget_s / max(one, 1e-6)) - 1))
     t0 = time.perf_counter()
-    ex2, _ = oracle.run(desc, st, n, mode, seed, step0=ex)
+    ex2, _ = pr.run(st, n, mode, seed, step0=ex)
     dt = time.perf_counter() - t0
-    return {"value": desc.num_syn * ex2 / dt, "unit": "synaptic updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"steps {ex}..{ex + ex2 - 1} of the 1,048,576-neuron workload, {dt:.1f} s, single thread"}
+    threads = oracle.threads()
+    st1 = oracle.initial_state(desc)
+    t0 = time.perf_counter()
+    e1, _ = oracle.run(desc, st1, 1, mode, seed)
+    one1 = time.perf_counter() - t0
+    n1 = max(1, min(400, int(budget_s / max(one1, 1e-6)) - 1))
+    t0 = time.perf_counter()
+    e2, _ = oracle.run(desc, st1, n1, mode, seed, step0=e1)
+    dt1 = time.perf_counter() - t0
+    return {"value": desc.num_syn * ex2 / dt, "unit": "synaptic updates/s", "cores": threads, "kind": "oracle",
+            "sample": f"steps {ex}..{ex + ex2 - 1} of the 1,048,576-neuron workload, {dt:.1f} s, "
+                      f"the oracle's parallel pull form on {threads} threads",
+            "single_thread_value": desc.num_syn * e2 / dt1,
+            "single_thread_sample": f"steps {e1}..{e1 + e2 - 1}, {dt1:.1f} s, neuron-by-neuron form, 1 thread"}
 
 
 def run_reference(args, ws, rank):
-    """The oracle arm: each step is one SNP step of the workload on the host."""
+    """The oracle arm: each bench step is one SNP step of the workload, run by
+    the oracle's parallel pull form on the host cores."""
     if rank != 0:
         return
     import oracle
     from paper_2408_04343_gb300 import synth
     oracle.build()
     desc, _, mode = synth.large_1m()
+    pr = oracle.PullRunner(desc)
     st = oracle.initial_state(desc)
     k = 0
     for _ in range(args.warmup):
-        ex, _ = oracle.run(desc, st, 1, mode, desc.seed, step0=k)
+        ex, _ = pr.run(st, 1, mode, desc.seed, step0=k)
         k += ex
     t0 = time.perf_counter()
     done = 0
     for _ in range(args.steps):
-        ex, _ = oracle.run(desc, st, 1, mode, desc.seed, step0=k)
+        ex, _ = pr.run(st, 1, mode, desc.seed, step0=k)
         k += ex
         done += ex
     dt = time.perf_counter() - t0
     v = desc.num_syn * done / dt
+    threads = oracle.threads()
     line = {"impl": "reference", "metric": "synaptic updates/s", "value": v, "unit": "synaptic updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / max(1, args.steps) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "engine": "CPU oracle, one SNP step per bench step"},
-            "cpu_baseline": {"value": v, "unit": "synaptic updates/s", "cores": 1, "kind": "oracle",
+            "config": {"workload": WORKLOAD, "engine": f"CPU oracle (parallel pull form, {threads} threads), "
+                                                       "one SNP step per bench step"},
+            "cpu_baseline": {"value": v, "unit": "synaptic updates/s", "cores": threads, "kind": "oracle",
                              "sample": f"{done} SNP steps of the 1,048,576-neuron workload"},
             "e2e": {"value": v, "unit": "synaptic updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -239,8 +258,11 @@ def main():
     stream = torch.cuda.Stream()
     T = args.call_steps
     engine = {"tiled": libsnp.SNP_ENGINE_TILED, "launch": libsnp.SNP_ENGINE_LAUNCH}[args.engine]
+    t_pack = time.perf_counter()  # load + pack + upload, outside the timed steps
     systems = [libsnp.System(desc, select=libsnp.SNP_SELECT_PHILOX, seed=desc.seed + 7919 * r + 104729 * rank,
                              engine=engine, stream=stream) for r in range(args.replicas)]
+    stream.synchronize()
+    t_pack = (time.perf_counter() - t_pack) / max(1, args.replicas)
     foot = sum(s.info().device_bytes for s in systems)
     for i in range(args.warmup):
         systems[i % len(systems)].step(T, wait=False)
@@ -266,8 +288,9 @@ def main():
     t_max = max_over_ranks(ws, dev_s)
     work = sum_over_ranks(ws, float(executed) * desc.num_syn)
     value = work / t_max
-    # launches of this library per call: begin, select, T-1 fused (plus one
-    # advance per captured chunk of 48), gather, finish
+    # launches of this library per call on this workload: begin, select,
+    # T-1 fused steps (plus one advance per captured chunk of 48), gather,
+    # finish -- the tiled engine's one-launch step (two source partitions)
     per_call = 4 + (T - 1) + (T - 1) // 48
     launches = per_call * args.steps
 
@@ -317,15 +340,17 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "engine": {"tiled": "tiled pull (emissions in shared memory): a gather and a select launch per SNP step, programmatic dependent launches replayed from CUDA graphs",
+            "config": {"workload": WORKLOAD, "engine": {"tiled": "tiled pull (emissions bit-packed in shared memory): one clustered launch per SNP step, programmatic dependent launches replayed from CUDA graphs",
                                                      "launch": "grid-wide pull, emissions gathered from L2, one fused launch per SNP step"}[args.engine],
                        "snp_steps_per_bench_step": T, "replicas_round_robin": len(systems),
                        "l2": f"inputs larger than L2: {len(systems)} replicas, {foot / 1e6:.0f} MB on the device, "
                              f"stepped round-robin", "parallelism": f"replicas x{ws}",
-                       "q": desc.q, "num_syn": desc.num_syn, "snp_steps_timed": int(executed)},
+                       "q": desc.q, "num_syn": desc.num_syn, "snp_steps_timed": int(executed),
+                       "snp_steps_per_s": work / desc.num_syn / t_max if t_max > 0 else None,
+                       "create_seconds_per_system": round(t_pack, 3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": {"tiled": "k_tiled_gather + k_tiled_select (one launch of each per SNP step; achieved = the step's algorithmic bytes / the step's live device time)",
+                         "kernel": {"tiled": "k_tiled_step (one launch per SNP step: gather, then select in thread-block clusters; achieved = a step's algorithmic bytes / its live device time)",
                                     "launch": "k_step_pull (fused gather + select, one launch per SNP step)"}[args.engine],
                          "algorithmic_bytes_per_snp_step": alg},
             "e2e": {"value": e2e_value, "unit": "synaptic updates/s", "h2d_bytes_per_step": 3 * 4 * q,

@@ -38,11 +38,16 @@ class _Sys(ct.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C, no vendor code)."""
+    """Compile the oracle with gcc (plain C, no vendor code); with OpenMP when
+    the compiler has it (only orc_run_pull's loops use it)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _OUT)
     return _OUT
 
@@ -64,6 +69,14 @@ def load():
             lib.orc_run.restype = ct.c_int
             lib.orc_is_halted.argtypes = [ct.POINTER(_Sys), ct.c_void_p, ct.c_void_p]
             lib.orc_is_halted.restype = ct.c_int
+            lib.orc_threads.argtypes = []
+            lib.orc_threads.restype = ct.c_int
+            lib.orc_in_lists.argtypes = [ct.POINTER(_Sys), ct.c_void_p, ct.c_void_p]
+            lib.orc_in_lists.restype = ct.c_int
+            lib.orc_run_pull.argtypes = [ct.POINTER(_Sys), ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                         ct.c_void_p, ct.c_uint64, ct.c_int64, ct.c_int, ct.c_uint64,
+                                         ct.c_void_p, ct.POINTER(ct.c_int64)]
+            lib.orc_run_pull.restype = ct.c_int
             _lib = lib
     return _lib
 
@@ -152,3 +165,33 @@ def run_trace(desc, nsteps: int, mode: int = FIRST, seed: int = 0):
             break
         out.append(tuple(x.copy() for x in state) + (S,))
     return out
+
+
+def threads() -> int:
+    """Threads orc_run_pull uses (1 without OpenMP)."""
+    return int(load().orc_threads())
+
+
+class PullRunner:
+    """The same definition with phase 2 as a pull over in-lists, each phase
+    split across threads (orc_run_pull).  Builds the in-lists once."""
+
+    def __init__(self, desc):
+        self.desc = desc
+        self.b = _Bound(desc)
+        self.in_off = np.zeros(desc.q + 1, np.int64)
+        self.in_src = np.zeros(max(1, int(desc.num_syn)), np.int32)
+        _check(load().orc_in_lists(ct.byref(self.b.s), _ptr(self.in_off), _ptr(self.in_src)))
+
+    def run(self, state, nsteps: int, mode: int = FIRST, seed: int = 0, step0: int = 0):
+        """Up to nsteps steps in place.  Returns (executed, S of the last executed step)."""
+        if mode not in (FIRST, PHILOX):
+            raise ValueError("orc_run_pull takes FIRST or PHILOX")
+        C, D, P = state
+        S = np.full(self.desc.q, -1, np.int32)
+        ex = ct.c_int64(0)
+        rc = load().orc_run_pull(ct.byref(self.b.s), _ptr(self.in_off), _ptr(self.in_src), _ptr(C), _ptr(D),
+                                 _ptr(P), ct.c_uint64(step0), ct.c_int64(nsteps), mode, ct.c_uint64(seed),
+                                 _ptr(S), ct.byref(ex))
+        _check(rc)
+        return int(ex.value), S

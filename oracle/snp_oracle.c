@@ -245,3 +245,117 @@ int orc_run(const orc_sys* s, int32_t* C, int32_t* D, int32_t* P, uint64_t step0
     free(Stmp);
     return ORC_OK;
 }
+
+/* ---- the same definition, pulled and in parallel ------------------------
+ * orc_run_pull applies exactly the three phases above, with phase 2 written
+ * as a pull over in-neighbour lists (C_{k+1}[j] gains the sum of E[i] over
+ * the synapses (i, j) when j receives) instead of a push along out-lists.
+ * Every phase is a loop over independent neurons; with OpenMP each loop is
+ * split across threads (without it the pragmas are ignored and the loops run
+ * in order).  Integer sums do not depend on order, so the result is the one
+ * orc_run gives.  in_off [q+1] / in_src [|syn|]: in-lists (orc_in_lists). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* In-neighbour lists of every neuron, sources in increasing order. */
+int orc_in_lists(const orc_sys* s, int64_t* in_off, int32_t* in_src) {
+    const int32_t q = s->q;
+    for (int32_t j = 0; j <= q; ++j) in_off[j] = 0;
+    for (int32_t i = 0; i < q; ++i)
+        for (int64_t e = s->syn_off[i]; e < s->syn_off[i + 1]; ++e) in_off[s->syn_tgt[e] + 1] += 1;
+    for (int32_t j = 0; j < q; ++j) in_off[j + 1] += in_off[j];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(q > 0 ? q : 1));
+    if (!fill) return ORC_ERR_OOM;
+    for (int32_t j = 0; j < q; ++j) fill[j] = in_off[j];
+    for (int32_t i = 0; i < q; ++i)
+        for (int64_t e = s->syn_off[i]; e < s->syn_off[i + 1]; ++e) in_src[fill[s->syn_tgt[e]]++] = i;
+    free(fill);
+    return ORC_OK;
+}
+
+int orc_run_pull(const orc_sys* s, const int64_t* in_off, const int32_t* in_src, int32_t* C, int32_t* D,
+                 int32_t* P, uint64_t step0, int64_t nsteps, int mode, uint64_t seed, int32_t* S,
+                 int64_t* executed) {
+    const int32_t q = s->q;
+    const size_t nq = (size_t)(q > 0 ? q : 1);
+    int64_t* Cn = (int64_t*)malloc(sizeof(int64_t) * nq);
+    int64_t* E = (int64_t*)malloc(sizeof(int64_t) * nq);
+    char* recv = (char*)malloc(nq);
+    int32_t* Sk = (int32_t*)malloc(sizeof(int32_t) * nq);
+    if (!Cn || !E || !recv || !Sk) {
+        free(Cn); free(E); free(recv); free(Sk);
+        return ORC_ERR_OOM;
+    }
+    *executed = 0;
+    int rc = ORC_OK;
+    for (int64_t t = 0; t < nsteps && rc == ORC_OK; ++t) {
+        const uint64_t step = step0 + (uint64_t)t;
+        /* halt test */
+        int busy = 0;
+#pragma omp parallel for reduction(| : busy) schedule(static)
+        for (int32_t i = 0; i < q; ++i)
+            busy |= P[i] != -1 || orc_count_applicable(s, i, C[i]) > 0;
+        if (!busy) break;
+        /* phase 1 */
+#pragma omp parallel for schedule(static)
+        for (int32_t i = 0; i < q; ++i) {
+            const int64_t n = C[i];
+            Cn[i] = n;
+            E[i] = 0;
+            recv[i] = 1;
+            Sk[i] = -1;
+            if (P[i] != -1 && D[i] == 0) {
+                E[i] = s->rp[P[i]];
+                P[i] = -1;
+            } else if (P[i] != -1) {
+                recv[i] = 0;
+            } else {
+                const int64_t a = orc_count_applicable(s, i, n);
+                if (a == 0) continue;
+                int64_t pick = 0;
+                if (mode == ORC_PHILOX) {
+                    uint32_t ctr[4] = {(uint32_t)step, (uint32_t)i, (uint32_t)(step >> 32), 0u};
+                    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+                    uint32_t x[4];
+                    orc_philox4x32_10(ctr, key, x);
+                    pick = (int64_t)(((uint64_t)x[0] * (uint64_t)a) >> 32);
+                }
+                const int64_t r = orc_nth_applicable(s, i, n, pick);
+                Sk[i] = (int32_t)r;
+                Cn[i] = n - s->rc[r];
+                if (s->rd[r] == 0) {
+                    E[i] = s->rp[r];
+                } else {
+                    P[i] = (int32_t)r;
+                    D[i] = s->rd[r];
+                    recv[i] = 0;
+                }
+            }
+        }
+        /* phase 2 (pull) and phase 3 */
+        int over = 0;
+#pragma omp parallel for reduction(| : over) schedule(static)
+        for (int32_t j = 0; j < q; ++j) {
+            int64_t c = Cn[j];
+            if (recv[j])
+                for (int64_t e = in_off[j]; e < in_off[j + 1]; ++e) c += E[in_src[e]];
+            if (P[j] != -1) D[j] -= 1;
+            over |= c > INT32_MAX || c < INT32_MIN;
+            C[j] = (int32_t)c;
+        }
+        if (over) rc = ORC_ERR_OVERFLOW;
+        memcpy(S, Sk, sizeof(int32_t) * (size_t)q);
+        *executed += 1;
+    }
+    free(Cn); free(E); free(recv); free(Sk);
+    return rc;
+}

@@ -409,3 +409,39 @@ def test_forgetting_rule_needs_exact_count():
     st = oracle.initial_state(d2)
     ex, S = oracle.run(d2, st, 5)
     assert ex == 1 and st[0].tolist() == [0, 0] and S.tolist() == [0, -1]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_parallel_pull_oracle_equals_definition_oracle(seed):
+    """orc_run_pull (phase 2 pulled over in-lists, each phase split across
+    threads) gives the state, spiking vector and executed step count of the
+    neuron-by-neuron oracle, step by step, with FIRST and PHILOX, up to and
+    past a fixed point."""
+    d = synth.random_system(3000 + 500 * seed, 40 + seed, outdeg=(1, 12), rules=(2, 4), d_range=(0, 4),
+                            spikes=(0, 15))
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        a = oracle.initial_state(d)
+        b = oracle.initial_state(d)
+        pr = oracle.PullRunner(d)
+        k = 0
+        for n in (1, 1, 5, 20, 60):
+            ea, Sa = oracle.run(d, a, n, mode, 99, step0=k)
+            eb, Sb = pr.run(b, n, mode, 99, step0=k)
+            assert ea == eb
+            for x, y in zip(a, b):
+                assert (x == y).all()
+            if ea:
+                assert (Sa == Sb).all()
+            k += ea
+    # a system that reaches a fixed point
+    h = synth.sort_system([3, 2, 1])
+    a, b = oracle.initial_state(h), oracle.initial_state(h)
+    ea, _ = oracle.run(h, a, 50)
+    eb, _ = oracle.PullRunner(h).run(b, 50)
+    assert ea == eb == 4 and all((x == y).all() for x, y in zip(a, b))
+
+
+def test_parallel_pull_oracle_reports_overflow():
+    d = synth.random_system(50, 5, outdeg=(20, 40), rules=(2, 2), spikes=(2**31 - 100, 2**31 - 50))
+    with pytest.raises(oracle.OracleOverflow):
+        oracle.PullRunner(d).run(oracle.initial_state(d), 20, oracle.FIRST)
