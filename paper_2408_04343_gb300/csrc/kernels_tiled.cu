@@ -283,9 +283,8 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
     kg_out = kg;
-    if (step_blocked(fl, s.step, kg)) return kPhaseBlocked;  // its barrier also publishes wb, acc, the mbarrier
-    allow_dependents();
-    if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
+    // the partition's emissions are requested before the fixed-point test, so
+    // the copy overlaps the flag read (a halted step waits for it and leaves)
     const uint32_t ebytes = (uint32_t)tl.part_words * 4u;
     if (threadIdx.x == 0) {
         const char* src = reinterpret_cast<const char*>(SNP_PICK(tl.Eg, kg) + (size_t)h * tl.part_words);
@@ -293,6 +292,12 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
         for (uint32_t o = 0; o < ebytes; o += kBulkChunk)
             bulk_g2s(esm + o, src + o, min((uint32_t)kBulkChunk, ebytes - o), ebar);
     }
+    if (step_blocked(fl, s.step, kg)) {  // its barrier also publishes wb, acc, the mbarrier
+        mbar_wait0(ebar, kWaitPolls);
+        return kPhaseBlocked;
+    }
+    allow_dependents();
+    if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 2ull) % 3ull)] = 0u;
     const bool landed = mbar_wait0(ebar, kWaitPolls);
     if (!__syncthreads_and(landed)) {  // the same answer in every thread of the CTA
         if (threadIdx.x == 0) atomicOr(fl + kFlagTimeout, 1u);
