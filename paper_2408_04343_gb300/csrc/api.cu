@@ -129,6 +129,9 @@ void build_plan(snp_system* s, std::vector<Piece>& plan) {
         tl.acc_words = tp.acc_words;
         tl.src_bits = tp.src_bits;
         tl.pairs = tp.pairs;
+        tl.rle = tp.rle;
+        tl.tstart = nullptr;
+        if (tp.rle) vec(&tl.tstart, tp.tstart);
         tl.ent_words = (int64_t)tp.ent.size();
         vec(&tl.sub, tp.sub);
         vec(&tl.ent, tp.ent);

@@ -37,7 +37,8 @@ int resident_max_smem();
 
 // Tiled engine (kernels_tiled.cu): device view of a TiledPack.
 struct TiledSys {
-    int32_t P, part_words, e_bits, G, acc_words, src_bits, pairs;
+    int32_t P, part_words, e_bits, G, acc_words, src_bits, pairs, rle;
+    const int32_t* tstart;  // run-length layout: first target of each thread's run, [G][kTiledThreads]
     const int32_t* sub;     // [G][kTiledMaxSub+1] window starts (words, multiples of 4); CTA g*P+h
     const uint32_t* ent;    // (dst_local << src_bits) | src_local
     int64_t ent_words;      // words of ent

@@ -135,6 +135,30 @@ __device__ __forceinline__ void pairs_merge(const uint32_t* __restrict__ Esm, ui
     cur = a1;
 }
 
+// Run-length layout, one 16-byte load: five 24-bit entries src | delta <<
+// sbits.  Each entry first advances the thread's target by delta -- adding
+// the run of the previous target to its accumulator when delta > 0 -- then
+// adds its emission to the run.  `cur` is the shared address of the current
+// target's accumulator.
+template <int EB>
+__device__ __forceinline__ void rle_vector(const uint32_t* __restrict__ Esm, const uint4& q, uint32_t wmask,
+                                           int sbits, uint32_t& cur, uint32_t& run) {
+    constexpr uint32_t M = 0xFFFFFFu;
+    const uint32_t e[5] = {q.x & M, __funnelshift_r(q.x, q.y, 24) & M, __funnelshift_r(q.y, q.z, 16) & M, q.z >> 8,
+                           q.w & M};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const uint32_t v = emission_of<EB>(Esm, e[i], wmask);
+        const uint32_t d = e[i] >> sbits;
+        const bool f = d != 0u;
+        red_add_if(cur, run, f);
+        run = (f ? 0u : run) + v;
+        cur += d * 4u;
+    }
+}
+
+enum : int { kLayoutRuns = 0, kLayoutPairs = 1, kLayoutRle = 2 };
+
 // ---- bulk copy of a partition's emissions into shared memory -------------
 __device__ __forceinline__ void mbar_init(uint32_t bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -194,11 +218,18 @@ constexpr int kWaitPolls = 1 << 20;     // each poll may suspend for a while; ~s
 // One batch of D 16-byte loads of a thread: its vectors u0 .. u0+D-1 (those
 // below nt), sorted indices s0 + u.  The window index k only moves forward;
 // a batch inside one window (the common case) takes its base once.
-template <int EB, bool PAIRS, int D>
+template <int EB, int LAYOUT, int D>
 __device__ __forceinline__ void gather_batch(const uint4 (&x)[D], int32_t u0, int32_t nt, int32_t s0,
                                              const int32_t* wb, int& k, const uint32_t* __restrict__ Esm,
                                              uint32_t acc0, int db, uint32_t wmask, int sbits, uint32_t& cur,
                                              uint32_t& run) {
+    constexpr bool PAIRS = LAYOUT == kLayoutPairs;
+    if constexpr (LAYOUT == kLayoutRle) {  // no target windows: the target is carried in cur
+#pragma unroll
+        for (int u = 0; u < D; ++u)
+            if (u0 + u < nt) rle_vector<EB>(Esm, x[u], wmask, sbits, cur, run);
+        return;
+    }
     if (u0 + D <= nt && s0 + u0 + D - 1 < wb[k + 1]) {  // k <= kTiledMaxSub - 1; wb[kTiledMaxSub] = group end
         const uint32_t abase = acc0 + ((uint32_t)k << db) * 4u;
 #pragma unroll
@@ -246,7 +277,7 @@ __device__ __forceinline__ void load_batch(uint4 (&x)[D], const uint4* col, int3
 // else kPhaseOk.  On return the accumulators are complete in this CTA.
 enum : int { kPhaseOk = 0, kPhaseBlocked = 1, kPhaseTimeout = 2 };
 
-template <int EB, bool PAIRS>
+template <int EB, int LAYOUT>
 __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSys& tl, int32_t t, uint32_t* Esm,
                                                   int* acc, int32_t* wb, unsigned long long* bar,
                                                   unsigned long long& kg_out) {
@@ -269,6 +300,7 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
     const uint4* col = reinterpret_cast<const uint4*>(tl.ent) + base + tid;
     uint4 qa[D], qb[D];
     load_batch(qa, col, 0, nt);
+    const int32_t tstart = LAYOUT == kLayoutRle ? __ldg(tl.tstart + (size_t)blockIdx.x * kTiledThreads + tid) : 0;
     if (threadIdx.x < 4) Esm[tl.part_words + threadIdx.x] = 0u;
     if (threadIdx.x == 0) mbar_init(ebar);
     for (int j = threadIdx.x; j < tl.acc_words; j += blockDim.x) acc[j] = 0;
@@ -307,25 +339,26 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
     // two batches in flight: the next batch loads while this one is added
     int k = 0;
     while (k + 1 < kTiledMaxSub && s0 >= wb[k + 1]) ++k;
-    uint32_t cur = acc0, run = 0u;  // paired layout: the target being summed and its sum so far
+    // paired and run-length layouts: the target being summed and its sum so far
+    uint32_t cur = acc0 + (LAYOUT == kLayoutRle ? (uint32_t)tstart * 4u : 0u), run = 0u;
     for (int32_t u = 0;;) {
         load_batch(qb, col, u + D, nt);
-        gather_batch<EB, PAIRS, D>(qa, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits, cur, run);
+        gather_batch<EB, LAYOUT, D>(qa, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits, cur, run);
         u += D;
         if (u >= nt) break;
         load_batch(qa, col, u + D, nt);
-        gather_batch<EB, PAIRS, D>(qb, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits, cur, run);
+        gather_batch<EB, LAYOUT, D>(qb, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits, cur, run);
         u += D;
         if (u >= nt) break;
     }
-    if (PAIRS) red_add_if(cur, run, run != 0u);
+    if (LAYOUT != kLayoutRuns) red_add_if(cur, run, run != 0u);
     __syncthreads();
     return kPhaseOk;
 }
 
 // Two-launch form (partitions P > kTiledMaxCluster): the gather writes
 // partition h's in-flow of step kg to tl.inflow; k_tiled_select sums them.
-template <int EB, bool PAIRS>
+template <int EB, int LAYOUT>
 __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl, int32_t t) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int32_t wb[kTiledMaxSub + 1];
@@ -333,7 +366,7 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_gather(DevSys s, TiledSys tl,
     uint32_t* Esm = smem;                                              // part_words + a zero word
     int* acc = reinterpret_cast<int*>(smem + tl.part_words + 4);
     unsigned long long kg;
-    if (tiled_gather_phase<EB, PAIRS>(s, tl, t, Esm, acc, wb, &bar, kg) != kPhaseOk) return;
+    if (tiled_gather_phase<EB, LAYOUT>(s, tl, t, Esm, acc, wb, &bar, kg) != kPhaseOk) return;
     const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
     const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
     const int32_t slot0 = lo * kSlice;
@@ -417,7 +450,7 @@ __device__ __forceinline__ void finish_select_slice(const DevSys& s, bool select
 // shared memory; a second cluster barrier keeps every accumulator alive until
 // the other CTAs have read it.  Each warp loads the next slice's state while
 // it works on the current one.
-template <int EB, bool PAIRS, int SEL>
+template <int EB, int LAYOUT, int SEL>
 __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, int32_t t, int select, int compact) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int32_t wb[kTiledMaxSub + 1];
@@ -440,7 +473,7 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
         }
     }
     unsigned long long kg;
-    const int ph = tiled_gather_phase<EB, PAIRS>(s, tl, t, Esm, acc, wb, &bar, kg);
+    const int ph = tiled_gather_phase<EB, LAYOUT>(s, tl, t, Esm, acc, wb, &bar, kg);
     if (ph == kPhaseBlocked) return;  // every CTA of the cluster returns here, before any cluster barrier
     cluster_sync();
     const unsigned long long ks = kg + 1ull;
@@ -620,7 +653,8 @@ static cudaError_t launch_dependent(void (*fn)(P...), unsigned grid, unsigned bl
 template <int EB>
 static cudaError_t launch_gather_eb(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st, size_t smem,
                                     int threads) {
-    auto fn = tl.pairs ? k_tiled_gather<EB, true> : k_tiled_gather<EB, false>;
+    auto fn = tl.rle ? k_tiled_gather<EB, kLayoutRle>
+                     : (tl.pairs ? k_tiled_gather<EB, kLayoutPairs> : k_tiled_gather<EB, kLayoutRuns>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     (void)threads;
@@ -640,7 +674,8 @@ static cudaError_t launch_select_t(const DevSys& s, const TiledSys& tl, int32_t 
 template <int EB, int SEL>
 static cudaError_t launch_step_eb(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st, size_t smem,
                                   bool select, bool compact) {
-    auto fn = tl.pairs ? k_tiled_step<EB, true, SEL> : k_tiled_step<EB, false, SEL>;
+    auto fn = tl.rle ? k_tiled_step<EB, kLayoutRle, SEL>
+                     : (tl.pairs ? k_tiled_step<EB, kLayoutPairs, SEL> : k_tiled_step<EB, kLayoutRuns, SEL>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};

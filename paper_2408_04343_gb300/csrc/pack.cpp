@@ -486,10 +486,12 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     tp->src_bits = src_bits;
     tp->cta_lo = cta_lo;
     const int db = 32 - src_bits;
-    // paired layout unless too many (target, partition) groups have an odd
-    // number of words
+    // run-length layout when a source fits 20 bits (at least 4 bits left for
+    // the target advance); otherwise the paired layout unless too many
+    // (target, partition) groups have an odd number of words
+    tp->rle = src_bits <= 20 ? 1 : 0;
+    int64_t odd = 0;
     {
-        int64_t odd = 0;
         for (int32_t s = 0; s < q; ++s) {
             auto b = isrc.begin() + ioff[s], e = isrc.begin() + ioff[s + 1];
             for (int h = 0; h < P && b != e; ++h) {
@@ -505,6 +507,79 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     tp->ent.reserve((size_t)hp.nsyn + (size_t)q + (size_t)G * kTiledMaxSub * 4);
     const uint32_t pad = (uint32_t)part_size;  // target 0 of the window, source = the zero word
     std::vector<int64_t> cur(kSlice), end(kSlice);
+    // the words of the other layouts, for the run-length layout to beat
+    const double other_words = (double)hp.nsyn + (tp->pairs ? (double)odd : 0.0) + 12.0 * G * kTiledMaxSub;
+    if (tp->rle) {
+        tp->tstart.assign((size_t)G * kTiledThreads, 0);
+        const int64_t T = kTiledThreads;
+        const uint32_t max_delta = (1u << (24 - src_bits)) - 1u;
+        std::vector<std::pair<uint32_t, uint32_t>> seq;  // (target local to the range, source local to the partition)
+        std::vector<std::vector<uint32_t>> runs(T);
+        for (int g = 0; g < NR; ++g) {
+            for (int h = 0; h < P; ++h) {
+                const int c = g * P + h;
+                int32_t* sb = tp->sub.data() + (size_t)c * (kTiledMaxSub + 1);
+                const int32_t lo_src = h * part_size;
+                const int32_t hi_src = (int32_t)std::min<int64_t>(q, (int64_t)(h + 1) * part_size);
+                seq.clear();
+                for (int64_t s = (int64_t)cta_lo[g] * kSlice; s < std::min<int64_t>(q, (int64_t)cta_lo[g + 1] * kSlice); ++s) {
+                    auto b = isrc.begin() + ioff[s], e = isrc.begin() + ioff[s + 1];
+                    const int64_t x0 = std::lower_bound(b, e, lo_src) - isrc.begin();
+                    const int64_t x1 = std::lower_bound(b, e, hi_src) - isrc.begin();
+                    const uint32_t local = (uint32_t)(s - (int64_t)cta_lo[g] * kSlice);
+                    for (int64_t x = x0; x < x1; ++x) seq.push_back({local, (uint32_t)(isrc[(size_t)x] - lo_src)});
+                }
+                // cut into T runs of nearly equal length and encode each
+                const int64_t n_e = (int64_t)seq.size();
+                size_t nvec = 0;
+                for (int64_t t = 0; t < T; ++t) {
+                    const int64_t a = n_e * t / T, b = n_e * (t + 1) / T;
+                    std::vector<uint32_t>& run = runs[t];
+                    run.clear();
+                    uint32_t cur = a < b ? seq[a].first : 0u;
+                    tp->tstart[(size_t)c * T + t] = (int32_t)cur;
+                    for (int64_t x = a; x < b; ++x) {
+                        uint32_t d = seq[x].first - cur;
+                        while (d > max_delta) {  // a long gap: advance with pad entries
+                            run.push_back(pad | (max_delta << src_bits));
+                            d -= max_delta;
+                        }
+                        run.push_back(seq[x].second | (d << src_bits));
+                        cur = seq[x].first;
+                    }
+                    while (run.size() % 5) run.push_back(pad);  // zero delta, zero emission
+                    nvec = std::max(nvec, run.size() / 5);
+                }
+                const size_t base = tp->ent.size() / 4;
+                sb[0] = (int32_t)(base * 4);
+                tp->ent.resize((base + nvec * T) * 4, 0u);
+                for (int64_t t = 0; t < T; ++t) {
+                    std::vector<uint32_t>& run = runs[t];
+                    while (run.size() < nvec * 5) run.push_back(pad);  // every thread the same count
+                    for (size_t u = 0; u < nvec; ++u) {
+                        const uint32_t* e = run.data() + u * 5;
+                        uint32_t* w = tp->ent.data() + (base + u * T + (size_t)t) * 4;
+                        w[0] = e[0] | (e[1] << 24);
+                        w[1] = (e[1] >> 8) | (e[2] << 16);
+                        w[2] = (e[2] >> 16) | (e[3] << 8);
+                        w[3] = e[4];
+                    }
+                }
+                for (int k = 1; k <= kTiledMaxSub; ++k) sb[k] = (int32_t)tp->ent.size();
+                if (tp->ent.size() > (size_t)INT32_MAX) return fail(SNP_ERR_UNSUPPORTED, "too many entries");
+            }
+        }
+        // short runs spend most of their words on padding: keep the run-length
+        // layout only when it is clearly smaller
+        if ((double)tp->ent.size() <= 0.9 * other_words) {
+            tp->pairs = 0;
+            return SNP_OK;
+        }
+        tp->rle = 0;
+        tp->tstart.clear();
+        tp->ent.clear();
+        std::fill(tp->sub.begin(), tp->sub.end(), 0);
+    }
     for (int g = 0; g < NR; ++g) {
         for (int h = 0; h < P; ++h) {
             int32_t* sb = tp->sub.data() + (size_t)(g * P + h) * (kTiledMaxSub + 1);

@@ -158,6 +158,15 @@ constexpr double kTiledPairSlack = 0.125;  // largest padding of the paired layo
 // adjacent: vector u of thread t sits at group offset u*T + t.  A warp's
 // load is then one contiguous 512-byte line set, while its lanes work on
 // targets far apart (no two lanes reducing into one accumulator).
+// Run-length layout (when the source field fits 20 bits): the target is not
+// stored.  A CTA's target-sorted in-edges are cut into kTiledThreads runs of
+// nearly equal length; each entry is 24 bits, src | delta << src_bits, delta
+// (24 - src_bits bits) = how many targets to advance before this entry, 0
+// on a run's first entry, whose target is tstart[thread]; longer gaps take
+// pad entries (source part_size, the zero word).  Five entries fill a
+// 16-byte vector (bits 24i..24i+23, the top 8 bits zero); each run is padded
+// with zero-delta pads to the CTA's longest run, and the vectors are stored
+// in the thread-contiguous order above (every thread has the same count).
 struct TiledPack {
     int e_bits = 0;          // bits per emission (2, 4, 8, 16)
     int P = 0;               // partitions
@@ -168,6 +177,8 @@ struct TiledPack {
     int acc_words = 0;       // shared in-flow accumulators per CTA (+ dummy)
     int src_bits = 0;        // low bits of an entry holding the source (0..part_size)
     int pairs = 0;           // 1: paired layout (every aligned word pair has one target)
+    int rle = 0;             // 1: run-length layout (24-bit entries, see below)
+    std::vector<int32_t> tstart;  // run-length layout: [G][kTiledThreads] first target of each thread's run
     std::vector<int32_t> sub;     // [G][kTiledMaxSub+1] window starts in ent (CTA g*P+h: range g, partition h)
     std::vector<uint32_t> ent;    // entries
     std::vector<int32_t> cta_lo;  // [G/P + 1] first slice of each range

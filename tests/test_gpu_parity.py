@@ -133,6 +133,15 @@ def test_tiled_cluster_sizes_and_two_launch_form(q, outdeg):
         compare(d, 8, mode, 17, engine="tiled", check_every=False, chunks=(3, 5))
 
 
+def test_tiled_run_length_layout():
+    """Long runs of in-edges per CTA thread (600k neurons, out-degree
+    8..24, two source partitions) take the run-length layout: 24-bit
+    entries, the target carried as a running offset."""
+    d = synth.random_system(600000, 66, outdeg=(8, 24), rules=(3, 4), d_range=(0, 5), spikes=(0, 20))
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        compare(d, 12, mode, 29, engine="tiled", check_every=False, chunks=(1, 4, 7))
+
+
 def test_auto_engine_choice():
     """AUTO: CTA-resident for small systems, tiled for one wave of tiled
     CTAs, the L2 gather for large low-degree systems whose emission copies
