@@ -16,6 +16,12 @@ skewed -- the 2,097,152-neuron system with truncated Zipf(2.1) out-degree on
           [1, 4096], 256 steps, on the engine AUTO picks (the headline value),
           the tiled, L2-gather and push engines and the ELL form; and its
           16,384-neuron copy on the dense M_Pi.
+families -- Sec. 6's families: the sort system on worst-case inputs
+          (n, ..., 1) for n up to 2,000 and the subset-sum-shaped stand-in
+          (q = sum(v) + 2n + 2, m = sum(v) + 4n + 2, z = n) for n up to
+          20,000: per n the device memory of each form against the paper's
+          element-count formulas, and the time of a run (sort: to its fixed
+          point, checked sorted; subset-sum-shaped: 200 Philox steps).
 All inputs are seeded synthetic systems (paper_2408_04343_gb300/synth.py).
 """
 from __future__ import annotations
@@ -35,7 +41,7 @@ def run(args, ws, rank, local):
     if rank == 0:
         B.build()
     torch.cuda.set_device(local)
-    fn = {"batch": batch, "serve": serve, "skewed": skewed}[args.workload]
+    fn = {"batch": batch, "serve": serve, "skewed": skewed, "families": families}[args.workload]
     line = fn(args, libsnp, synth)
     line.update({"n_gpus": ws, "data": "synthetic", "dtype": "int32", "higher_is_better": True})
     if rank == 0:
@@ -198,3 +204,51 @@ def skewed(args, libsnp, synth):
     return {"metric": "synaptic updates/s", "workload": "skewed", "value": res["auto"].get("syn_updates_per_s"),
             "unit": "synaptic updates/s", "engines": res,
             "config": {"q": d.q, "num_syn": d.num_syn, "steps": nsteps, "dense_copy_q": dd.q, "dense_copy_m": dd.m}}
+
+
+def families(args, libsnp, synth):
+    import torch
+    import numpy as np
+    forms = {"compressed": dict(form=libsnp.SNP_FORM_OPT), "ell": dict(form=libsnp.SNP_FORM_ELL),
+             "sparse": dict(form=libsnp.SNP_FORM_DENSE)}
+    paper_form = {"compressed": libsnp.SNP_FORM_OPT, "ell": libsnp.SNP_FORM_ELL, "sparse": libsnp.SNP_FORM_DENSE}
+    out = {"sort": [], "subset_sum_shaped": []}
+    dense_cap = 24 << 30   # the dense form is built on the host too: keep it to 24 GB
+
+    def run_one(d, fam, n, nsteps, select, check=None):
+        z = int(np.diff(d.syn_offsets).max()) if d.q else 0
+        row = {"n": n, "q": d.q, "m": d.m, "z": z, "forms": {}}
+        for name, kw in forms.items():
+            elems = libsnp.paper_format_elements(paper_form[name], d.q, d.m, z)
+            ent = {"paper_elements": elems, "paper_mb_at_2_bytes": elems * 2 / 1e6}
+            if name == "sparse" and d.m * d.q * 4 > dense_cap:
+                ent["unavailable"] = "dense m x q matrix above 24 GB"
+                row["forms"][name] = ent
+                continue
+            try:
+                g = libsnp.System(d, select=select, seed=d.seed, **kw)
+            except libsnp.SnpError as e:
+                ent["unavailable"] = str(e)
+                row["forms"][name] = ent
+                continue
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            done = g.step(nsteps)
+            dt = time.perf_counter() - t0
+            ent.update({"device_mb": g.info().device_bytes / 1e6, "steps": done, "run_ms": dt * 1e3,
+                        "us_per_step": dt / max(done, 1) * 1e6})
+            if check is not None:
+                ent["correct"] = bool(check(g.get_state()[0], done))
+            g.close()
+            row["forms"][name] = ent
+        out[fam].append(row)
+
+    for n in (10, 50, 100, 250, 500, 1000, 2000):
+        d = synth.sort_system(list(range(n, 0, -1)))
+        run_one(d, "sort", n, 4 * n + 10, libsnp.SNP_SELECT_FIRST,
+                check=lambda C, done, n=n: done == n + 1 and bool((C[2 * n:] == np.arange(1, n + 1)).all()))
+    for n in (100, 1000, 5000, 20000):
+        d = synth.subset_sum_shaped(n)
+        run_one(d, "subset_sum_shaped", n, 200, libsnp.SNP_SELECT_PHILOX)
+    return {"metric": "device memory and run time per instance size", "workload": "families", "value": None,
+            "unit": "MB / ms", **out}

@@ -291,18 +291,20 @@ int effective_engine(const snp_system* s) {
     if (s->opt.engine == SNP_ENGINE_RESIDENT) return SNP_ENGINE_RESIDENT;
     if (s->opt.engine == SNP_ENGINE_LAUNCH) return SNP_ENGINE_LAUNCH;
     if (s->opt.engine == SNP_ENGINE_TILED) return SNP_ENGINE_TILED;
-    if (s->q <= kAutoResidentMaxQ && resident_fits(s, nullptr)) return SNP_ENGINE_RESIDENT;
+    if (s->q <= kAutoResidentMaxQ && s->m <= kAutoResidentMaxRules && resident_fits(s, nullptr))
+        return SNP_ENGINE_RESIDENT;
     return s->has_tiled ? SNP_ENGINE_TILED : SNP_ENGINE_LAUNCH;
 }
 
 // Which layouts a system needs, from its options and size (before packing).
-static void plan_layouts(const snp_options& o, int32_t q, bool* want_tiled, bool* want_in_lists) {
+static void plan_layouts(const snp_options& o, int32_t q, int64_t m, bool* want_tiled, bool* want_in_lists) {
     if (o.form != SNP_FORM_OPT) {
         *want_tiled = *want_in_lists = false;
         return;
     }
     *want_tiled = o.prop == SNP_PROP_PULL &&
-                  (o.engine == SNP_ENGINE_TILED || (o.engine == SNP_ENGINE_AUTO && q > kAutoResidentMaxQ));
+                  (o.engine == SNP_ENGINE_TILED ||
+                   (o.engine == SNP_ENGINE_AUTO && (q > kAutoResidentMaxQ || m > kAutoResidentMaxRules)));
     // sliced ELL in-lists: the L2-gather and resident engines and the batch
     *want_in_lists = o.engine != SNP_ENGINE_TILED;
 }
@@ -422,7 +424,7 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     HostImage& im = *s->img;
     HostPack& hp = im.hp;
     bool want_tiled = false, want_in = false;
-    plan_layouts(o, desc->q, &want_tiled, &want_in);
+    plan_layouts(o, desc->q, desc->rule_offsets[desc->q], &want_tiled, &want_in);
     // the tiled layout needs no in-degree order; without it slots are the caller's neurons
     const int window = (o.form == SNP_FORM_OPT && o.engine == SNP_ENGINE_TILED) ? 0 : kSortWindow;
     st = pack_system(desc, o.form == SNP_FORM_OPT && o.prop == SNP_PROP_PUSH, false, window, &hp);

@@ -246,6 +246,59 @@ def serving_requests(rate_per_s: float, count: int, seed: int = 5005,
     return [Request(float(a), int(qv), int(sv), int(sd)) for a, qv, sv, sd in zip(t, qs, st, seeds)]
 
 
+def subset_sum_shaped(n: int, seed: int = 6006, v=None) -> SystemDesc:
+    """A stand-in with the sizes of Sec. 6's subset-sum family (the
+    construction itself is not in the paper): for n numbers v_i drawn from
+    U[0, 50] (or given), q = sum(v) + 2n + 2 neurons, m = sum(v) + 4n + 2
+    rules and maximum out-degree z = n, with delays and a nondeterministic
+    choice.  Neuron 0 (one spike, a -> a) feeds n "choice" neurons; each
+    choice neuron holds a -> a;0 and a -> a;1 (both apply to one spike: the
+    choice is the branch) and feeds its "check" neuron and the head of a
+    chain of v_i neurons (a -> a;0 each, the last into the output neuron);
+    each check neuron holds a -> a;0 and a^2 -> lambda and feeds the output
+    neuron, the last neuron, which holds a -> a;0 with no synapses."""
+    rng = np.random.default_rng(seed)
+    vals = [int(x) for x in (v if v is not None else rng.integers(0, 51, size=n))]
+    n = len(vals)
+    total = sum(vals)
+    q = total + 2 * n + 2
+    ks, js, cs, ps, ds, offs = [], [], [], [], [], [0]
+    def rule(k, j, c, p, d):
+        ks.append(k); js.append(j); cs.append(c); ps.append(p); ds.append(d)
+    src = 0
+    choice0, check0, chain0, out = 1, 1 + n, 1 + 2 * n, q - 1
+    targets = [[] for _ in range(q)]
+    rule(1, 0, 1, 1, 0); offs.append(len(ks))                       # source
+    targets[src] = list(range(choice0, choice0 + n))
+    heads = []
+    pos = chain0
+    for i in range(n):
+        heads.append(pos if vals[i] > 0 else -1)
+        pos += vals[i]
+    for i in range(n):                                               # choice neurons
+        rule(1, 0, 1, 1, 0); rule(1, 0, 1, 1, 1); offs.append(len(ks))
+        targets[choice0 + i] = [check0 + i] + ([heads[i]] if heads[i] >= 0 else [])
+    for i in range(n):                                               # check neurons
+        rule(1, 0, 1, 1, 0); rule(2, 0, 2, 0, 0); offs.append(len(ks))
+        targets[check0 + i] = [out]
+    pos = chain0
+    for i in range(n):                                               # chains
+        for t in range(vals[i]):
+            rule(1, 0, 1, 1, 0); offs.append(len(ks))
+            targets[pos + t] = [pos + t + 1] if t + 1 < vals[i] else [out]
+        pos += vals[i]
+    rule(1, 0, 1, 1, 0); offs.append(len(ks))                        # output
+    init = np.zeros(q, np.int32)
+    init[src] = 1
+    so = np.zeros(q + 1, np.int64)
+    so[1:] = np.cumsum([len(t) for t in targets])
+    tg = np.asarray([x for t in targets for x in t], np.int32)
+    a = lambda x: np.asarray(x, np.int32)
+    return SystemDesc(q=q, init_spikes=init, rule_offsets=np.asarray(offs, np.int64),
+                      rule_k=a(ks), rule_j=a(js), rule_c=a(cs), rule_p=a(ps), rule_d=a(ds),
+                      syn_offsets=so, syn_targets=tg, out_neuron=out, seed=seed, name=f"subset-sum-shaped-{n}")
+
+
 def sort_system(values) -> SystemDesc:
     """The sorting system of Sec. 6 for the given natural numbers (Table 1's
     layout): neurons i_1..i_n, s_1..s_n, o_1..o_n.

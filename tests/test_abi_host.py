@@ -132,3 +132,22 @@ def test_strerror_names_every_status():
     for st in range(8):
         assert lib.snp_strerror(st)
     assert lib.snp_strerror(99) == b"unknown status"
+
+
+def test_family_generators_have_the_papers_sizes():
+    """The sort family (q = 3n, m = n + n^2, z = n) and the subset-sum-shaped
+    stand-in (V = {1..100}: q = 5,252, m = 5,452, z = 100) have the sizes
+    Sec. 6 states, so the size formulas give its printed element counts."""
+    import numpy as np
+    for n in (3, 10, 100):
+        d = synth.sort_system(list(range(n, 0, -1)))
+        z = int(np.diff(d.syn_offsets).max())
+        assert (d.q, d.m, z) == (3 * n, n + n * n, n)
+    d = synth.subset_sum_shaped(100, v=list(range(1, 101)))
+    z = int(np.diff(d.syn_offsets).max())
+    assert (d.q, d.m, z) == (5252, 5452, 100)
+    assert libsnp.paper_format_elements(libsnp.SNP_FORM_OPT, d.q, d.m, z) == 562765
+    assert libsnp.paper_format_elements(libsnp.SNP_FORM_ELL, d.q, d.m, z) == 1128165
+    assert libsnp.paper_format_elements(libsnp.SNP_FORM_DENSE, d.q, d.m, z) == 28660765
+    r = synth.subset_sum_shaped(30, seed=5)           # v drawn from U[0, 50]
+    assert r.m - r.q == 2 * 30 and r.q >= 2 * 30 + 2

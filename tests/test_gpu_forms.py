@@ -106,3 +106,37 @@ def test_overflow_is_reported_in_every_form():
         with pytest.raises(libsnp.SnpError) as ei:
             g.step(5)
         assert ei.value.status == libsnp.SNP_ERR_OVERFLOW, form
+
+
+@pytest.mark.parametrize("form", list(FORMS) + ["opt"])
+def test_paper_families_sort_and_subset_sum_shaped(form):
+    """Sec. 6's families on every form: the sort system on a worst-case
+    input (n, n-1, ..., 1) halts after n + 1 steps with o_k = k (the closed
+    form) and matches the oracle step for step; the subset-sum-shaped
+    stand-in (delays, a branching choice per number) matches it under
+    Philox."""
+    n = 40
+    d = synth.sort_system(list(range(n, 0, -1)))
+    if form == "opt":
+        gs = libsnp.System(d, select=libsnp.SNP_SELECT_FIRST)
+        done = gs.step(4 * n)
+        C = gs.get_state()[0]
+        gs.close()
+    else:
+        done = compare(d, 4 * n, oracle.FIRST, 0, form, chunks=(5, 13))
+        st = oracle.initial_state(d)
+        oracle.run(d, st, 4 * n)
+        C = st[0]
+    assert done == n + 1
+    assert (C[2 * n:] == np.arange(1, n + 1)).all()
+    s = synth.subset_sum_shaped(12, seed=3)
+    if form == "opt":
+        gs = libsnp.System(s, select=libsnp.SNP_SELECT_PHILOX, seed=8)
+        done = gs.step(100)
+        st = oracle.initial_state(s)
+        ex, S = oracle.run(s, st, 100, oracle.PHILOX, 8)
+        C, D, P, _ = gs.get_state()
+        assert done == ex and (C == st[0]).all() and (D == st[1]).all() and (P == st[2]).all()
+        gs.close()
+    else:
+        compare(s, 100, oracle.PHILOX, 8, form, chunks=(7,))

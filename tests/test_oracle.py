@@ -445,3 +445,23 @@ def test_parallel_pull_oracle_reports_overflow():
     d = synth.random_system(50, 5, outdeg=(20, 40), rules=(2, 2), spikes=(2**31 - 100, 2**31 - 50))
     with pytest.raises(oracle.OracleOverflow):
         oracle.PullRunner(d).run(oracle.initial_state(d), 20, oracle.FIRST)
+
+
+def test_subset_sum_shaped_stand_in_runs_and_branches():
+    """The stand-in is a valid system with delays; its choice neurons each
+    have two applicable rules on one spike (the computation tree branches),
+    and with FIRST every value chain delivers sum(v) spikes to the output
+    neuron over the run (one per chain step), besides the check neurons'."""
+    import numpy as np
+    v = [3, 0, 5, 2]
+    d = synth.subset_sum_shaped(len(v), v=v)
+    st = oracle.initial_state(d)
+    S, E, halted = oracle.step(d, st, 0)
+    assert not halted and S[0] == 0          # the source fires
+    S, E, halted = oracle.step(d, st, 1)
+    # each choice neuron (1..n) holds one spike and two applicable rules
+    for i in range(1, 1 + len(v)):
+        r0 = int(d.rule_offsets[i])
+        assert S[i] == r0                     # FIRST takes a -> a;0
+    ex, _ = oracle.run(d, st, 200, oracle.FIRST, 0, step0=2)
+    assert ex < 200                           # reaches a fixed point
