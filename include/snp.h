@@ -212,6 +212,26 @@ int snp_set_state(snp_system* sys, const int32_t* C, const int32_t* D, const int
                   int64_t len, uint64_t step);
 int snp_get_info(const snp_system* sys, snp_info* info);
 
+/* ---- computation-tree exploration (Sec. 2 SV_k; Sec. 5's future work) ----
+ * The paper's semantics are nondeterministic: at step k every idle open
+ * neuron with applicable rules picks one of them, and each combination is a
+ * spiking vector of SV_k, one branch of the computation tree.  These two
+ * calls let a caller walk that tree with the library's own step:
+ *
+ * snp_count_choices: out[i] (caller's neuron ids, host or device buffer,
+ *   len >= q) = how many rules neuron i may choose at the next step -- the
+ *   applicable rules of an idle open neuron, 0 while a rule is pending.  The
+ *   branches of the next step are the products of these counts.
+ * snp_set_choices: idx[i] (host or device, len >= q, copied) = which of
+ *   neuron i's applicable rules (0-based, in rule order) the FIRST step of
+ *   the next snp_step call takes, instead of the system's selection; neurons
+ *   with no applicable rule ignore their entry.  The call's later steps
+ *   select as usual.  An index outside 0 .. count-1 makes that snp_step
+ *   return SNP_ERR_INVALID (the step has run, with the neuron's first rule).
+ * Both return SNP_ERR_BUSY while a batch owns the system.                  */
+int snp_count_choices(const snp_system* sys, int32_t* out, int64_t len);
+int snp_set_choices(snp_system* sys, const int32_t* idx, int64_t len);
+
 /* ---- batched and served forms ----------------------------------------- */
 /* A batch runs many independent systems in one persistent launch, each
  * system owned by one CTA for all its steps, systems taken largest first

@@ -69,6 +69,8 @@ def load():
             lib.orc_run.restype = ct.c_int
             lib.orc_is_halted.argtypes = [ct.POINTER(_Sys), ct.c_void_p, ct.c_void_p]
             lib.orc_is_halted.restype = ct.c_int
+            lib.orc_count_choices.argtypes = [ct.POINTER(_Sys), ct.c_void_p, ct.c_void_p, ct.c_void_p]
+            lib.orc_count_choices.restype = None
             lib.orc_threads.argtypes = []
             lib.orc_threads.restype = ct.c_int
             lib.orc_in_lists.argtypes = [ct.POINTER(_Sys), ct.c_void_p, ct.c_void_p]
@@ -195,3 +197,12 @@ class PullRunner:
                                  _ptr(S), ct.byref(ex))
         _check(rc)
         return int(ex.value), S
+
+
+def count_choices(desc, state) -> np.ndarray:
+    """Per neuron, how many rules it may choose at the next step (|A_i|, 0 while pending)."""
+    b = _Bound(desc)
+    C, D, P = state
+    out = np.zeros(desc.q, np.int32)
+    load().orc_count_choices(ct.byref(b.s), _ptr(C), _ptr(P), _ptr(out))
+    return out

@@ -359,3 +359,10 @@ int orc_run_pull(const orc_sys* s, const int64_t* in_off, const int32_t* in_src,
     free(Cn); free(E); free(recv); free(Sk);
     return rc;
 }
+
+/* Number of rules neuron i may choose at the next step (the definition of
+ * phase 1): |A_i| for an idle neuron, 0 while a rule is pending. */
+void orc_count_choices(const orc_sys* s, const int32_t* C, const int32_t* P, int32_t* out) {
+    for (int32_t i = 0; i < s->q; ++i)
+        out[i] = P[i] != -1 ? 0 : (int32_t)orc_count_applicable(s, i, C[i]);
+}

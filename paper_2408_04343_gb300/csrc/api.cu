@@ -357,6 +357,12 @@ int read_flags(snp_system* s, int64_t* exec) {
         return fail(SNP_ERR_OVERFLOW, "a spike count left the int32 range");
     }
     if (fl[kFlagTimeout]) return fail(SNP_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (fl[kFlagChoice]) {
+        const uint32_t zero = 0;
+        cudaMemcpyAsync(s->dev.flags + kFlagChoice, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream);
+        cudaStreamSynchronize(s->stream);
+        return fail(SNP_ERR_INVALID, "a forced choice index was out of range for its neuron");
+    }
     return SNP_OK;
 }
 
@@ -525,6 +531,16 @@ int snp_destroy(snp_system* s) {
     return SNP_OK;
 }
 
+// The system's descriptor with `forced` set (or cleared), also in its device
+// copy (read by the CTA-resident engine).
+static int set_forced(snp_system* s, const int32_t* forced) {
+    s->dev.forced = forced;
+    if (s->d_self &&
+        cudaMemcpyAsync(s->d_self, &s->dev, sizeof(DevSys), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        return cuda_fail("descriptor upload");
+    return SNP_OK;
+}
+
 int snp_step(snp_system* s, int64_t n, int64_t* steps_done) {
     if (!s) return fail(SNP_ERR_INVALID, "system is NULL");
     if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
@@ -532,9 +548,54 @@ int snp_step(snp_system* s, int64_t n, int64_t* steps_done) {
     if (n < 0) return fail(SNP_ERR_INVALID, "n < 0");
     if (steps_done) *steps_done = 0;
     if (n == 0) return SNP_OK;
+    if (s->choices_pending) {
+        // the first step alone, with the forced choices, then the rest
+        s->choices_pending = false;
+        int rc = set_forced(s, s->d_forced);
+        if (!rc) rc = run_steps(s, 1);
+        const int rc2 = set_forced(s, nullptr);
+        if (rc) return rc;
+        if (rc2) return rc2;
+        int64_t first = 0;
+        if ((rc = read_flags(s, &first))) return rc;
+        if (steps_done) *steps_done = first;
+        if (n == 1 || first == 0) return SNP_OK;
+        if ((rc = run_steps(s, n - 1))) return rc;
+        int64_t rest = 0;
+        if ((rc = read_flags(s, &rest))) return rc;
+        if (steps_done) *steps_done += rest;
+        return SNP_OK;
+    }
     int rc = run_steps(s, n);
     if (rc) return rc;
     if (steps_done) return read_flags(s, steps_done);
+    return SNP_OK;
+}
+
+int snp_set_choices(snp_system* s, const int32_t* idx, int64_t len) {
+    if (!s || !idx) return fail(SNP_ERR_INVALID, "NULL argument");
+    if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
+    if (int rc_ = materialize(s)) return rc_;
+    if (len < s->q) return fail(SNP_ERR_INVALID, "choices shorter than q");
+    std::vector<int32_t> host((size_t)s->q), slots((size_t)s->q);
+    if (is_device_ptr(idx)) {
+        if (cudaMemcpyAsync(host.data(), idx, sizeof(int32_t) * (size_t)s->q, cudaMemcpyDeviceToHost, s->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            return cuda_fail("choices copy");
+    } else {
+        std::memcpy(host.data(), idx, sizeof(int32_t) * (size_t)s->q);
+    }
+    for (int32_t slot = 0; slot < s->q; ++slot) slots[slot] = host[(size_t)s->perm[slot]];
+    if (!s->d_forced) {
+        s->d_forced = (int32_t*)sys_alloc(s, sizeof(int32_t) * (size_t)std::max(1, s->q));
+        if (!s->d_forced) return fail(SNP_ERR_OOM, "device allocation for forced choices failed");
+    }
+    if (cudaMemcpyAsync(s->d_forced, slots.data(), sizeof(int32_t) * (size_t)s->q, cudaMemcpyHostToDevice,
+                        s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return cuda_fail("choices upload");
+    s->choices_pending = true;
     return SNP_OK;
 }
 
@@ -546,7 +607,8 @@ static int export_vec(const snp_system* sc, int what, int32_t* out, int64_t len)
     if (len < s->q) return fail(SNP_ERR_INVALID, "output shorter than q");
     const bool dev = is_device_ptr(out);
     int32_t* dst = dev ? out : s->scratch;
-    if (launch_export(s->dev, s->d_rule_base, what, dst, -1, s->stream) != cudaSuccess) return cuda_fail("export");
+    if (launch_export(s->dev, s->d_rule_base, what, dst, -1, s->stream, s->compact) != cudaSuccess)
+        return cuda_fail("export");
     if (!dev) {
         if (cudaMemcpyAsync(out, s->scratch, sizeof(int32_t) * (size_t)s->q, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
             cudaStreamSynchronize(s->stream) != cudaSuccess)
@@ -556,6 +618,9 @@ static int export_vec(const snp_system* sc, int what, int32_t* out, int64_t len)
 }
 
 int snp_get_config(const snp_system* s, int32_t* out, int64_t len) { return export_vec(s, kExportConfig, out, len); }
+int snp_count_choices(const snp_system* s, int32_t* out, int64_t len) {
+    return export_vec(s, kExportChoices, out, len);
+}
 int snp_get_spiking(const snp_system* s, int32_t* out, int64_t len) { return export_vec(s, kExportSpiking, out, len); }
 int snp_get_status(const snp_system* s, int32_t* out, int64_t len) { return export_vec(s, kExportStatus, out, len); }
 int snp_get_pending(const snp_system* s, int32_t* out, int64_t len) { return export_vec(s, kExportPending, out, len); }

@@ -354,11 +354,76 @@ __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, ui
     return o;
 }
 
+// ---- forced choices (computation-tree exploration) ----------------------
+// Applicable rules of an idle neuron with n spikes, in index order: bit t of
+// the result (up to 32 rules) and the count.
+template <bool COMPACT>
+__device__ __forceinline__ int32_t count_applicable(const uint32_t* __restrict__ rules, int32_t r0, int32_t r1,
+                                                    int32_t n) {
+    int32_t cnt = 0;
+    for (int32_t r = r0; r < r1; ++r) cnt += rule_applies(n, load_rule<COMPACT>(rules, r)) ? 1 : 0;
+    return cnt;
+}
+
+// How many rules neuron `slot` may choose at the step about to run: the
+// applicable rules of an idle neuron, 0 while a rule is pending.
+template <bool COMPACT>
+__device__ __forceinline__ int32_t choices_of(const DevSys& s, int32_t slot) {
+    if ((s.st[slot] >> kPendShift) != 0u) return 0;
+    return count_applicable<COMPACT>(s.rules, rule_lo(s, slot), rule_hi(s, slot), s.C[slot]);
+}
+
+// The select phase with the choice given: an idle neuron with applicable
+// rules takes the fidx-th of them (0-based, index order); an index outside
+// 0 .. count-1 raises kFlagChoice and takes the first.  Pending neurons
+// complete or count down as in select_neuron.
+template <bool COMPACT>
+__device__ SelOut select_forced(const DevSys& s, int32_t slot, int32_t n, uint32_t st) {
+    const int32_t r0 = rule_lo(s, slot), r1 = rule_hi(s, slot);
+    SelOut o;
+    o.c_after = n;
+    o.emit = 0;
+    o.s = -1;
+    o.st = 0u;
+    o.active = false;
+    const uint32_t pend = st >> kPendShift;
+    if (pend != 0u) {
+        o.active = true;
+        if ((st & kDMask) == 0u) {
+            o.emit = load_rule<COMPACT>(s.rules, r0 + (int32_t)pend - 1).p;
+        } else {
+            o.st = st - 1u;
+        }
+        return o;
+    }
+    const int32_t cnt = count_applicable<COMPACT>(s.rules, r0, r1, n);
+    if (cnt == 0) return o;
+    int32_t idx = s.forced[slot];
+    if (idx < 0 || idx >= cnt) {
+        atomicOr(s.flags + kFlagChoice, 1u);
+        idx = 0;
+    }
+    int32_t pick = -1;
+    for (int32_t r = r0; r < r1 && pick < 0; ++r)
+        if (rule_applies(n, load_rule<COMPACT>(s.rules, r)) && idx-- == 0) pick = r;
+    const RuleF f = load_rule<COMPACT>(s.rules, pick);
+    o.active = true;
+    o.s = pick - r0;
+    o.c_after = n - f.c;
+    if (f.d == 0)
+        o.emit = f.p;
+    else
+        o.st = ((uint32_t)(o.s + 1) << kPendShift) | (uint32_t)(f.d - 1);
+    return o;
+}
+
 // The select phase of a slot through its compiled record when the system has
-// one, else through its rule table.
+// one, else through its rule table; with forced choices set (only for the
+// first step of a call, see snp_set_choices) through select_forced.
 template <bool COMPACT, int SEL>
 __device__ __forceinline__ SelOut select_slot(const DevSys& s, int32_t slot, int32_t n, uint32_t st,
                                               unsigned long long k) {
+    if (s.forced) return select_forced<COMPACT>(s, slot, n, st);
     if (s.rec)
         return select_compiled<SEL>(__ldg(reinterpret_cast<const uint4*>(s.rec) + slot), n, st, k, neuron_id(s, slot),
                                     s.seed);

@@ -8,7 +8,7 @@
 namespace snp {
 
 enum PullKind : int { kPullSelectOnly = 0, kPullFused = 1, kPullGatherOnly = 2 };
-enum ExportWhat : int { kExportConfig = 0, kExportStatus = 1, kExportPending = 2, kExportSpiking = 3 };
+enum ExportWhat : int { kExportConfig = 0, kExportStatus = 1, kExportPending = 2, kExportSpiking = 3, kExportChoices = 4 };
 
 // Grid-wide engine (kernels_step.cu).  t is the step index relative to the
 // system's device base step k.
@@ -18,7 +18,7 @@ cudaError_t launch_begin(const DevSys& s, cudaStream_t st);
 cudaError_t launch_advance(const DevSys& s, int32_t count, cudaStream_t st);
 cudaError_t launch_finish(const DevSys& s, int32_t tail, cudaStream_t st);
 cudaError_t launch_export(const DevSys& s, const int32_t* rule_base, int what, int32_t* out, int parity,
-                          cudaStream_t st);
+                          cudaStream_t st, bool compact = true);
 
 // CTA-resident engine (kernels_resident.cu): each CTA takes whole systems
 // from `work` (largest first as listed) and runs all their steps.

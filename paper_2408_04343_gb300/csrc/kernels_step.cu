@@ -230,7 +230,7 @@ cudaError_t launch_finish(const DevSys& s, int32_t tail, cudaStream_t st) {
 // ---- state export / import ------------------------------------------------
 
 __global__ void k_export(const DevSys s, const int32_t* __restrict__ rule_base, int what, int32_t* out,
-                         int parity) {
+                         int parity, int compact) {
     const int32_t slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= s.q) return;
     const int32_t nid = s.orig[slot];
@@ -248,14 +248,15 @@ __global__ void k_export(const DevSys s, const int32_t* __restrict__ rule_base, 
             v = x >= 0 ? rule_base[slot] + x : -1;
             break;
         }
+        case kExportChoices: v = compact ? choices_of<true>(s, slot) : choices_of<false>(s, slot); break;
     }
     out[nid] = v;
 }
 
 cudaError_t launch_export(const DevSys& s, const int32_t* rule_base, int what, int32_t* out, int parity,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool compact) {
     if (s.q == 0) return cudaSuccess;
-    k_export<<<(s.q + 255) / 256, 256, 0, st>>>(s, rule_base, what, out, parity);
+    k_export<<<(s.q + 255) / 256, 256, 0, st>>>(s, rule_base, what, out, parity, compact ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -616,7 +616,8 @@ __global__ void __launch_bounds__(256) k_tiled_select(DevSys s, TiledSys tl, int
         }
         uint32_t emit = 0u;
         if (SELECT && valid) {
-            const SelOut o = has_rec ? select_compiled<SEL>(rec[j], cj, st[j], ks, neuron_id(s, slot), s.seed)
+            const SelOut o = s.forced ? select_forced<COMPACT>(s, slot, cj, st[j])
+                             : has_rec ? select_compiled<SEL>(rec[j], cj, st[j], ks, neuron_id(s, slot), s.seed)
                                      : select_neuron<COMPACT, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), cj,
                                                                    st[j], ks, neuron_id(s, slot), s.seed);
             cj = o.c_after;

@@ -32,6 +32,7 @@ enum Flag : int {
     kFlagHalted = 3,   // set when a step found the system at a fixed point
     kFlagOverflow = 4, // a spike count left the int32 range (sticky until reported)
     kFlagTimeout = 5,  // a bounded wait gave up
+    kFlagChoice = 6,   // a forced choice index was out of range (snp_set_choices)
     kNumFlags = 8
 };
 // Device step counters of one system (uint64).
@@ -72,6 +73,7 @@ struct DevSys {
     int32_t max_p;
     const void* rec;           // [q] 16-byte compiled rule records, or NULL (see compile_rules)
     uint32_t philox_rk[20];    // Philox4x32-10 round keys of seed (philox_round_keys)
+    const int32_t* forced;     // [q] slot order: forced choice index of each neuron, or NULL (see select_forced)
     int32_t rules_per_neuron;  // > 0: every neuron has this many rules (rule r0 = slot * R)
     int32_t identity;          // 1: slot order is the caller's order (orig[slot] = slot)
 };

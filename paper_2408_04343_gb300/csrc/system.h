@@ -56,6 +56,8 @@ struct snp_system {
     int32_t max_p = 0, max_rules = 0;
     bool compact = true;
     bool compiled = false;     // compiled rule records uploaded (OPT form)
+    int32_t* d_forced = nullptr;  // [q] forced choices in slot order (allocated by snp_set_choices)
+    bool choices_pending = false; // the next snp_step's first step takes d_forced
     int32_t uniform_rules = 0;
     bool identity = false;
     int64_t in_entries = 0, out_entries = 0, rule_words = 0;

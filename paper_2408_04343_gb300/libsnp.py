@@ -102,6 +102,8 @@ _SIGS = {
     "snp_step_noalloc": (ct.c_int, [ct.POINTER(snp_device_system), ct.c_int32, ct.c_uint64, ct.c_uint64,
                                      ct.c_int64, _P, ct.POINTER(ct.c_int64)]),
     "snp_check_bounded_wait": (ct.c_int, [ct.c_int32]),
+    "snp_count_choices": (ct.c_int, [_P, ct.c_void_p, ct.c_int64]),
+    "snp_set_choices": (ct.c_int, [_P, ct.c_void_p, ct.c_int64]),
     "snp_strerror": (ct.c_char_p, [ct.c_int]),
     "snp_last_error": (ct.c_char_p, []),
 }
@@ -252,6 +254,18 @@ class System:
         k = ct.c_uint64(0)
         check(self._lib.snp_get_state(self.handle, _ptr(C), _ptr(D), _ptr(P), self.q, ct.byref(k)))
         return C, D, P, int(k.value)
+
+    def count_choices(self, out=None):
+        """snp_count_choices: per neuron, how many rules it may choose next."""
+        return self._get(self._lib.snp_count_choices, out)
+
+    def set_choices(self, idx):
+        """snp_set_choices: the choice index of every neuron for the first step
+        of the next step() call."""
+        if not hasattr(idx, "data_ptr"):
+            idx = np.ascontiguousarray(idx, np.int32)
+        n = idx.numel() if hasattr(idx, "numel") else idx.size
+        check(self._lib.snp_set_choices(self.handle, _ptr(idx), int(n)))
 
     def set_state(self, C, D, P, step: int):
         n = C.numel() if hasattr(C, "numel") else np.asarray(C).size

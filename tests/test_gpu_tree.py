@@ -1,0 +1,109 @@
+"""Computation-tree exploration on the GPU: snp_count_choices,
+snp_set_choices and paper_2408_04343_gb300.tree.explore against the
+oracle's forced-choice step (its FORCED mode) and its choice counts."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_04343_gb300 import libsnp, synth, tree
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ENGINES = {"launch": libsnp.SNP_ENGINE_LAUNCH, "resident": libsnp.SNP_ENGINE_RESIDENT,
+           "tiled": libsnp.SNP_ENGINE_TILED}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_04343_gb300 import build
+    build.build()
+    libsnp.load()
+
+
+def tiny(seed, q):
+    """A tiny random system with delays and overlapping rules (branching)."""
+    rng = np.random.default_rng(seed)
+    offs, ks, js, cs, ps, ds = [0], [], [], [], [], []
+    for _ in range(q):
+        for _ in range(int(rng.integers(1, 4))):
+            k = int(rng.integers(1, 4)); j = int(rng.integers(0, 3))
+            c = int(rng.integers(1, k + 1)); p = int(rng.integers(0, 3))
+            ks.append(k); js.append(j); cs.append(c); ps.append(p)
+            ds.append(int(rng.integers(0, 3)) if p > 0 else 0)
+        offs.append(len(ks))
+    out = [[b for b in range(q) if b != a and rng.random() < 0.5] for a in range(q)]
+    so = np.zeros(q + 1, np.int64)
+    so[1:] = np.cumsum([len(o) for o in out])
+    a32 = lambda x: np.asarray(x, np.int32)
+    return synth.SystemDesc(q=q, init_spikes=a32(rng.integers(1, 7, size=q)), rule_offsets=np.asarray(offs, np.int64),
+                            rule_k=a32(ks), rule_j=a32(js), rule_c=a32(cs), rule_p=a32(ps), rule_d=a32(ds),
+                            syn_offsets=so, syn_targets=a32([x for o in out for x in o]))
+
+
+def oracle_children(d, st, k):
+    """Every child of configuration st under the oracle's forced step."""
+    counts = oracle.count_choices(d, st)
+    if oracle.is_halted(d, st[0], st[2]):
+        return None
+    kids = set()
+    for combo in itertools.product(*[range(max(1, int(c))) for c in counts]):
+        s2 = tuple(x.copy() for x in st)
+        oracle.step(d, s2, k, oracle.FORCED, forced=np.asarray(combo, np.int32))
+        kids.add(tuple(tuple(int(v) for v in x) for x in s2))
+    return kids
+
+
+@pytest.mark.parametrize("engine", list(ENGINES))
+@pytest.mark.parametrize("seed", range(4))
+def test_explored_tree_equals_oracle_branches(engine, seed):
+    d = tiny(300 + seed, q=4 + seed % 3)
+    t = tree.explore(d, 4, max_branches=4096, engine=ENGINES[engine])
+    assert not t.truncated
+    children = {}
+    for parent, child, _ in t.edges:
+        children.setdefault(parent, set()).add(child)
+    for node, st in enumerate(t.states):
+        if t.depth[node] >= 4:
+            continue
+        want = oracle_children(d, st, t.depth[node])
+        if want is None:
+            assert node in t.halted and node not in children
+            continue
+        got = {tuple(tuple(int(v) for v in x) for x in t.states[c]) for c in children.get(node, ())}
+        assert got == want, (node, t.depth[node])
+
+
+@pytest.mark.parametrize("engine", list(ENGINES))
+def test_counts_forced_first_step_and_invalid_index(engine):
+    d = synth.random_system(3000, 17, outdeg=(2, 8), rules=(3, 4), d_range=(0, 3), spikes=(0, 12))
+    gs = libsnp.System(d, select=libsnp.SNP_SELECT_FIRST, engine=ENGINES[engine])
+    st = oracle.initial_state(d)
+    gs.step(3)
+    oracle.run(d, st, 3)
+    assert (gs.count_choices() == oracle.count_choices(d, st)).all()
+    # a forced first step, then first-applicable steps
+    counts = oracle.count_choices(d, st)
+    rng = np.random.default_rng(5)
+    choice = (rng.integers(0, 1 << 30, size=d.q) % np.maximum(counts, 1)).astype(np.int32)
+    gs.set_choices(choice)
+    assert gs.step(6) == 6
+    oracle.step(d, st, 3, oracle.FORCED, forced=choice)
+    oracle.run(d, st, 5, step0=4)
+    C, D, P, k = gs.get_state()
+    assert k == 9 and (C == st[0]).all() and (D == st[1]).all() and (P == st[2]).all()
+    # an index beyond a neuron's choices is refused after the step
+    bad = np.zeros(d.q, np.int32)
+    counts = gs.count_choices()
+    i = int(np.nonzero(counts > 0)[0][0])
+    bad[i] = counts[i]
+    gs.set_choices(bad)
+    with pytest.raises(libsnp.SnpError) as ei:
+        gs.step(1)
+    assert ei.value.status == libsnp.SNP_ERR_INVALID
+    assert gs.step(1) == 1      # the next call selects as usual
+    gs.close()

@@ -465,3 +465,43 @@ def test_subset_sum_shaped_stand_in_runs_and_branches():
         assert S[i] == r0                     # FIRST takes a -> a;0
     ex, _ = oracle.run(d, st, 200, oracle.FIRST, 0, step0=2)
     assert ex < 200                           # reaches a fixed point
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_count_choices_is_the_branching_of_sv_k(seed):
+    """orc_count_choices gives |A_i| per neuron: on tiny systems the product
+    over neurons equals the number of spiking vectors the independent
+    enumerator finds, level after level."""
+    d = tiny_random(2000 + seed, q=int(np.random.default_rng(seed).integers(2, 6)))
+    frontier = [oracle.initial_state(d)]
+    for k in range(4):
+        nxt = []
+        for st in frontier:
+            succ = py_successors(d, *st)
+            counts = oracle.count_choices(d, st)
+            if succ is None:
+                assert counts.sum() == 0
+                continue
+            assert int(np.prod(np.maximum(counts, 1))) == len(succ)
+            for forced, _ in succ[:6]:
+                s2 = tuple(x.copy() for x in st)
+                oracle.step(d, s2, k, oracle.FORCED, forced=np.asarray(forced, np.int32))
+                nxt.append(s2)
+        frontier = nxt[:12]
+
+
+def test_branch_enumeration_order_and_cap():
+    """paper_2408_04343_gb300.tree.branch_choices: every combination exactly
+    once (the product of the counts), neurons with one choice fixed at 0,
+    and the cap reported."""
+    import itertools
+    from paper_2408_04343_gb300.tree import branch_choices
+    counts = np.array([0, 3, 1, 2, 4], np.int32)
+    combos, cut = branch_choices(counts, 1000)
+    assert not cut and len(combos) == 24
+    want = {tuple(c) for c in itertools.product(*[range(max(1, int(x))) for x in counts])}
+    assert {tuple(int(v) for v in c) for c in combos} == want
+    combos, cut = branch_choices(counts, 10)
+    assert cut and len(combos) == 10
+    combos, cut = branch_choices(np.zeros(4, np.int32), 5)
+    assert not cut and len(combos) == 1
