@@ -232,6 +232,23 @@ int snp_get_info(const snp_system* sys, snp_info* info);
 int snp_count_choices(const snp_system* sys, int32_t* out, int64_t len);
 int snp_set_choices(snp_system* sys, const int32_t* idx, int64_t len);
 
+/* snp_branch_step: one forced step of nb configurations of the system at
+ * once (a level of the computation tree in one launch), leaving the
+ * system's own state untouched.  Arrays are [nb][q] int32 in the caller's
+ * neuron order, host or device: C, D (steps until the neuron reopens), P
+ * (global id of the pending rule, -1 none) and choices (as snp_set_choices)
+ * in; C_out, D_out, P_out out; executed[nb] = 1, or 0 for a configuration
+ * at a fixed point (copied unchanged); bad[nb] = 1 when one of its choice
+ * indices was out of range (that neuron took its first applicable rule);
+ * counts (optional, NULL to skip) = snp_count_choices of each resulting
+ * configuration, the branching of the next level.
+ * Needs the optimized form with in-neighbour lists (the launch or resident
+ * engine, or AUTO) and q <= 8192: SNP_ERR_UNSUPPORTED otherwise.
+ * SNP_ERR_OVERFLOW if a spike count left the int32 range.                 */
+int snp_branch_step(snp_system* sys, int32_t nb, const int32_t* C, const int32_t* D, const int32_t* P,
+                    const int32_t* choices, int32_t* C_out, int32_t* D_out, int32_t* P_out, int32_t* executed,
+                    int32_t* bad, int32_t* counts);
+
 /* ---- batched and served forms ----------------------------------------- */
 /* A batch runs many independent systems in one persistent launch, each
  * system owned by one CTA for all its steps, systems taken largest first

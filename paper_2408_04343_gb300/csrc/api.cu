@@ -572,6 +572,76 @@ int snp_step(snp_system* s, int64_t n, int64_t* steps_done) {
     return SNP_OK;
 }
 
+int snp_branch_step(snp_system* s, int32_t nb, const int32_t* C, const int32_t* D, const int32_t* P,
+                    const int32_t* choices, int32_t* C_out, int32_t* D_out, int32_t* P_out, int32_t* executed,
+                    int32_t* bad, int32_t* counts) {
+    if (!s) return fail(SNP_ERR_INVALID, "system is NULL");
+    if (nb < 0) return fail(SNP_ERR_INVALID, "nb < 0");
+    if (nb == 0) return SNP_OK;
+    if (!C || !D || !P || !choices || !C_out || !D_out || !P_out || !executed || !bad)
+        return fail(SNP_ERR_INVALID, "NULL argument");
+    if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
+    if (int rc_ = materialize(s)) return rc_;
+    if (s->opt.form != SNP_FORM_OPT || !s->has_in_lists || s->q > kBranchMaxQ)
+        return fail(SNP_ERR_UNSUPPORTED, "branch steps need the optimized form with in-lists and q <= 8192");
+    const size_t n = (size_t)nb * (size_t)s->q;
+    cudaStream_t st = s->stream;
+    // host buffers are staged through stream-ordered device copies
+    struct Buf {
+        const void* user;
+        void* dev;
+        size_t bytes;
+        bool in, host;
+    };
+    Buf bufs[10] = {{C, nullptr, n * 4, true, false},      {D, nullptr, n * 4, true, false},
+                    {P, nullptr, n * 4, true, false},      {choices, nullptr, n * 4, true, false},
+                    {C_out, nullptr, n * 4, false, false}, {D_out, nullptr, n * 4, false, false},
+                    {P_out, nullptr, n * 4, false, false}, {executed, nullptr, (size_t)nb * 4, false, false},
+                    {bad, nullptr, (size_t)nb * 4, false, false}, {counts, nullptr, n * 4, false, false}};
+    int rc = SNP_OK;
+    for (Buf& b : bufs) {
+        if (!b.user) continue;  // counts is optional
+        b.host = !is_device_ptr(b.user);
+        if (!b.host) {
+            b.dev = const_cast<void*>(b.user);
+            continue;
+        }
+        if (cudaMallocAsync(&b.dev, std::max<size_t>(b.bytes, 4), st) != cudaSuccess) {
+            b.dev = nullptr;
+            rc = fail(SNP_ERR_OOM, "staging buffer");
+            break;
+        }
+        if (b.in && cudaMemcpyAsync(b.dev, b.user, b.bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            rc = cuda_fail("staging copy");
+            break;
+        }
+    }
+    if (!rc && launch_branch_step(s->dev, s->d_rule_base, resident_e_bits(s->max_p), s->compact, nb,
+                                  (const int32_t*)bufs[0].dev, (const int32_t*)bufs[1].dev, (const int32_t*)bufs[2].dev,
+                                  (const int32_t*)bufs[3].dev, (int32_t*)bufs[4].dev, (int32_t*)bufs[5].dev,
+                                  (int32_t*)bufs[6].dev, (int32_t*)bufs[7].dev, (int32_t*)bufs[8].dev,
+                                  (int32_t*)bufs[9].dev, st) != cudaSuccess)
+        rc = cuda_fail("branch step");
+    for (Buf& b : bufs) {
+        if (!b.host || !b.dev) continue;
+        if (!rc && !b.in && cudaMemcpyAsync(const_cast<void*>(b.user), b.dev, b.bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = cuda_fail("staging copy");
+        cudaFreeAsync(b.dev, st);
+    }
+    uint32_t over = 0;
+    if (cudaMemcpyAsync(&over, s->dev.flags + kFlagOverflow, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return rc ? rc : cuda_fail("branch step");
+    if (rc) return rc;
+    if (over) {
+        const uint32_t zero = 0;
+        cudaMemcpyAsync(s->dev.flags + kFlagOverflow, &zero, 4, cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+        return fail(SNP_ERR_OVERFLOW, "a spike count left the int32 range");
+    }
+    return SNP_OK;
+}
+
 int snp_set_choices(snp_system* s, const int32_t* idx, int64_t len) {
     if (!s || !idx) return fail(SNP_ERR_INVALID, "NULL argument");
     if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");

@@ -378,7 +378,8 @@ __device__ __forceinline__ int32_t choices_of(const DevSys& s, int32_t slot) {
 // 0 .. count-1 raises kFlagChoice and takes the first.  Pending neurons
 // complete or count down as in select_neuron.
 template <bool COMPACT>
-__device__ SelOut select_forced(const DevSys& s, int32_t slot, int32_t n, uint32_t st) {
+__device__ SelOut select_forced_idx(const DevSys& s, int32_t slot, int32_t n, uint32_t st, int32_t fidx,
+                                    bool& bad) {
     const int32_t r0 = rule_lo(s, slot), r1 = rule_hi(s, slot);
     SelOut o;
     o.c_after = n;
@@ -398,9 +399,9 @@ __device__ SelOut select_forced(const DevSys& s, int32_t slot, int32_t n, uint32
     }
     const int32_t cnt = count_applicable<COMPACT>(s.rules, r0, r1, n);
     if (cnt == 0) return o;
-    int32_t idx = s.forced[slot];
+    int32_t idx = fidx;
     if (idx < 0 || idx >= cnt) {
-        atomicOr(s.flags + kFlagChoice, 1u);
+        bad = true;
         idx = 0;
     }
     int32_t pick = -1;
@@ -414,6 +415,16 @@ __device__ SelOut select_forced(const DevSys& s, int32_t slot, int32_t n, uint32
         o.emit = f.p;
     else
         o.st = ((uint32_t)(o.s + 1) << kPendShift) | (uint32_t)(f.d - 1);
+    return o;
+}
+
+// The same with the index from the system's forced-choice array; an index
+// out of range raises kFlagChoice.
+template <bool COMPACT>
+__device__ __forceinline__ SelOut select_forced(const DevSys& s, int32_t slot, int32_t n, uint32_t st) {
+    bool bad = false;
+    const SelOut o = select_forced_idx<COMPACT>(s, slot, n, st, s.forced[slot], bad);
+    if (bad) atomicOr(s.flags + kFlagChoice, 1u);
     return o;
 }
 

@@ -34,6 +34,13 @@ size_t resident_smem_bytes(int max_q, int e_bits);
 cudaError_t launch_resident(const DevSys* d_systems, const long long* d_nsteps, int nsys, unsigned int* d_work,
                             const ResidentPlan& plan, bool compact, int sel, cudaStream_t st);
 int resident_max_smem();
+// One forced step of nb configurations of one system (computation-tree
+// exploration); see k_branch_step.
+size_t branch_smem_bytes(int q, int e_bits);
+cudaError_t launch_branch_step(const DevSys& s, const int32_t* rule_base, int e_bits, bool compact, int nb,
+                               const int32_t* C0, const int32_t* D0, const int32_t* P0, const int32_t* ch,
+                               int32_t* C1, int32_t* D1, int32_t* P1, int32_t* ex, int32_t* bad, int32_t* counts,
+                               cudaStream_t st);
 
 // Tiled engine (kernels_tiled.cu): device view of a TiledPack.
 struct TiledSys {

@@ -14,6 +14,8 @@
 // test (Alg. 1 stop condition).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -166,6 +168,134 @@ cudaError_t launch_gather_results(const DevSys* d_systems, int nsys, unsigned lo
     if (nsys <= 0) return cudaSuccess;
     k_gather_results<<<(nsys + 255) / 256, 256, 0, st>>>(d_systems, nsys, d_out);
     return cudaGetLastError();
+}
+
+// ---- batched forced steps (computation-tree exploration) -----------------
+// One forced step of each of nb configurations of one system, one CTA per
+// configuration at a time.  Branch b reads C0/D0/P0 and its choice indices
+// at offset b*q in the caller's neuron order (D = steps until the neuron
+// reopens, P = global id of its pending rule or -1) and writes C1/D1/P1 and
+// executed[b] = 1, or 0 at a fixed point (the configuration is copied), and
+// bad[b] = 1 when a choice index was out of range (that neuron took its
+// first rule).  Phase 1 selects every neuron (select_forced_idx) into
+// shared memory and packs the emissions; phase 2 gathers the in-lists
+// against them and finishes the step, as run_resident does.
+template <bool COMPACT, int EB>
+__global__ void __launch_bounds__(256) k_branch_step(DevSys s, const int32_t* __restrict__ rule_base, int nb,
+                                                     const int32_t* __restrict__ C0, const int32_t* __restrict__ D0,
+                                                     const int32_t* __restrict__ P0, const int32_t* __restrict__ ch,
+                                                     int32_t* C1, int32_t* D1, int32_t* P1, int32_t* executed,
+                                                     int32_t* bad, int32_t* counts) {
+    extern __shared__ uint32_t sm[];
+    __shared__ int s_bad;
+    const int words = (int)(((long long)(s.nslices * 32 + 32) * EB + 31) / 32);
+    uint32_t* Esm = sm;
+    int32_t* csm = reinterpret_cast<int32_t*>(sm + words);  // c after the selection
+    uint32_t* ssm = reinterpret_cast<uint32_t*>(csm + s.nslices * 32);  // status after the selection
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // the words past the last slice stay zero (slot q, the in-lists' pad, emits 0)
+    for (int i = s.nslices * EB + threadIdx.x; i < words; i += blockDim.x) Esm[i] = 0u;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        const size_t off = (size_t)b * s.q;
+        if (threadIdx.x == 0) s_bad = 0;
+        __syncthreads();
+        bool act = false, badl = false;
+        for (int32_t sl = warp; sl < s.nslices; sl += nw) {
+            const int32_t slot = sl * kSlice + lane;
+            int32_t emit = 0;
+            if (slot < s.q) {
+                const int32_t nid = (int32_t)neuron_id(s, slot);
+                const int32_t c = C0[off + nid], d = D0[off + nid], p = P0[off + nid];
+                const uint32_t st = p >= 0 ? ((uint32_t)(p - rule_base[slot] + 1) << kPendShift) | (uint32_t)d : 0u;
+                const SelOut o = select_forced_idx<COMPACT>(s, slot, c, st, ch[off + nid], badl);
+                csm[slot] = o.c_after;
+                ssm[slot] = o.st;
+                emit = o.emit;
+                act |= o.active;
+            }
+            e_put_slice<EB>(Esm, sl, lane, emit);
+        }
+        if (badl) s_bad = 1;
+        const bool any = __syncthreads_or(act);
+        for (int32_t sl = warp; sl < s.nslices; sl += nw) {
+            const int32_t slot = sl * kSlice + lane;
+            long long in = 0;
+            if (any) {
+                const int32_t b0 = __ldg(s.slice_ptr + sl);
+                const int32_t w = __ldg(s.slice_ptr + sl + 1) - b0;
+                const int32_t* __restrict__ p = s.in_idx + (size_t)b0 * kSlice + lane;
+                for (int32_t col = 0; col < w; ++col) in += e_get<EB>(Esm, __ldg(p + col * kSlice));
+            }
+            if (slot < s.q) {
+                const int32_t nid = (int32_t)neuron_id(s, slot);
+                if (!any) {  // a fixed point: the configuration does not change
+                    C1[off + nid] = C0[off + nid];
+                    D1[off + nid] = D0[off + nid];
+                    P1[off + nid] = P0[off + nid];
+                    if (counts) counts[off + nid] = 0;
+                    continue;
+                }
+                const uint32_t st = ssm[slot];
+                long long c = csm[slot];
+                if ((st >> kPendShift) == 0u) c += in;
+                if (c > 2147483647ll) {
+                    atomicOr(s.flags + kFlagOverflow, 1u);
+                    c = 2147483647ll;
+                }
+                const uint32_t pend = st >> kPendShift;
+                C1[off + nid] = (int32_t)c;
+                D1[off + nid] = pend ? (int32_t)(st & kDMask) : 0;
+                P1[off + nid] = pend ? rule_base[slot] + (int32_t)pend - 1 : -1;
+                if (counts)  // the choices of the new configuration (its next level)
+                    counts[off + nid] =
+                        pend ? 0 : count_applicable<COMPACT>(s.rules, rule_lo(s, slot), rule_hi(s, slot), (int32_t)c);
+            }
+        }
+        if (threadIdx.x == 0) {
+            executed[b] = any ? 1 : 0;
+            bad[b] = s_bad;
+        }
+        __syncthreads();  // the next configuration reuses the shared memory
+    }
+}
+
+size_t branch_smem_bytes(int q, int e_bits) {
+    const long long nslices = ((long long)q + 31) / 32;
+    const long long words = ((nslices * 32 + 32) * e_bits + 31) / 32;
+    return (size_t)(words * 4 + nslices * 32 * 8);
+}
+
+template <bool C, int EB>
+static cudaError_t launch_branch_t(const DevSys& s, const int32_t* rule_base, int nb, const int32_t* C0,
+                                   const int32_t* D0, const int32_t* P0, const int32_t* ch, int32_t* C1, int32_t* D1,
+                                   int32_t* P1, int32_t* ex, int32_t* bad, int32_t* counts, cudaStream_t st) {
+    auto fn = k_branch_step<C, EB>;
+    const size_t smem = branch_smem_bytes(s.q, EB);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(nb, sms * 8));
+    fn<<<grid, 256, smem, st>>>(s, rule_base, nb, C0, D0, P0, ch, C1, D1, P1, ex, bad, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_branch_step(const DevSys& s, const int32_t* rule_base, int e_bits, bool compact, int nb,
+                               const int32_t* C0, const int32_t* D0, const int32_t* P0, const int32_t* ch,
+                               int32_t* C1, int32_t* D1, int32_t* P1, int32_t* ex, int32_t* bad, int32_t* counts,
+                               cudaStream_t st) {
+#define SNP_BR(CC, EE) \
+    return launch_branch_t<CC, EE>(s, rule_base, nb, C0, D0, P0, ch, C1, D1, P1, ex, bad, counts, st)
+    if (compact) {
+        if (e_bits == 4) SNP_BR(true, 4);
+        if (e_bits == 8) SNP_BR(true, 8);
+        SNP_BR(true, 16);
+    }
+    if (e_bits == 4) SNP_BR(false, 4);
+    if (e_bits == 8) SNP_BR(false, 8);
+    SNP_BR(false, 16);
+#undef SNP_BR
 }
 
 int resident_e_bits(int max_p) {

@@ -17,6 +17,7 @@ constexpr int kChunk = 48;                 // steps per captured CUDA graph
 constexpr int kSortWindow = 8192;          // in-degree sort window (slots)
 constexpr int kAutoResidentMaxQ = 8192;    // AUTO picks the resident engine up to here
 constexpr int64_t kAutoResidentMaxRules = 65536;  // ... and up to this many rules (one CTA does all the work)
+constexpr int kBranchMaxQ = 8192;           // snp_branch_step: one configuration per CTA, state in shared memory
 
 // Host-side layouts of a system kept until they are uploaded.
 struct HostImage {

@@ -104,6 +104,7 @@ _SIGS = {
     "snp_check_bounded_wait": (ct.c_int, [ct.c_int32]),
     "snp_count_choices": (ct.c_int, [_P, ct.c_void_p, ct.c_int64]),
     "snp_set_choices": (ct.c_int, [_P, ct.c_void_p, ct.c_int64]),
+    "snp_branch_step": (ct.c_int, [_P, ct.c_int32] + [ct.c_void_p] * 10),
     "snp_strerror": (ct.c_char_p, [ct.c_int]),
     "snp_last_error": (ct.c_char_p, []),
 }
@@ -266,6 +267,19 @@ class System:
             idx = np.ascontiguousarray(idx, np.int32)
         n = idx.numel() if hasattr(idx, "numel") else idx.size
         check(self._lib.snp_set_choices(self.handle, _ptr(idx), int(n)))
+
+    def branch_step(self, C, D, P, choices):
+        """snp_branch_step over [nb][q] numpy arrays: one forced step of each
+        configuration.  Returns (C1, D1, P1, executed, bad, counts), counts
+        being the choices of each new configuration."""
+        C, D, P, ch = (np.ascontiguousarray(x, np.int32) for x in (C, D, P, choices))
+        nb = C.shape[0]
+        C1, D1, P1, cnt = (np.empty_like(C) for _ in range(4))
+        ex = np.empty(nb, np.int32)
+        bad = np.empty(nb, np.int32)
+        check(self._lib.snp_branch_step(self.handle, nb, _ptr(C), _ptr(D), _ptr(P), _ptr(ch), _ptr(C1), _ptr(D1),
+                                        _ptr(P1), _ptr(ex), _ptr(bad), _ptr(cnt)))
+        return C1, D1, P1, ex, bad, cnt
 
     def set_state(self, C, D, P, step: int):
         n = C.numel() if hasattr(C, "numel") else np.asarray(C).size

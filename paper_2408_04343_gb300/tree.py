@@ -59,11 +59,21 @@ def branch_choices(counts: np.ndarray, limit: int):
 
 
 def explore(desc, depth: int, *, max_branches: int = 1024, max_nodes: int = 100000,
-            engine: int = libsnp.SNP_ENGINE_AUTO) -> Tree:
+            engine: int = libsnp.SNP_ENGINE_AUTO, batched: bool = None, chunk: int = 8192) -> Tree:
     """Breadth-first computation tree of `desc` from its initial
-    configuration, `depth` levels deep (level = step)."""
+    configuration, `depth` levels deep (level = step).
+
+    batched (default: when the system has at most 8,192 neurons): each level
+    runs as snp_branch_step launches of up to `chunk` configurations, which
+    also return the next level's choice counts; otherwise every branch is
+    one forced snp_step."""
+    if batched is None:
+        batched = desc.q <= 8192 and engine in (libsnp.SNP_ENGINE_AUTO, libsnp.SNP_ENGINE_LAUNCH,
+                                                libsnp.SNP_ENGINE_RESIDENT)
     sys_ = libsnp.System(desc, select=libsnp.SNP_SELECT_FIRST, engine=engine)
     try:
+        if batched:
+            return _explore_batched(sys_, desc, depth, max_branches, max_nodes, chunk)
         C0 = np.array(desc.init_spikes, np.int32)
         D0 = np.zeros(desc.q, np.int32)
         P0 = np.full(desc.q, -1, np.int32)
@@ -101,3 +111,49 @@ def explore(desc, depth: int, *, max_branches: int = 1024, max_nodes: int = 1000
         return tree
     finally:
         sys_.close()
+
+
+def _explore_batched(sys_, desc, depth, max_branches, max_nodes, chunk):
+    C0 = np.array(desc.init_spikes, np.int32)
+    D0 = np.zeros(desc.q, np.int32)
+    P0 = np.full(desc.q, -1, np.int32)
+    sys_.set_state(C0, D0, P0, 0)
+    tree = Tree(states=[(C0, D0, P0)], depth=[0], edges=[], halted=set(), truncated=set())
+    seen = {_key(C0, D0, P0): 0}
+    counts = {0: sys_.count_choices()}
+    frontier = [0]
+    for level in range(depth):
+        work = []  # (parent, choice vector)
+        for node in frontier:
+            combos, cut = branch_choices(counts[node], max_branches)
+            if cut:
+                tree.truncated.add(node)
+            work.extend((node, c) for c in combos)
+        nxt = []
+        for a in range(0, len(work), chunk):
+            part = work[a:a + chunk]
+            Cs = np.stack([tree.states[p][0] for p, _ in part])
+            Ds = np.stack([tree.states[p][1] for p, _ in part])
+            Ps = np.stack([tree.states[p][2] for p, _ in part])
+            ch = np.stack([c for _, c in part])
+            C1, D1, P1, ex, bad, cnt = sys_.branch_step(Cs, Ds, Ps, ch)
+            if bad.any():
+                raise RuntimeError("a choice index was out of range")
+            for r, (parent, choice) in enumerate(part):
+                if not ex[r]:
+                    tree.halted.add(parent)
+                    continue
+                key = _key(C1[r], D1[r], P1[r])
+                child = seen.get(key)
+                if child is None:
+                    if len(tree.states) >= max_nodes:
+                        return tree
+                    child = len(tree.states)
+                    seen[key] = child
+                    tree.states.append((C1[r].copy(), D1[r].copy(), P1[r].copy()))
+                    tree.depth.append(level + 1)
+                    counts[child] = cnt[r].copy()
+                    nxt.append(child)
+                tree.edges.append((parent, child, choice))
+        frontier = nxt
+    return tree

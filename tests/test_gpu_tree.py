@@ -58,11 +58,17 @@ def oracle_children(d, st, k):
     return kids
 
 
-@pytest.mark.parametrize("engine", list(ENGINES))
+@pytest.mark.parametrize("mode", ["launch", "resident", "tiled", "batched"])
 @pytest.mark.parametrize("seed", range(4))
-def test_explored_tree_equals_oracle_branches(engine, seed):
+def test_explored_tree_equals_oracle_branches(mode, seed):
+    """Per-branch forced steps on each engine, and the batched branch step
+    (one launch per level), give every configuration's children exactly as
+    the oracle's forced step enumerates them."""
     d = tiny(300 + seed, q=4 + seed % 3)
-    t = tree.explore(d, 4, max_branches=4096, engine=ENGINES[engine])
+    if mode == "batched":
+        t = tree.explore(d, 4, max_branches=4096, batched=True, chunk=7)
+    else:
+        t = tree.explore(d, 4, max_branches=4096, engine=ENGINES[mode], batched=False)
     assert not t.truncated
     children = {}
     for parent, child, _ in t.edges:
@@ -106,4 +112,40 @@ def test_counts_forced_first_step_and_invalid_index(engine):
         gs.step(1)
     assert ei.value.status == libsnp.SNP_ERR_INVALID
     assert gs.step(1) == 1      # the next call selects as usual
+    gs.close()
+
+
+def test_branch_step_matches_oracle_on_many_configurations():
+    """snp_branch_step on 300 configurations of a 2,000-neuron system with
+    delays (random reachable states, random valid choices): every result,
+    executed flag and next-level count equals the oracle's; an invalid index
+    is reported per configuration; the system's own state is untouched."""
+    d = synth.random_system(2000, 23, outdeg=(2, 10), rules=(2, 4), d_range=(0, 3), spikes=(0, 12))
+    gs = libsnp.System(d, select=libsnp.SNP_SELECT_FIRST)
+    rng = np.random.default_rng(4)
+    states = []
+    st = oracle.initial_state(d)
+    for k in range(300):
+        oracle.run(d, st, 1, oracle.PHILOX, 9, step0=k)
+        states.append(tuple(x.copy() for x in st))
+    C = np.stack([s_[0] for s_ in states]); D = np.stack([s_[1] for s_ in states]); P = np.stack([s_[2] for s_ in states])
+    counts = np.stack([oracle.count_choices(d, s_) for s_ in states])
+    ch = (rng.integers(0, 1 << 30, size=counts.shape) % np.maximum(counts, 1)).astype(np.int32)
+    ch[7, int(np.nonzero(counts[7] > 0)[0][0])] = 99     # one invalid index
+    before = gs.get_state()
+    C1, D1, P1, ex, bad, cnt = gs.branch_step(C, D, P, ch)
+    after = gs.get_state()
+    assert all((x == y).all() for x, y in zip(before[:3], after[:3])) and before[3] == after[3]
+    assert bad[7] == 1 and bad.sum() == 1
+    for b in range(len(states)):
+        s2 = tuple(x.copy() for x in states[b])
+        fc = ch[b].copy()
+        if b == 7:
+            fc[fc == 99] = 0
+        halted = oracle.is_halted(d, s2[0], s2[2])
+        if not halted:
+            oracle.step(d, s2, 0, oracle.FORCED, forced=fc)
+        assert ex[b] == (0 if halted else 1)
+        assert (C1[b] == s2[0]).all() and (D1[b] == s2[1]).all() and (P1[b] == s2[2]).all(), b
+        assert (cnt[b] == oracle.count_choices(d, s2)).all(), b
     gs.close()
