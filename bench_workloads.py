@@ -22,6 +22,10 @@ families -- Sec. 6's families: the sort system on worst-case inputs
           20,000: per n the device memory of each form against the paper's
           element-count formulas, and the time of a run (sort: to its fixed
           point, checked sorted; subset-sum-shaped: 200 Philox steps).
+tree   -- computation-tree exploration of the subset-sum-shaped stand-in
+          (n = 14: 2^14 branches when the choice neurons fire): branches per
+          second explored breadth first with the batched branch step (one
+          launch per level) and with one forced step per branch.
 All inputs are seeded synthetic systems (paper_2408_04343_gb300/synth.py).
 """
 from __future__ import annotations
@@ -41,7 +45,7 @@ def run(args, ws, rank, local):
     if rank == 0:
         B.build()
     torch.cuda.set_device(local)
-    fn = {"batch": batch, "serve": serve, "skewed": skewed, "families": families}[args.workload]
+    fn = {"batch": batch, "serve": serve, "skewed": skewed, "families": families, "tree": tree_workload}[args.workload]
     line = fn(args, libsnp, synth)
     line.update({"n_gpus": ws, "data": "synthetic", "dtype": "int32", "higher_is_better": True})
     if rank == 0:
@@ -252,3 +256,20 @@ def families(args, libsnp, synth):
         run_one(d, "subset_sum_shaped", n, 200, libsnp.SNP_SELECT_PHILOX)
     return {"metric": "device memory and run time per instance size", "workload": "families", "value": None,
             "unit": "MB / ms", **out}
+
+
+def tree_workload(args, libsnp, synth):
+    import torch
+    from paper_2408_04343_gb300 import tree
+    d = synth.subset_sum_shaped(14, seed=7007)
+    res = {}
+    for name, kw, depth in [("batched", dict(batched=True), 12), ("per_branch", dict(batched=False), 3)]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = tree.explore(d, depth, max_branches=1 << 16, max_nodes=1 << 20, **kw)
+        dt = time.perf_counter() - t0
+        res[name] = {"depth": depth, "nodes": len(t.states), "branches": len(t.edges), "seconds": dt,
+                     "branches_per_s": len(t.edges) / dt, "truncated": len(t.truncated)}
+    return {"metric": "computation-tree branches explored per second", "workload": "tree",
+            "value": res["batched"]["branches_per_s"], "unit": "branches/s",
+            "config": {"system": "subset-sum-shaped stand-in, n = 14", "q": d.q, "m": d.m}, **res}
