@@ -34,7 +34,8 @@ class _Sys(ct.Structure):
     _fields_ = [("q", ct.c_int32),
                 ("rule_off", ct.c_void_p), ("rk", ct.c_void_p), ("rj", ct.c_void_p),
                 ("rc", ct.c_void_p), ("rp", ct.c_void_p), ("rd", ct.c_void_p),
-                ("syn_off", ct.c_void_p), ("syn_tgt", ct.c_void_p)]
+                ("syn_off", ct.c_void_p), ("syn_tgt", ct.c_void_p),
+                ("term_off", ct.c_void_p), ("tk", ct.c_void_p), ("tj", ct.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -95,7 +96,8 @@ class _Bound:
         self.arrays = a
         self.s = _Sys(desc.q, _ptr(a["rule_offsets"]), _ptr(a["rule_k"]), _ptr(a["rule_j"]),
                       _ptr(a["rule_c"]), _ptr(a["rule_p"]), _ptr(a["rule_d"]),
-                      _ptr(a["syn_offsets"]), _ptr(a["syn_targets"]))
+                      _ptr(a["syn_offsets"]), _ptr(a["syn_targets"]),
+                      *(None if a.get(n) is None else _ptr(a[n]) for n in ("rule_term_offsets", "term_k", "term_j")))
 
 
 def _check(rc: int):

@@ -27,7 +27,10 @@
  *            - idle: the applicable rules A_i (in index order) are those with
  *              n >= k_r and (j_r = 0 ? n = k_r : (n - k_r) mod j_r = 0) and
  *              n >= c_r, for the regex a^k (a^j)* (type-4 form, Sec. 7; the
- *              three types of Sec. 2 are a^n exactly, a* and a+).  If A_i is
+ *              three types of Sec. 2 are a^n exactly, a* and a+).  A rule
+ *              given as a finite union of such terms, a^k1 (a^j1)* U ...
+ *              U a^kT (a^jT)*, applies when n >= c_r and n lies in any one
+ *              of the terms' languages (the same test, term by term).  If A_i is
  *              empty nothing happens; else one rule r is chosen and c_r
  *              spikes are consumed.  With d_r = 0 the neuron emits p_r now;
  *              with d_r > 0 it closes (P = r, D = d_r) and emits at k + d_r.
@@ -99,6 +102,9 @@ typedef struct {
     const int32_t* rd;         /* [m] delay */
     const int64_t* syn_off;    /* [q+1] out-lists */
     const int32_t* syn_tgt;    /* [|syn|] */
+    const int64_t* term_off;   /* [m+1] or NULL: rule r's regex is the union of */
+    const int32_t* tk;         /*   a^tk[t] (a^tj[t])* over t in [term_off[r],  */
+    const int32_t* tj;         /*   term_off[r+1]); rk and rj are then unused   */
 } orc_sys;
 
 static int orc_applicable(int64_t n, int32_t k, int32_t j, int32_t c) {
@@ -111,18 +117,26 @@ static int orc_applicable(int64_t n, int32_t k, int32_t j, int32_t c) {
     return n >= c;
 }
 
+/* Rule r against n spikes: its single term, or any term of its union. */
+static int orc_rule_applies(const orc_sys* s, int64_t r, int64_t n) {
+    if (!s->term_off) return orc_applicable(n, s->rk[r], s->rj[r], s->rc[r]);
+    for (int64_t t = s->term_off[r]; t < s->term_off[r + 1]; ++t)
+        if (orc_applicable(n, s->tk[t], s->tj[t], s->rc[r])) return 1;
+    return 0;
+}
+
 /* Number of applicable rules of idle neuron i with n spikes. */
 static int64_t orc_count_applicable(const orc_sys* s, int32_t i, int64_t n) {
     int64_t cnt = 0;
     for (int64_t r = s->rule_off[i]; r < s->rule_off[i + 1]; ++r)
-        cnt += orc_applicable(n, s->rk[r], s->rj[r], s->rc[r]);
+        cnt += orc_rule_applies(s, r, n);
     return cnt;
 }
 
 /* The idx-th applicable rule (0-based) of idle neuron i. */
 static int64_t orc_nth_applicable(const orc_sys* s, int32_t i, int64_t n, int64_t idx) {
     for (int64_t r = s->rule_off[i]; r < s->rule_off[i + 1]; ++r) {
-        if (orc_applicable(n, s->rk[r], s->rj[r], s->rc[r])) {
+        if (orc_rule_applies(s, r, n)) {
             if (idx == 0) return r;
             --idx;
         }

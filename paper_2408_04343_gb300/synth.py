@@ -15,6 +15,9 @@ expression and delay, then synapses):
                              consumed c, produced p (0 = forgetting), delay d
 * ``syn_offsets[q+1]``, ``syn_targets[|syn|]`` -- out-lists of syn, no
                              self-loops, no duplicates (Sec. 2)
+* optional ``rule_term_offsets[m+1]``, ``term_k/term_j[T]`` -- rule r's regex
+                             is the finite union of a^term_k[t](a^term_j[t])*
+                             over its terms; rule_k/rule_j are then unused
 
 Rule recipe (the evaluation workloads): per neuron, R-1 firing rules followed
 by one forgetting rule.  A firing rule draws k in [1,4], j in [0,3], c in [1,k],
@@ -44,6 +47,9 @@ class SystemDesc:
     out_neuron: int = 0
     seed: int = 0          # key of the nondeterministic choice (Philox)
     name: str = ""
+    rule_term_offsets: np.ndarray | None = None   # [m+1]: union expressions (optional)
+    term_k: np.ndarray | None = None
+    term_j: np.ndarray | None = None
 
     @property
     def m(self) -> int:
@@ -65,6 +71,10 @@ class SystemDesc:
             rule_d=np.ascontiguousarray(self.rule_d, np.int32),
             syn_offsets=np.ascontiguousarray(self.syn_offsets, np.int64),
             syn_targets=np.ascontiguousarray(self.syn_targets, np.int32),
+            rule_term_offsets=(None if self.rule_term_offsets is None
+                               else np.ascontiguousarray(self.rule_term_offsets, np.int64)),
+            term_k=None if self.term_k is None else np.ascontiguousarray(self.term_k, np.int32),
+            term_j=None if self.term_j is None else np.ascontiguousarray(self.term_j, np.int32),
         )
 
 
@@ -156,6 +166,26 @@ def random_system(q: int, seed: int, *, outdeg=(1, 8), zipf=None, rules=(3, 3),
 
 SEL_FIRST = 0
 SEL_PHILOX = 1
+
+
+def with_unions(desc: SystemDesc, seed: int, terms=(1, 3), k_max: int = 5, j_max: int = 3,
+                decoy: bool = True) -> SystemDesc:
+    """The same system with each rule's expression replaced by a union of
+    ``terms`` random terms a^k(a^j)* (k in [0, k_max], j in [0, j_max]).
+    With ``decoy`` the now unused rule_k/rule_j hold values that would make
+    no rule applicable, so a path that still read them would show."""
+    rng = np.random.default_rng(seed)
+    m = desc.m
+    cnt = rng.integers(terms[0], terms[1] + 1, size=m)
+    off = np.zeros(m + 1, np.int64)
+    off[1:] = np.cumsum(cnt)
+    T = int(off[-1])
+    tk = rng.integers(0, k_max + 1, size=T).astype(np.int32)
+    tj = rng.integers(0, j_max + 1, size=T).astype(np.int32)
+    rk = np.full(m, 1000, np.int32) if decoy else np.asarray(desc.rule_k, np.int32).copy()
+    rj = np.zeros(m, np.int32) if decoy else np.asarray(desc.rule_j, np.int32).copy()
+    return dataclasses.replace(desc, rule_k=rk, rule_j=rj, rule_term_offsets=off, term_k=tk, term_j=tj,
+                               name=(desc.name + "+unions") if desc.name else "unions")
 
 
 def small_1k(seed: int = 1001):

@@ -505,3 +505,135 @@ def test_branch_enumeration_order_and_cap():
     assert cut and len(combos) == 10
     combos, cut = branch_choices(np.zeros(4, np.int32), 5)
     assert not cut and len(combos) == 1
+
+
+# ---------------------------------------------------------------- finite unions
+
+def _terms_of(d, r):
+    return [(int(d.term_k[t]), int(d.term_j[t])) for t in range(d.rule_term_offsets[r], d.rule_term_offsets[r + 1])]
+
+
+def _union_member(n, terms, c):
+    """n in the union of the terms' languages, by listing each language's
+    word lengths k, k+j, k+2j, ... up to n (not by the modular test)."""
+    if n < c:
+        return False
+    for k, j in terms:
+        lengths = [k] if j == 0 else range(k, n + 1, j)
+        if n in lengths:
+            return True
+    return False
+
+
+def _single_term_union(d, decoy=True):
+    """d with every rule a^k(a^j)* written as a one-term union."""
+    import dataclasses
+    m = d.m
+    return dataclasses.replace(d, rule_term_offsets=np.arange(m + 1, dtype=np.int64),
+                               term_k=np.asarray(d.rule_k, np.int32).copy(), term_j=np.asarray(d.rule_j, np.int32).copy(),
+                               rule_k=np.full(m, 1000, np.int32) if decoy else d.rule_k,
+                               rule_j=np.zeros(m, np.int32) if decoy else d.rule_j)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_one_term_unions_equal_plain_rules(seed):
+    """A rule given as a one-term union behaves exactly as the plain rule
+    (rule_k/rule_j hold decoys that would make nothing applicable)."""
+    d = synth.random_system(300, 50 + seed, outdeg=(1, 6), rules=(1, 4), d_range=(0, 3), spikes=(0, 9))
+    u = _single_term_union(d)
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        a, b = oracle.initial_state(d), oracle.initial_state(u)
+        for k in range(25):
+            Sa, _, ha = oracle.step(d, a, k, mode, seed=seed)
+            Sb, _, hb = oracle.step(u, b, k, mode, seed=seed)
+            assert ha == hb and (Sa == Sb).all()
+            assert all((x == y).all() for x, y in zip(a, b))
+            if ha:
+                break
+
+
+def test_union_equal_to_one_expression():
+    """a^2(a^2)* U a^3(a^2)* is a^2 a* (every n >= 2), and a^1(a^3)* U
+    a^2(a^3)* U a^3(a^3)* is a+: systems written either way run identically."""
+    rules = [[(2, 1, 1, 1, 0), (1, 0, 1, 0, 0)], [(1, 1, 1, 2, 1)], [(3, 2, 2, 1, 0), (1, 1, 1, 1, 0)]]
+    syn = [(0, 1), (0, 2), (1, 0), (2, 1), (2, 0)]
+    plain = make_desc(3, rules, syn, [5, 2, 4])
+    import dataclasses
+    # rule 0: a^2 a*  -> two terms; rule 2: a+ (k=1, j=1) -> three terms; others one term
+    terms = [[(2, 2), (3, 2)], [(1, 0)], [(1, 3), (2, 3), (3, 3)], [(3, 2)], [(1, 1)]]
+    off = np.zeros(plain.m + 1, np.int64)
+    off[1:] = np.cumsum([len(t) for t in terms])
+    u = dataclasses.replace(plain, rule_term_offsets=off,
+                            term_k=np.asarray([k for t in terms for k, _ in t], np.int32),
+                            term_j=np.asarray([j for t in terms for _, j in t], np.int32),
+                            rule_k=np.full(plain.m, 1000, np.int32), rule_j=np.zeros(plain.m, np.int32))
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        ta = oracle.run_trace(plain, 40, mode, seed=3)
+        tb = oracle.run_trace(u, 40, mode, seed=3)
+        assert len(ta) == len(tb) and len(ta) > 5
+        for x, y in zip(ta, tb):
+            assert all((p == r).all() for p, r in zip(x, y))
+
+
+def test_union_hand_trace():
+    """Neuron 0 holds 5 spikes and one rule (a^4 U a^1(a^3)*)/a^2 -> a;
+    neuron 1 has (a^2 U a^5)/a -> a, neuron 2 forgets a^3.  By hand:
+    step 0: n0 = 5 is neither 4 nor 1 mod 3 -> idle; n1 = 0 idle; halted.
+    With 7 spikes instead (7 = 1 + 2*3): n0 fires, 7-2 = 5, sends 1 to n1 and
+    n2; then n0 = 5 idle, n1 = 1 idle -- but n2 = 1 idle: halted after one
+    step.  With 4 spikes: n0 fires (a^4), 4-2 = 2 -> n1 = 1, n2 = 1; step 1:
+    n0 = 2 idle (2 != 4, 2-1 = 1 not a multiple of 3): halted."""
+    import dataclasses
+    base = make_desc(3, [[(9, 0, 2, 1, 0)], [(9, 0, 1, 1, 0)], [(3, 0, 3, 0, 0)]], [(0, 1), (0, 2), (1, 2)], [5, 0, 0])
+    terms = [[(4, 0), (1, 3)], [(2, 0), (5, 0)], [(3, 0)]]
+    off = np.zeros(4, np.int64)
+    off[1:] = np.cumsum([len(t) for t in terms])
+    mk = lambda init: dataclasses.replace(base, init_spikes=np.asarray(init, np.int32), rule_term_offsets=off,
+                                          term_k=np.asarray([k for t in terms for k, _ in t], np.int32),
+                                          term_j=np.asarray([j for t in terms for _, j in t], np.int32))
+    st = oracle.initial_state(mk([5, 0, 0]))
+    assert oracle.run(mk([5, 0, 0]), st, 5)[0] == 0
+    d = mk([7, 0, 0]); st = oracle.initial_state(d)
+    ex, S = oracle.run(d, st, 5)
+    assert ex == 1 and S.tolist() == [0, -1, -1] and st[0].tolist() == [5, 1, 1]
+    d = mk([4, 0, 0]); st = oracle.initial_state(d)
+    ex, S = oracle.run(d, st, 5)
+    assert ex == 1 and st[0].tolist() == [2, 1, 1]
+    # n1 = 2 fires its a^2 term: send n1 two spikes as well
+    d = mk([7, 1, 0]); st = oracle.initial_state(d)
+    S, _, h = oracle.step(d, st, 0)
+    assert S.tolist() == [0, -1, -1] and st[0].tolist() == [5, 2, 1]
+    S, _, h = oracle.step(d, st, 1)
+    assert S.tolist() == [-1, 1, -1] and st[0].tolist() == [5, 1, 2]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_union_bruteforce_tree(seed):
+    """Random unions on tiny systems: the oracle's choice counts equal the
+    number of rules whose union lists n (by enumeration), and its forced
+    steps give every branch the enumerator finds."""
+    q = int(np.random.default_rng(seed).integers(2, 6))
+    d = synth.with_unions(tiny_random(2000 + seed, q=q), seed, terms=(1, 3), k_max=4, j_max=3)
+    frontier = [oracle.initial_state(d)]
+    for k in range(4):
+        nxt = []
+        for st in frontier:
+            C, D, P = st
+            A = []
+            for i in range(q):
+                rs = [r for r in range(d.rule_offsets[i], d.rule_offsets[i + 1])
+                      if _union_member(int(C[i]), _terms_of(d, r), int(d.rule_c[r]))]
+                A.append(rs if P[i] == -1 else [])
+            assert oracle.count_choices(d, st).tolist() == [len(a) for a in A]
+            halted = all(not a for a in A) and all(p == -1 for p in P)
+            assert oracle.is_halted(d, C, P) == halted
+            if halted:
+                continue
+            for combo in itertools.islice(itertools.product(*[range(max(1, len(a))) for a in A]), 16):
+                s2 = tuple(x.copy() for x in st)
+                S, _, _ = oracle.step(d, s2, k, oracle.FORCED, forced=np.asarray(combo, np.int32))
+                for i in range(q):
+                    if A[i]:
+                        assert S[i] == A[i][combo[i]]
+                nxt.append(s2)
+        frontier = nxt[:24]
