@@ -132,7 +132,24 @@ typedef struct snp_options {
  *   num_syn            |syn|.
  *   syn_offsets[q+1]   out-list of neuron i: syn_targets[syn_offsets[i] ..
  *   syn_targets[]      syn_offsets[i+1]-1]; no self-loops, no duplicates.
- *   out_neuron         i_out (kept, not used by the step).                */
+ *   out_neuron         i_out (kept, not used by the step).
+ *   rule_term_offsets  optional (NULL: every rule has the single term
+ *     [m+1]            (rule_k, rule_j)).  When set, rule r's expression is
+ *   term_k/term_j[]    the finite union of a^term_k[t] (a^term_j[t])* over
+ *                      t = rule_term_offsets[r] .. rule_term_offsets[r+1]-1
+ *                      (the type-4 form of Sec. 7, several terms per rule):
+ *                      the rule applies to n spikes when n >= c and n is in
+ *                      any term's language.  rule_k and rule_j are then not
+ *                      read and may be NULL.  rule_term_offsets[0] = 0,
+ *                      monotone, at least one term per rule; term_k, term_j
+ *                      >= 0.  The step runs unions through compiled
+ *                      per-neuron applicability tables only, so snp_create
+ *                      returns SNP_ERR_UNSUPPORTED unless every neuron has
+ *                      at most 4 rules, c < 64, p < 32, d < 32 and
+ *                      K + L <= 14, with K = 1 + the largest term_k or c of
+ *                      the neuron and L the lcm of its non-zero term_j.
+ *                      Zero-initialise the struct so that callers unaware
+ *                      of these fields leave them NULL.                  */
 typedef struct snp_desc {
     int32_t q;
     const int32_t* init_spikes;
@@ -146,6 +163,9 @@ typedef struct snp_desc {
     const int64_t* syn_offsets;
     const int32_t* syn_targets;
     int32_t out_neuron;
+    const int64_t* rule_term_offsets;
+    const int32_t* term_k;
+    const int32_t* term_j;
 } snp_desc;
 
 /* Sizes of a created system, for accounting and roofline arithmetic. */

@@ -87,7 +87,7 @@ void build_plan(snp_system* s, std::vector<Piece>& plan) {
     vec(&d.rule_off, hp.rule_off);
     vec(&d.rules, hp.rules);
     d.rec = nullptr;
-    if (s->opt.form == SNP_FORM_OPT && !hp.rec.empty()) vec(&d.rec, hp.rec);
+    if ((s->opt.form == SNP_FORM_OPT || s->unions) && !hp.rec.empty()) vec(&d.rec, hp.rec);
     vec(&d.orig, hp.perm);
     vec(&s->d_rule_base, hp.rule_base);
     vec(&d.C, hp.C0);
@@ -440,6 +440,13 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
         delete s;
         return st;
     }
+    // union expressions step through the compiled records only (on every form)
+    s->unions = desc->rule_term_offsets != nullptr;
+    if (s->unions && hp.rec.empty()) {
+        delete s;
+        return fail(SNP_ERR_UNSUPPORTED,
+                    "rules given as unions need <= 4 rules per neuron, c < 64, p < 32, d < 32 and K + L <= 14");
+    }
     if (want_tiled) {
         int dev = 0, sms = 0, optin = 0;
         cudaGetDevice(&dev);
@@ -484,7 +491,7 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     s->uniform_rules = hp.uniform_rules;
     s->identity = hp.identity;
     s->compact = hp.compact;
-    s->compiled = s->opt.form == SNP_FORM_OPT && !hp.rec.empty();
+    s->compiled = (s->opt.form == SNP_FORM_OPT || s->unions) && !hp.rec.empty();
     s->in_entries = (int64_t)hp.in_idx.size();
     s->out_entries = (int64_t)hp.out_idx.size();
     if (o.form == SNP_FORM_ELL) {

@@ -299,6 +299,24 @@ struct ModMagic {
 };
 __constant__ ModMagic kModMagic = ModMagic();
 
+// Applicable rules of an idle neuron with n spikes from its compiled record:
+// bit t set when rule t applies (n indexes the table directly below K and
+// by K + (n - K) mod L from K on).
+__device__ __forceinline__ uint32_t compiled_mask(const uint4& rec, int32_t n) {
+    const uint32_t K = (rec.y >> 24) & 15u, L = rec.y >> 28;
+    uint32_t e = (uint32_t)n;
+    if (e >= K) {
+        const unsigned long long low = kModMagic.m[L] * (unsigned long long)(e - K);
+        e = K + (uint32_t)__umul64hi(low, (unsigned long long)L);
+    }
+    return e < 8u ? (rec.x >> (4u * e)) & 15u : (rec.y >> (4u * (e - 8u))) & 15u;
+}
+
+// The 16-bit (c, p, d) field of rule t of a compiled record.
+__device__ __forceinline__ uint32_t compiled_field(const uint4& rec, uint32_t t) {
+    return ((t < 2u ? rec.z : rec.w) >> (16u * (t & 1u))) & 0xffffu;
+}
+
 // RK: take the Philox round keys from rk (else derive them from seed).
 template <int SEL, bool RK = false>
 __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, uint32_t st, unsigned long long k,
@@ -311,9 +329,7 @@ __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, ui
     if (pend != 0u) {
         o.active = true;
         if ((st & kDMask) == 0u) {
-            const uint32_t t = pend - 1u;
-            const uint32_t f = ((t < 2u ? rec.z : rec.w) >> (16u * (t & 1u))) & 0xffffu;
-            o.emit = (int32_t)((f >> 6) & 31u);
+            o.emit = (int32_t)((compiled_field(rec, pend - 1u) >> 6) & 31u);
             o.st = 0u;
         } else {
             o.st = st - 1u;
@@ -322,13 +338,7 @@ __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, ui
     }
     o.st = 0u;
     o.active = false;
-    const uint32_t K = (rec.y >> 24) & 15u, L = rec.y >> 28;
-    uint32_t e = (uint32_t)n;
-    if (e >= K) {
-        const unsigned long long low = kModMagic.m[L] * (unsigned long long)(e - K);
-        e = K + (uint32_t)__umul64hi(low, (unsigned long long)L);
-    }
-    uint32_t mask = e < 8u ? (rec.x >> (4u * e)) & 15u : (rec.y >> (4u * (e - 8u))) & 15u;
+    uint32_t mask = compiled_mask(rec, n);
     if (mask == 0u) return o;
     if (SEL == SNP_SELECT_PHILOX && (mask & (mask - 1u)) != 0u) {
         const uint32_t cnt = (uint32_t)__popc(mask);
@@ -342,7 +352,7 @@ __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, ui
         mask = idx > 2u ? mask & (mask - 1u) : mask;
     }
     const uint32_t t = (uint32_t)(__ffs(mask) - 1);
-    const uint32_t f = ((t < 2u ? rec.z : rec.w) >> (16u * (t & 1u))) & 0xffffu;
+    const uint32_t f = compiled_field(rec, t);
     const int32_t c = (int32_t)(f & 63u), p = (int32_t)((f >> 6) & 31u), d = (int32_t)(f >> 11);
     o.active = true;
     o.s = (int32_t)t;
@@ -365,12 +375,20 @@ __device__ __forceinline__ int32_t count_applicable(const uint32_t* __restrict__
     return cnt;
 }
 
+// The same for neuron `slot`, through its compiled record when the system
+// has one (always so for rules given as unions of terms).
+template <bool COMPACT>
+__device__ __forceinline__ int32_t count_applicable_slot(const DevSys& s, int32_t slot, int32_t n) {
+    if (s.rec) return __popc(compiled_mask(__ldg(reinterpret_cast<const uint4*>(s.rec) + slot), n));
+    return count_applicable<COMPACT>(s.rules, rule_lo(s, slot), rule_hi(s, slot), n);
+}
+
 // How many rules neuron `slot` may choose at the step about to run: the
 // applicable rules of an idle neuron, 0 while a rule is pending.
 template <bool COMPACT>
 __device__ __forceinline__ int32_t choices_of(const DevSys& s, int32_t slot) {
     if ((s.st[slot] >> kPendShift) != 0u) return 0;
-    return count_applicable<COMPACT>(s.rules, rule_lo(s, slot), rule_hi(s, slot), s.C[slot]);
+    return count_applicable_slot<COMPACT>(s, slot, s.C[slot]);
 }
 
 // The select phase with the choice given: an idle neuron with applicable
@@ -388,6 +406,37 @@ __device__ SelOut select_forced_idx(const DevSys& s, int32_t slot, int32_t n, ui
     o.st = 0u;
     o.active = false;
     const uint32_t pend = st >> kPendShift;
+    if (s.rec) {  // compiled record: mask of applicable rules, fields inline
+        const uint4 rec = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
+        if (pend != 0u) {
+            o.active = true;
+            if ((st & kDMask) == 0u)
+                o.emit = (int32_t)((compiled_field(rec, pend - 1u) >> 6) & 31u);
+            else
+                o.st = st - 1u;
+            return o;
+        }
+        uint32_t mask = compiled_mask(rec, n);
+        const int32_t cnt = __popc(mask);
+        if (cnt == 0) return o;
+        int32_t idx = fidx;
+        if (idx < 0 || idx >= cnt) {
+            bad = true;
+            idx = 0;
+        }
+        for (; idx > 0; --idx) mask &= mask - 1u;  // drop the idx lowest applicable rules
+        const uint32_t t = (uint32_t)(__ffs(mask) - 1);
+        const uint32_t f = compiled_field(rec, t);
+        const int32_t c = (int32_t)(f & 63u), p = (int32_t)((f >> 6) & 31u), d = (int32_t)(f >> 11);
+        o.active = true;
+        o.s = (int32_t)t;
+        o.c_after = n - c;
+        if (d == 0)
+            o.emit = p;
+        else
+            o.st = ((t + 1u) << kPendShift) | (uint32_t)(d - 1);
+        return o;
+    }
     if (pend != 0u) {
         o.active = true;
         if ((st & kDMask) == 0u) {

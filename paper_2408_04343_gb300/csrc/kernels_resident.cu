@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) k_branch_step(DevSys s, const int32_t* __
                 P1[off + nid] = pend ? rule_base[slot] + (int32_t)pend - 1 : -1;
                 if (counts)  // the choices of the new configuration (its next level)
                     counts[off + nid] =
-                        pend ? 0 : count_applicable<COMPACT>(s.rules, rule_lo(s, slot), rule_hi(s, slot), (int32_t)c);
+                        pend ? 0 : count_applicable_slot<COMPACT>(s, slot, (int32_t)c);
             }
         }
         if (threadIdx.x == 0) {

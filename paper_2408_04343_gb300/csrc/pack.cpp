@@ -54,10 +54,24 @@ int validate_desc(const snp_desc* d) {
     }
     const int64_t m = d->rule_offsets[q];
     if (m > INT32_MAX - 1) return fail(SNP_ERR_INVALID, "too many rules");
-    if (m > 0 && (!d->rule_k || !d->rule_j || !d->rule_c || !d->rule_p || !d->rule_d))
+    const bool unions = d->rule_term_offsets != nullptr;
+    if (m > 0 && ((!unions && (!d->rule_k || !d->rule_j)) || !d->rule_c || !d->rule_p || !d->rule_d))
         return fail(SNP_ERR_INVALID, "rule arrays are required when m > 0");
+    if (!unions && (d->term_k || d->term_j))
+        return fail(SNP_ERR_INVALID, "term_k/term_j given without rule_term_offsets");
+    if (unions) {
+        if (d->rule_term_offsets[0] != 0) return fail(SNP_ERR_INVALID, "rule_term_offsets[0] != 0");
+        for (int64_t r = 0; r < m; ++r)
+            if (d->rule_term_offsets[r + 1] <= d->rule_term_offsets[r])
+                return fail(SNP_ERR_INVALID, "rule " + std::to_string(r) + " has no term (rule_term_offsets must increase)");
+        const int64_t T = d->rule_term_offsets[m];
+        if (T > 0 && (!d->term_k || !d->term_j)) return fail(SNP_ERR_INVALID, "term_k and term_j are required");
+        for (int64_t t = 0; t < T; ++t)
+            if (d->term_k[t] < 0 || d->term_j[t] < 0)
+                return fail(SNP_ERR_INVALID, "negative term_k or term_j in term " + std::to_string(t));
+    }
     for (int64_t r = 0; r < m; ++r) {
-        if (d->rule_k[r] < 0 || d->rule_j[r] < 0 || d->rule_c[r] < 0)
+        if ((!unions && (d->rule_k[r] < 0 || d->rule_j[r] < 0)) || d->rule_c[r] < 0)
             return fail(SNP_ERR_INVALID, "negative k, j or c in rule " + std::to_string(r));
         if (d->rule_p[r] < 0 || d->rule_p[r] > kMaxP)
             return fail(SNP_ERR_INVALID, "p out of [0, 65535] in rule " + std::to_string(r));
@@ -143,11 +157,15 @@ int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int 
         hp->rule_base[s] = (int32_t)d->rule_offsets[i];
         max_rules = std::max(max_rules, R);
     }
+    // with union expressions the rule table carries (k, j) = (0, 0): every
+    // kernel then reads the compiled records (compile_rules) instead
+    const bool unions = d->rule_term_offsets != nullptr;
+    auto rk = [&](int64_t r) { return unions ? 0 : d->rule_k[r]; };
+    auto rj = [&](int64_t r) { return unions ? 0 : d->rule_j[r]; };
     for (int64_t r = 0; r < m; ++r) {
         max_p = std::max(max_p, d->rule_p[r]);
         max_d = std::max(max_d, d->rule_d[r]);
-        if (d->rule_k[r] > 255 || d->rule_j[r] > 255 || d->rule_c[r] > 255 || d->rule_p[r] > 15 ||
-            d->rule_d[r] > 15)
+        if (rk(r) > 255 || rj(r) > 255 || d->rule_c[r] > 255 || d->rule_p[r] > 15 || d->rule_d[r] > 15)
             compact = false;
     }
     hp->max_rules = max_rules;
@@ -170,11 +188,10 @@ int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int 
             int64_t r = r0 + t;
             int64_t dst = hp->rule_off[s] + t;
             if (compact) {
-                hp->rules[dst] = pack_rule_compact(d->rule_k[r], d->rule_j[r], d->rule_c[r], d->rule_p[r],
-                                                   d->rule_d[r]);
+                hp->rules[dst] = pack_rule_compact(rk(r), rj(r), d->rule_c[r], d->rule_p[r], d->rule_d[r]);
             } else {
-                hp->rules[dst * 4 + 0] = (uint32_t)d->rule_k[r];
-                hp->rules[dst * 4 + 1] = (uint32_t)d->rule_j[r];
+                hp->rules[dst * 4 + 0] = (uint32_t)rk(r);
+                hp->rules[dst * 4 + 1] = (uint32_t)rj(r);
                 hp->rules[dst * 4 + 2] = (uint32_t)d->rule_c[r];
                 hp->rules[dst * 4 + 3] = (uint32_t)d->rule_p[r] | ((uint32_t)d->rule_d[r] << 16);
             }
@@ -342,6 +359,12 @@ bool compile_rules(const snp_desc* d, HostPack* hp) {
     const int32_t q = hp->q;
     hp->rec.clear();
     if (hp->max_rules > 4) return false;
+    // the terms of rule r: its own (k, j), or its union's terms
+    const bool unions = d->rule_term_offsets != nullptr;
+    auto t_lo = [&](int64_t r) { return unions ? d->rule_term_offsets[r] : r; };
+    auto t_hi = [&](int64_t r) { return unions ? d->rule_term_offsets[r + 1] : r + 1; };
+    auto t_k = [&](int64_t u) { return unions ? d->term_k[u] : d->rule_k[u]; };
+    auto t_j = [&](int64_t u) { return unions ? d->term_j[u] : d->rule_j[u]; };
     std::vector<uint32_t> rec((size_t)q * 4, 0u);
     for (int32_t s = 0; s < q; ++s) {
         const int32_t i = hp->perm[s];
@@ -350,10 +373,15 @@ bool compile_rules(const snp_desc* d, HostPack* hp) {
         for (int64_t t = 0; t < R; ++t) {
             const int64_t r = r0 + t;
             if (d->rule_c[r] >= 64 || d->rule_p[r] >= 32 || d->rule_d[r] >= 32) return false;
-            K = std::max<int64_t>(K, 1 + std::max<int64_t>(d->rule_k[r], d->rule_c[r]));
-            if (d->rule_j[r] > 0) {
-                L = L / gcd64(L, d->rule_j[r]) * d->rule_j[r];
-                if (L > 14) return false;
+            K = std::max<int64_t>(K, 1 + (int64_t)d->rule_c[r]);
+            for (int64_t u = t_lo(r); u < t_hi(r); ++u) {
+                if (t_k(u) >= 14) return false;
+                K = std::max<int64_t>(K, 1 + (int64_t)t_k(u));
+                if (t_j(u) > 0) {
+                    if (t_j(u) > 14) return false;
+                    L = L / gcd64(L, t_j(u)) * t_j(u);
+                    if (L > 14) return false;
+                }
             }
         }
         if (K + L > 14) return false;
@@ -362,9 +390,13 @@ bool compile_rules(const snp_desc* d, HostPack* hp) {
             const int64_t n = e;  // entries K.. stand for n = K + (n - K) mod L; n = e is such an n
             uint32_t mask = 0;
             for (int64_t t = 0; t < R; ++t) {
-                const int64_t r = r0 + t, k = d->rule_k[r], j = d->rule_j[r], c = d->rule_c[r];
-                const bool ok = n >= k && n >= c && (j == 0 ? n == k : (n - k) % j == 0);
-                if (ok) mask |= 1u << t;
+                const int64_t r = r0 + t, c = d->rule_c[r];
+                bool ok = false;
+                for (int64_t u = t_lo(r); u < t_hi(r) && !ok; ++u) {
+                    const int64_t k = t_k(u), j = t_j(u);
+                    ok = n >= k && (j == 0 ? n == k : (n - k) % j == 0);
+                }
+                if (ok && n >= c) mask |= 1u << t;
             }
             table |= (uint64_t)mask << (4 * e);
         }

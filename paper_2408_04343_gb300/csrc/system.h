@@ -56,7 +56,8 @@ struct snp_system {
     int64_t m = 0, nsyn = 0;
     int32_t max_p = 0, max_rules = 0;
     bool compact = true;
-    bool compiled = false;     // compiled rule records uploaded (OPT form)
+    bool compiled = false;     // compiled rule records uploaded (OPT form, or any form with unions)
+    bool unions = false;       // rules given as unions of terms (need the compiled records)
     int32_t* d_forced = nullptr;  // [q] forced choices in slot order (allocated by snp_set_choices)
     bool choices_pending = false; // the next snp_step's first step takes d_forced
     int32_t uniform_rules = 0;

@@ -47,7 +47,8 @@ class snp_desc(ct.Structure):
     _fields_ = [("q", ct.c_int32), ("init_spikes", ct.c_void_p), ("rule_offsets", ct.c_void_p),
                 ("rule_k", ct.c_void_p), ("rule_j", ct.c_void_p), ("rule_c", ct.c_void_p),
                 ("rule_p", ct.c_void_p), ("rule_d", ct.c_void_p), ("num_syn", ct.c_int64),
-                ("syn_offsets", ct.c_void_p), ("syn_targets", ct.c_void_p), ("out_neuron", ct.c_int32)]
+                ("syn_offsets", ct.c_void_p), ("syn_targets", ct.c_void_p), ("out_neuron", ct.c_int32),
+                ("rule_term_offsets", ct.c_void_p), ("term_k", ct.c_void_p), ("term_j", ct.c_void_p)]
 
 
 class snp_info(ct.Structure):
@@ -170,7 +171,8 @@ class _DescHolder:
         self.d = snp_desc(desc.q, _ptr(a["init_spikes"]), _ptr(a["rule_offsets"]), _ptr(a["rule_k"]),
                           _ptr(a["rule_j"]), _ptr(a["rule_c"]), _ptr(a["rule_p"]), _ptr(a["rule_d"]),
                           int(a["syn_offsets"][-1]), _ptr(a["syn_offsets"]), _ptr(a["syn_targets"]),
-                          int(getattr(desc, "out_neuron", 0)))
+                          int(getattr(desc, "out_neuron", 0)), _ptr(a.get("rule_term_offsets")),
+                          _ptr(a.get("term_k")), _ptr(a.get("term_j")))
 
 
 def make_options(form=SNP_FORM_OPT, prop=SNP_PROP_PULL, select=SNP_SELECT_FIRST, engine=SNP_ENGINE_AUTO,

@@ -127,6 +127,29 @@ def test_rejects_malformed_systems():
     assert base.q == 40
 
 
+def test_union_descriptions_are_checked():
+    """Union expressions: malformed term arrays are SNP_ERR_INVALID; unions
+    the compiled applicability table cannot hold are SNP_ERR_UNSUPPORTED
+    (both refused on the host, before any device work)."""
+    import dataclasses
+    base = synth.random_system(40, 9, outdeg=(1, 5), rules=(2, 3))
+    u = synth.with_unions(base, 3)
+    off = u.rule_term_offsets.copy(); off[5] = off[4]                  # rule 4 without a term
+    _bad(dataclasses.replace(u, rule_term_offsets=off, term_k=u.term_k, term_j=u.term_j))
+    tk = u.term_k.copy(); tk[2] = -1                                 # negative term
+    _bad(dataclasses.replace(u, term_k=tk))
+    _bad(dataclasses.replace(u, rule_term_offsets=None))             # terms without offsets
+    for tk_big, tj_big in ((20, 0), (2, 13)):                        # K + L > 14 (K >= 2)
+        tk = u.term_k.copy(); tj = u.term_j.copy(); tk[0] = tk_big; tj[0] = tj_big
+        with pytest.raises(libsnp.SnpError) as ei:
+            libsnp.System(dataclasses.replace(u, term_k=tk, term_j=tj))
+        assert ei.value.status == libsnp.SNP_ERR_UNSUPPORTED
+    five = synth.with_unions(synth.random_system(40, 9, outdeg=(1, 5), rules=(5, 5)), 3)   # 5 rules per neuron
+    with pytest.raises(libsnp.SnpError) as ei:
+        libsnp.System(five)
+    assert ei.value.status == libsnp.SNP_ERR_UNSUPPORTED
+
+
 def test_strerror_names_every_status():
     lib = libsnp.load()
     for st in range(8):
