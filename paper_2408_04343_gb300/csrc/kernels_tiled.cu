@@ -135,24 +135,41 @@ __device__ __forceinline__ void pairs_merge(const uint32_t* __restrict__ Esm, ui
     cur = a1;
 }
 
-// Run-length layout, one 16-byte load: five 24-bit entries src | delta <<
-// sbits.  Each entry first advances the thread's target by delta -- adding
-// the run of the previous target to its accumulator when delta > 0 -- then
-// adds its emission to the run.  `cur` is the shared address of the current
-// target's accumulator.
+// Run-length step: when the advance d is non-zero, add the run to the
+// accumulator at shared address a and start a new run (returns 0), else
+// return the run.  One predicate serves the reduction and the reset.
+__device__ __forceinline__ uint32_t run_flush(uint32_t a, uint32_t run, uint32_t d) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %2, 0;\n\t"
+        "@p red.shared.add.u32 [%1], %3;\n\t"
+        "selp.u32 %0, 0, %3, p;\n\t}"
+        : "=r"(r)
+        : "r"(a), "r"(d), "r"(run));
+    return r;
+}
+
+// Run-length layout, one 16-byte load: five 24-bit entries b << db | d,
+// where b is the source's bit index in the packed emissions (source x EB)
+// and d the target advance.  Each entry first advances the thread's target
+// by d -- adding the run of the previous target to its accumulator when
+// d > 0 -- then adds its emission to the run: word b / 32 of Esm, rotated
+// by b mod 32 (the funnel shift takes its count mod 32).  `cur` is the
+// shared address of the current target's accumulator.
 template <int EB>
-__device__ __forceinline__ void rle_vector(const uint32_t* __restrict__ Esm, const uint4& q, uint32_t wmask,
-                                           int sbits, uint32_t& cur, uint32_t& run) {
+__device__ __forceinline__ void rle_vector(const uint32_t* __restrict__ Esm, const uint4& q, int db,
+                                           uint32_t& cur, uint32_t& run) {
     constexpr uint32_t M = 0xFFFFFFu;
     const uint32_t e[5] = {q.x & M, __funnelshift_r(q.x, q.y, 24) & M, __funnelshift_r(q.y, q.z, 16) & M, q.z >> 8,
                            q.w & M};
+    const uint32_t dmask = (1u << db) - 1u;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const uint32_t v = emission_of<EB>(Esm, e[i], wmask);
-        const uint32_t d = e[i] >> sbits;
-        const bool f = d != 0u;
-        red_add_if(cur, run, f);
-        run = (f ? 0u : run) + v;
+        const uint32_t word = Esm[e[i] >> (db + 5)];
+        const uint32_t v = __funnelshift_r(word, word, e[i] >> db) & ((1u << EB) - 1u);
+        const uint32_t d = e[i] & dmask;
+        run = run_flush(cur, run, d) + v;
         cur += d * 4u;
     }
 }
@@ -227,7 +244,7 @@ __device__ __forceinline__ void gather_batch(const uint4 (&x)[D], int32_t u0, in
     if constexpr (LAYOUT == kLayoutRle) {  // no target windows: the target is carried in cur
 #pragma unroll
         for (int u = 0; u < D; ++u)
-            if (u0 + u < nt) rle_vector<EB>(Esm, x[u], wmask, sbits, cur, run);
+            if (u0 + u < nt) rle_vector<EB>(Esm, x[u], db, cur, run);
         return;
     }
     if (u0 + D <= nt && s0 + u0 + D - 1 < wb[k + 1]) {  // k <= kTiledMaxSub - 1; wb[kTiledMaxSub] = group end
@@ -305,7 +322,8 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
     if (threadIdx.x == 0) mbar_init(ebar);
     for (int j = threadIdx.x; j < tl.acc_words; j += blockDim.x) acc[j] = 0;
     const int sbits = tl.src_bits;
-    const int db = 32 - sbits;
+    // target bits of a 32-bit entry; for run-length entries, the advance's bits
+    const int db = LAYOUT == kLayoutRle ? 24 - sbits - __builtin_ctz((unsigned)EB) : 32 - sbits;
     constexpr uint32_t per = 32u / EB;
     const uint32_t wmask = ((1u << sbits) - 1u) >> __builtin_ctz(per);
     const uint32_t esm = smem_u32(Esm);

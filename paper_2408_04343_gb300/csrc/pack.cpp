@@ -518,10 +518,12 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     tp->src_bits = src_bits;
     tp->cta_lo = cta_lo;
     const int db = 32 - src_bits;
-    // run-length layout when a source fits 20 bits (at least 4 bits left for
-    // the target advance); otherwise the paired layout unless too many
-    // (target, partition) groups have an odd number of words
-    tp->rle = src_bits <= 20 ? 1 : 0;
+    // run-length layout when a source's bit index in the packed emissions
+    // (source x e_bits) fits 21 bits, leaving at least 3 bits for the target
+    // advance; otherwise the paired layout unless too many (target,
+    // partition) groups have an odd number of words
+    const int rle_bits = src_bits + __builtin_ctz((unsigned)eb);  // bits of a bit index 0 .. part_size * eb
+    tp->rle = rle_bits <= 21 ? 1 : 0;
     int64_t odd = 0;
     {
         for (int32_t s = 0; s < q; ++s) {
@@ -538,13 +540,15 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     tp->ent.clear();
     tp->ent.reserve((size_t)hp.nsyn + (size_t)q + (size_t)G * kTiledMaxSub * 4);
     const uint32_t pad = (uint32_t)part_size;  // target 0 of the window, source = the zero word
+    const int rle_db = 24 - rle_bits;          // run-length entries: bit index << rle_db | advance
     std::vector<int64_t> cur(kSlice), end(kSlice);
     // the words of the other layouts, for the run-length layout to beat
     const double other_words = (double)hp.nsyn + (tp->pairs ? (double)odd : 0.0) + 12.0 * G * kTiledMaxSub;
     if (tp->rle) {
         tp->tstart.assign((size_t)G * kTiledThreads, 0);
         const int64_t T = kTiledThreads;
-        const uint32_t max_delta = (1u << (24 - src_bits)) - 1u;
+        const uint32_t max_delta = (1u << rle_db) - 1u;
+        const uint32_t rle_pad = (pad * (uint32_t)eb) << rle_db;  // the zero word, no advance
         std::vector<std::pair<uint32_t, uint32_t>> seq;  // (target local to the range, source local to the partition)
         std::vector<std::vector<uint32_t>> runs(T);
         for (int g = 0; g < NR; ++g) {
@@ -573,13 +577,13 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
                     for (int64_t x = a; x < b; ++x) {
                         uint32_t d = seq[x].first - cur;
                         while (d > max_delta) {  // a long gap: advance with pad entries
-                            run.push_back(pad | (max_delta << src_bits));
+                            run.push_back(rle_pad | max_delta);
                             d -= max_delta;
                         }
-                        run.push_back(seq[x].second | (d << src_bits));
+                        run.push_back(((seq[x].second * (uint32_t)eb) << rle_db) | d);
                         cur = seq[x].first;
                     }
-                    while (run.size() % 5) run.push_back(pad);  // zero delta, zero emission
+                    while (run.size() % 5) run.push_back(rle_pad);  // zero delta, zero emission
                     nvec = std::max(nvec, run.size() / 5);
                 }
                 const size_t base = tp->ent.size() / 4;
@@ -587,7 +591,7 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
                 tp->ent.resize((base + nvec * T) * 4, 0u);
                 for (int64_t t = 0; t < T; ++t) {
                     std::vector<uint32_t>& run = runs[t];
-                    while (run.size() < nvec * 5) run.push_back(pad);  // every thread the same count
+                    while (run.size() < nvec * 5) run.push_back(rle_pad);  // every thread the same count
                     for (size_t u = 0; u < nvec; ++u) {
                         const uint32_t* e = run.data() + u * 5;
                         uint32_t* w = tp->ent.data() + (base + u * T + (size_t)t) * 4;

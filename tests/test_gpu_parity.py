@@ -133,11 +133,19 @@ def test_tiled_cluster_sizes_and_two_launch_form(q, outdeg):
         compare(d, 8, mode, 17, engine="tiled", check_every=False, chunks=(3, 5))
 
 
-def test_tiled_run_length_layout():
+@pytest.mark.parametrize("p_max", [3, 15])
+def test_tiled_run_length_layout(p_max):
     """Long runs of in-edges per CTA thread (600k neurons, out-degree
-    8..24, two source partitions) take the run-length layout: 24-bit
-    entries, the target carried as a running offset."""
-    d = synth.random_system(600000, 66, outdeg=(8, 24), rules=(3, 4), d_range=(0, 5), spikes=(0, 20))
+    8..24) take the run-length layout: 24-bit entries (the source's bit
+    index in the packed emissions, then the target advance), the target
+    carried as a running offset; 2-bit emissions in one source partition,
+    4-bit ones (p up to 15) in two."""
+    d = synth.random_system(600000, 66 if p_max == 3 else 67, outdeg=(8, 24), rules=(3, 4), p_range=(1, p_max),
+                            d_range=(0, 5), spikes=(0, 20))
+    gs = libsnp.System(d, engine=libsnp.SNP_ENGINE_TILED)
+    info = gs.info()
+    gs.close()
+    assert info.e_bits == (2 if p_max == 3 else 4)
     for mode in (oracle.FIRST, oracle.PHILOX):
         compare(d, 12, mode, 29, engine="tiled", check_every=False, chunks=(1, 4, 7))
 
