@@ -455,7 +455,14 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
             delete s;
             return cuda_fail("device query");
         }
-        st = pack_tiled(desc, hp, sms, (size_t)optin - 2048, &im.tp);
+        // the gather sums a partition's in-flow in 32-bit shared accumulators,
+        // read back as int32: a target must not be able to receive more than
+        // INT32_MAX spikes from one partition in one step (the int64 sums of
+        // the other engines carry any in-flow to the overflow check)
+        if ((int64_t)hp.max_in * (int64_t)hp.max_p > (int64_t)INT32_MAX)
+            st = fail(SNP_ERR_UNSUPPORTED, "in-degree x p can exceed the tiled engine's 32-bit accumulators");
+        else
+            st = pack_tiled(desc, hp, sms, (size_t)optin - 2048, &im.tp);
         // Under AUTO the tiled engine must pay for itself: every CTA copies a
         // whole emission partition into shared memory each step.  With one
         // wave of CTAs that copy overlaps the entry stream; with several

@@ -249,6 +249,33 @@ def test_overflow_is_reported():
         assert ei.value.status == libsnp.SNP_ERR_OVERFLOW
 
 
+def test_in_flow_beyond_int32_from_one_partition():
+    """40,000 neurons each send 60,000 spikes to one hub in the same step
+    (2.4e9 > INT32_MAX).  The tiled engine, whose per-partition shared
+    accumulators are 32-bit, refuses the system; AUTO and the other engines
+    report the overflow, as the oracle does."""
+    import oracle as orc
+    n = 40000
+    q = n + 1
+    ones = np.ones(n, np.int32)
+    offs = np.concatenate([[0], np.arange(n + 1)]).astype(np.int64)   # neuron 0: no rule, no synapse
+    d = synth.SystemDesc(q=q, init_spikes=np.concatenate([[0], ones]).astype(np.int32), rule_offsets=offs,
+                         rule_k=ones, rule_j=0 * ones, rule_c=ones, rule_p=60000 * ones, rule_d=0 * ones,
+                         syn_offsets=offs, syn_targets=0 * ones)
+    with pytest.raises(orc.OracleOverflow):
+        orc.run(d, orc.initial_state(d), 2)
+    with pytest.raises(libsnp.SnpError) as ei:
+        libsnp.System(d, engine=libsnp.SNP_ENGINE_TILED)
+    assert ei.value.status == libsnp.SNP_ERR_UNSUPPORTED
+    for eng in (libsnp.SNP_ENGINE_AUTO, libsnp.SNP_ENGINE_LAUNCH):
+        g = libsnp.System(d, engine=eng)
+        assert g.info().engine != libsnp.SNP_ENGINE_TILED
+        with pytest.raises(libsnp.SnpError) as ei:
+            g.step(2)
+        assert ei.value.status == libsnp.SNP_ERR_OVERFLOW
+        g.close()
+
+
 def test_halted_system_reports_zero_steps():
     from tests.test_oracle import make_desc
     d = make_desc(3, [[], [(2, 0, 2, 1, 0)], []], [(1, 0)], [5, 1, 0])
