@@ -289,15 +289,24 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
 }
 
 // ---- compiled rule records (see compile_rules) ---------------------------
-// x mod L for L in 1..14 by multiplication (Lemire, Kaser and Kurz 2019):
-// with M = floor((2^64-1)/L) + 1, x mod L = hi64((M * x mod 2^64) * L).
-struct ModMagic {
-    unsigned long long m[16];
-    constexpr ModMagic() : m() {
-        for (int l = 1; l < 16; ++l) m[l] = ~0ull / (unsigned long long)l + 1ull;
+// x / L for x < 2^31 and L in 2..15 by one high multiply (Granlund and
+// Montgomery, PLDI 1994): with c = ceil(log2 L) and M = ceil(2^(31+c) / L),
+// M < 2^32 and M*L - 2^(31+c) < L <= 2^c, so floor(x / L) = floor(x * M /
+// 2^(31+c)) = umulhi(x, M) >> (c - 1) for every such x.  L = 1 is handled
+// apart (x mod 1 = 0).
+struct ModMagic32 {
+    uint32_t m[16];
+    uint32_t sh[16];
+    constexpr ModMagic32() : m(), sh() {
+        for (int l = 2; l < 16; ++l) {
+            int c = 0;
+            while ((1 << c) < l) ++c;
+            m[l] = (uint32_t)((((unsigned long long)1 << (31 + c)) + (unsigned long long)l - 1ull) / (unsigned long long)l);
+            sh[l] = (uint32_t)(c - 1);
+        }
     }
 };
-__constant__ ModMagic kModMagic = ModMagic();
+__constant__ ModMagic32 kMod32 = ModMagic32();
 
 // Applicable rules of an idle neuron with n spikes from its compiled record:
 // bit t set when rule t applies (n indexes the table directly below K and
@@ -306,8 +315,9 @@ __device__ __forceinline__ uint32_t compiled_mask(const uint4& rec, int32_t n) {
     const uint32_t K = (rec.y >> 24) & 15u, L = rec.y >> 28;
     uint32_t e = (uint32_t)n;
     if (e >= K) {
-        const unsigned long long low = kModMagic.m[L] * (unsigned long long)(e - K);
-        e = K + (uint32_t)__umul64hi(low, (unsigned long long)L);
+        const uint32_t x = e - K;
+        const uint32_t qq = __umulhi(x, kMod32.m[L]) >> kMod32.sh[L];
+        e = K + (L > 1u ? x - qq * L : 0u);
     }
     return e < 8u ? (rec.x >> (4u * e)) & 15u : (rec.y >> (4u * (e - 8u))) & 15u;
 }

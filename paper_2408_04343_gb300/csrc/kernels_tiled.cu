@@ -52,9 +52,17 @@ template <int EB>
 __device__ __forceinline__ void pk_put_slice(uint32_t* e, int32_t slice, int lane, uint32_t v) {
     constexpr int per = 32 / EB;
     uint32_t w = v << ((lane % per) * EB);
+    if constexpr (EB <= 4) {
 #pragma unroll
-    for (int off = 1; off < per; off <<= 1) w |= __shfl_xor_sync(0xffffffffu, w, off);
-    if (lane % per == 0) e[slice * EB + lane / per] = w;
+        for (int g = 0; g < EB; ++g) {
+            const uint32_t part = __reduce_or_sync(0xffffffffu, lane / per == g ? w : 0u);
+            if (lane == g * per) e[slice * EB + g] = part;
+        }
+    } else {
+#pragma unroll
+        for (int off = 1; off < per; off <<= 1) w |= __shfl_xor_sync(0xffffffffu, w, off);
+        if (lane % per == 0) e[slice * EB + lane / per] = w;
+    }
 }
 
 // ---- shared-memory access by 32-bit shared addresses ----------------------
@@ -298,7 +306,7 @@ template <int EB, int LAYOUT>
 __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSys& tl, int32_t t, uint32_t* Esm,
                                                   int* acc, int32_t* wb, unsigned long long* bar,
                                                   unsigned long long& kg_out) {
-    constexpr int D = 4;  // vectors per batch; two batches in registers
+    constexpr int D = 2;  // vectors per batch; two batches in registers
     const int h = blockIdx.x % tl.P;
     const uint32_t ebar = smem_u32(bar);
     // every thread reads its own bounds (one broadcast line), so the first

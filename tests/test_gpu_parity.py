@@ -276,6 +276,35 @@ def test_in_flow_beyond_int32_from_one_partition():
         g.close()
 
 
+@pytest.mark.parametrize("engine", ["launch", "resident", "tiled"])
+def test_compiled_records_at_huge_spike_counts(engine):
+    """Spike counts spread up to 2^31 - 100 with periodic rules (period 2..7
+    per neuron, so every neuron compiles): the compiled table's index
+    K + (n - K) mod L is taken for counts far above any the other tests
+    reach; the chosen rules and the state match the oracle."""
+    rng = np.random.default_rng(44)
+    q = 4096
+    offs, ks, js, cs, ps, ds = [0], [], [], [], [], []
+    for _ in range(q):
+        j = int(rng.integers(2, 8))
+        for _ in range(3):
+            k = int(rng.integers(0, 6))
+            ks.append(k); js.append(j); cs.append(int(rng.integers(0, k + 1)))
+            ps.append(int(rng.integers(1, 4))); ds.append(int(rng.integers(0, 3)))
+        offs.append(len(ks))
+    a32 = lambda x: np.asarray(x, np.int32)
+    init = rng.integers(0, 2**31 - 100, size=q)
+    init[:64] = np.arange(64)                         # and the smallest counts
+    d = synth.SystemDesc(q=q, init_spikes=a32(init), rule_offsets=np.asarray(offs, np.int64), rule_k=a32(ks),
+                         rule_j=a32(js), rule_c=a32(cs), rule_p=a32(ps), rule_d=a32(ds),
+                         syn_offsets=np.zeros(q + 1, np.int64), syn_targets=a32([]))
+    g = libsnp.System(d, engine=ENGINES[engine])
+    assert g.info().compiled_rules == 1
+    g.close()
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        compare(d, 6, mode, 91, engine=engine)
+
+
 def test_halted_system_reports_zero_steps():
     from tests.test_oracle import make_desc
     d = make_desc(3, [[], [(2, 0, 2, 1, 0)], []], [(1, 0)], [5, 1, 0])
