@@ -354,7 +354,10 @@ int64_t snp_paper_format_elements(int32_t form, int64_t q, int64_t m, int64_t z)
  * serialised by the caller.  Work is ordered on `stream`; with steps_done
  * non-NULL the call waits for it and reports the executed step count,
  * SNP_ERR_OVERFLOW, or SNP_ERR_INVALID if the kernels found an index in the
- * device arrays out of range.                                              */
+ * device arrays out of range, a neuron with more than 32,766 rules, or a
+ * rule that a step fires with a field outside snp_desc's ranges (k, j,
+ * c >= 0; p, d in [0, 65535]; d = 0 when p = 0); such a neuron is treated as
+ * idle for the rest of the call.                                           */
 #define SNP_NOALLOC_MAX_Q 262144
 typedef struct snp_device_system {
     int32_t q;

@@ -13,8 +13,11 @@
 // one launch per SNP step fuses the gather of step k with the select of step
 // k+1, on the caller's neuron order and in-neighbour CSR lists, with the
 // state kept as the caller's (C, D, P) arrays.  Every index read from the
-// caller's arrays is bounds-checked; a bad one sets an error flag and the
-// call returns SNP_ERR_INVALID.
+// caller's arrays is bounds-checked, and so are the fields of every rule a
+// step fires (the ranges snp_create enforces on the host: k, j, c >= 0,
+// p and d in [0, 65535], no delay on a forgetting rule) and the number of
+// rules of a neuron; a bad one sets an error flag and the call returns
+// SNP_ERR_INVALID instead of silently packing an out-of-range value.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -76,11 +79,20 @@ __device__ __forceinline__ RuleF na_rule(const NaSys& s, int32_t r) {
     return f;
 }
 
+// The field ranges snp_create's validation enforces on the host; the status
+// word and the emission words below hold p and d in 16 bits.
+__device__ __forceinline__ bool na_rule_ok(const RuleF& f) {
+    return f.k >= 0 && f.j >= 0 && f.c >= 0 && f.p >= 0 && f.p <= kMaxP && f.d >= 0 && f.d <= kMaxDelay &&
+           (f.p != 0 || f.d == 0);
+}
+
 // Select phase of neuron j at step k on the caller's state; same rules as
 // select_neuron in device_common.cuh, over rule fields held as separate arrays.
+// *bad is set when a rule the step fires has a field out of range (the step
+// then treats the neuron as idle).
 template <int SEL>
 __device__ __forceinline__ SelOut na_select(const NaSys& s, int32_t j, int32_t r0, int32_t r1, int32_t n,
-                                            uint32_t st, unsigned long long k) {
+                                            uint32_t st, unsigned long long k, bool* bad) {
     SelOut o;
     o.c_after = n;
     o.emit = 0;
@@ -89,7 +101,13 @@ __device__ __forceinline__ SelOut na_select(const NaSys& s, int32_t j, int32_t r
     if (pend != 0u) {
         o.active = true;
         if ((st & kDMask) == 0u) {
-            o.emit = na_rule(s, r0 + (int32_t)pend - 1).p;
+            const RuleF f = na_rule(s, r0 + (int32_t)pend - 1);
+            if (!na_rule_ok(f)) {
+                *bad = true;
+                o.active = false;
+            } else {
+                o.emit = f.p;
+            }
             o.st = 0u;
         } else {
             o.st = st - 1u;
@@ -124,6 +142,10 @@ __device__ __forceinline__ SelOut na_select(const NaSys& s, int32_t j, int32_t r
     }
     if (pick >= 0) {
         const RuleF f = na_rule(s, pick);
+        if (!na_rule_ok(f)) {
+            *bad = true;
+            return o;
+        }
         o.active = true;
         o.s = pick - r0;
         o.c_after = n - f.c;
@@ -157,7 +179,7 @@ __global__ void __launch_bounds__(256) k_na_step(NaSys s, int32_t t) {
     bool active = false;
     if (j < s.q) {
         int32_t r0 = s.rule_off[j], r1 = s.rule_off[j + 1];
-        bool ok = r0 >= 0 && r0 <= r1 && (long long)r1 <= s.m;
+        bool ok = r0 >= 0 && r0 <= r1 && (long long)r1 <= s.m && r1 - r0 <= kMaxRulesPerNeuron;
         int32_t c = s.C[j];
         const int32_t P = s.P[j], D = s.D[j];
         uint32_t st = 0u;
@@ -199,7 +221,9 @@ __global__ void __launch_bounds__(256) k_na_step(NaSys s, int32_t t) {
             s.S[j] = sel ? r0 + (int32_t)sel - 1 : -1;
         }
         if (SELECT) {
-            const SelOut o = na_select<SEL>(s, j, r0, r1, c, st, ks);
+            bool bad = false;
+            const SelOut o = na_select<SEL>(s, j, r0, r1, c, st, ks, &bad);
+            if (bad) atomicOr(fl + kNaInvalid, 1u);
             c = o.c_after;
             active = o.active;
             na_e(s, ks)[j] = ((uint32_t)o.emit & 0xffffu) | ((uint32_t)(o.s + 1) << 16);
@@ -329,7 +353,7 @@ extern "C" int snp_step_noalloc(const snp_device_system* d, int32_t select, uint
         return fail(SNP_ERR_CUDA, std::string("snp_step_noalloc: ") + cudaGetErrorString(e));
     }
     *steps_done = (int64_t)sw[kNaExec];
-    if (fl[kNaInvalid]) return fail(SNP_ERR_INVALID, "an index in the device arrays was out of range");
+    if (fl[kNaInvalid]) return fail(SNP_ERR_INVALID, "an index or a fired rule's field in the device arrays was out of range");
     if (fl[kNaOverflow]) return fail(SNP_ERR_OVERFLOW, "a spike count left the int32 range");
     return SNP_OK;
 }

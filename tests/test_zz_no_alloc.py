@@ -76,3 +76,39 @@ def test_noalloc_rejects_too_large_systems():
         libsnp.snp_step_noalloc(q, 1, x, x, x, x, x, x, x, x, x, x, x, x, n=1)
     assert ei.value.status == libsnp.SNP_ERR_INVALID
     assert "SNP_NOALLOC_MAX_Q" in str(ei.value)
+
+
+@pytest.mark.parametrize("field,value", [("rule_p", 70000), ("rule_d", 70000), ("rule_c", -1)])
+def test_noalloc_rejects_fired_rules_out_of_range(field, value):
+    # The device arrays bypass snp_create's validation, so the kernels check
+    # the fields of every rule they fire; a step that fires one out of range
+    # must report SNP_ERR_INVALID rather than pack a wrapped value.  A valid
+    # call afterwards still matches snp_step.
+    q, select, seed = 4096, libsnp.SNP_SELECT_FIRST, 7
+    d = synth.random_system(q, 31, outdeg=(2, 8), rules=(3, 3), d_range=(0, 3), spikes=(0, 10))
+    tabs = device_tables(d)
+    bad = dict(tabs)
+    col = tabs[field].clone()
+    firing = torch.from_numpy(d.rule_p > 0).cuda()
+    col[firing] = value
+    bad[field] = col
+
+    def fresh():
+        return (torch.from_numpy(d.init_spikes.astype(np.int32)).cuda(),
+                torch.zeros(q, dtype=torch.int32, device="cuda"),
+                torch.full((q,), -1, dtype=torch.int32, device="cuda"),
+                torch.full((q,), -1, dtype=torch.int32, device="cuda"))
+
+    C, D, P, S = fresh()
+    with pytest.raises(libsnp.SnpError) as ei:
+        libsnp.snp_step_noalloc(q, d.m, C=C, D=D, P=P, S=S, select=select, seed=seed, step=0, n=5, **bad)
+    assert ei.value.status == libsnp.SNP_ERR_INVALID
+
+    C, D, P, S = fresh()
+    ref = libsnp.System(d, select=select, seed=seed, engine=libsnp.SNP_ENGINE_LAUNCH)
+    done = libsnp.snp_step_noalloc(q, d.m, C=C, D=D, P=P, S=S, select=select, seed=seed, step=0, n=9, **tabs)
+    assert done == ref.step(9)
+    rC, rD, rP, _ = ref.get_state()
+    assert (C.cpu().numpy() == rC).all() and (D.cpu().numpy() == rD).all() and (P.cpu().numpy() == rP).all()
+    assert (S.cpu().numpy() == ref.spiking()).all()
+    ref.close()
