@@ -273,7 +273,11 @@ int snp_branch_step(snp_system* sys, int32_t nb, const int32_t* C, const int32_t
 /* A batch runs many independent systems in one persistent launch, each
  * system owned by one CTA for all its steps, systems taken largest first
  * from a device work counter.  mem_budget (bytes) bounds the device memory
- * of the systems a batch keeps admitted at once; 0 = no bound.            */
+ * of the systems the batch uploaded (created with SNP_FLAG_DEFER_UPLOAD)
+ * and that are not yet destroyed; 0 = no bound.  The bound is hard: the
+ * first waiting system is admitted only when it fits beside them.  A
+ * finished system keeps its memory until snp_destroy (its state is still
+ * read), so callers make room by destroying finished systems.             */
 int snp_batch_create(const snp_options* opts, size_t mem_budget, snp_batch** out);
 int snp_batch_destroy(snp_batch* b);
 /* Queues count systems, each to advance steps[i] steps (stopping early at
@@ -284,6 +288,13 @@ int snp_batch_destroy(snp_batch* b);
 int snp_batch_submit(snp_batch* b, snp_system* const* sys, const int64_t* steps, int32_t count,
                      int64_t* ticket);
 int snp_batch_poll(snp_batch* b, int64_t ticket, int* done);
+/* Blocks until the ticket completes (SNP_OK, or the first error of its
+ * systems).  Returns SNP_ERR_BUSY instead of blocking forever when the
+ * ticket waits for memory that only a destroy can free: nothing runs and
+ * the first waiting system does not fit beside the finished ones still
+ * held.  Destroy finished systems, then wait again.  Systems still waiting
+ * when the batch is destroyed are released unrun (their tickets complete
+ * with SNP_ERR_BUSY).                                                      */
 int snp_batch_wait(snp_batch* b, int64_t ticket);
 /* Executed steps of system `index` of a completed ticket.                 */
 int snp_batch_steps_done(snp_batch* b, int64_t ticket, int32_t index, int64_t* steps_done);

@@ -127,6 +127,7 @@ struct snp_batch {
     int64_t rounds = 0, admitted = 0, finished = 0;
     int64_t next_id = 1;
     bool stop = false;
+    bool admitting = false;        // the worker is uploading a system outside the lock
     std::thread worker;
     // device tables of the resident launch, grown on demand
     snp::DevSys* d_sys = nullptr;
@@ -303,17 +304,42 @@ static void finish_item(snp_batch* b, Item* it, int rc, const std::string& err) 
     b->finished += 1;
 }
 
+// b->mu held.  The budget is a hard bound on the device memory of the systems
+// this batch uploaded: the first waiting system is admitted only if it fits
+// beside them.  Finished systems keep their memory until they are destroyed
+// (their state is still read), so once nothing is running, only a destroy
+// can make room.
+static bool front_fits(const snp_batch* b) {
+    if (b->pending.empty()) return false;
+    const snp_system* s = b->pending.front()->sys;
+    const size_t need = s->materialized ? 0 : s->planned_bytes;
+    return !b->budget || b->resident_bytes + need <= b->budget;
+}
+
+// b->mu held.  Waiting systems that nothing but a destroy can admit: no
+// system runs or is being uploaded, and the first waiting one does not fit.
+static bool stalled(const snp_batch* b) {
+    return !b->admitting && b->active.empty() && !b->pending.empty() && !front_fits(b);
+}
+
 static void worker_main(snp_batch* b) {
     std::unique_lock<std::mutex> lk(b->mu);
     for (;;) {
-        b->cv.wait(lk, [&] { return b->stop || !b->pending.empty() || !b->active.empty(); });
+        // a waiting system that does not fit wakes the worker only when a
+        // destroy returns memory (batch_release notifies)
+        b->cv.wait(lk, [&] { return b->stop || front_fits(b) || !b->active.empty(); });
         if (b->stop && b->pending.empty() && b->active.empty()) return;
+        if (b->stop && b->active.empty() && !front_fits(b)) {
+            // destroyed while systems wait for memory: release them unrun
+            for (Item* it : b->pending) finish_item(b, it, SNP_ERR_BUSY, "batch destroyed before admission");
+            b->pending.clear();
+            b->cv.notify_all();
+            return;
+        }
         // admission, first come first served, within the memory budget
-        while (!b->pending.empty()) {
+        while (front_fits(b)) {
             Item* it = b->pending.front();
             snp_system* s = it->sys;
-            const size_t need = s->materialized ? 0 : s->planned_bytes;
-            if (b->budget && b->resident_bytes + need > b->budget && !(b->active.empty())) break;
             b->pending.pop_front();
             int rc = SNP_OK;
             if (!s->stream) {
@@ -328,10 +354,12 @@ static void worker_main(snp_batch* b) {
                 }
             }
             if (!s->materialized) {
+                b->admitting = true;
                 lk.unlock();
                 rc = materialize(s);
                 std::string err = rc ? last_error() : "";
                 lk.lock();
+                b->admitting = false;
                 if (!rc) {
                     b->resident_bytes += s->device_bytes;
                     b->peak_bytes = std::max(b->peak_bytes, b->resident_bytes);
@@ -494,7 +522,10 @@ int snp_batch_wait(snp_batch* b, int64_t ticket) {
     std::unique_lock<std::mutex> lk(b->mu);
     auto it = b->tickets.find(ticket);
     if (it == b->tickets.end()) return fail(SNP_ERR_INVALID, "unknown ticket");
-    b->cv.wait(lk, [&] { return it->second.complete(); });
+    b->cv.wait(lk, [&] { return it->second.complete() || stalled(b); });
+    if (!it->second.complete())
+        return fail(SNP_ERR_BUSY, "ticket " + std::to_string(ticket) +
+                                      " waits for memory that only destroying finished systems can free");
     if (it->second.status) return fail(it->second.status, it->second.error);
     return SNP_OK;
 }

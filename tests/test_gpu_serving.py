@@ -147,6 +147,36 @@ def test_admission_respects_memory_budget():
     b.close()
 
 
+def test_wait_reports_memory_held_by_finished_systems():
+    """The budget is hard: a request that fits only once a finished system
+    is destroyed is not admitted, and waiting on it reports SNP_ERR_BUSY
+    instead of blocking forever; after the destroy it runs and matches the
+    same system stepped alone."""
+    d = synth.random_system(30000, 41, outdeg=(4, 16), rules=(3, 3), d_range=(0, 4), spikes=(0, 20))
+    size = libsnp.System(d, deferred=True)
+    budget = int(size.info().device_bytes * 1.5)   # room for one system, not two
+    size.close()
+    b = libsnp.Batch(mem_budget=budget)
+    ga = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=1, deferred=True)
+    gb = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=2, deferred=True)
+    ta = b.submit([ga], [40])
+    tb = b.submit([gb], [40])
+    b.wait(ta)
+    with pytest.raises(libsnp.SnpError) as ei:
+        b.wait(tb)
+    assert ei.value.status == libsnp.SNP_ERR_BUSY
+    assert not b.poll(tb) and b.info().waiting == 1
+    ga.close()
+    done = b.wait(tb)[0]
+    alone = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=2)
+    assert alone.step(40) == done
+    assert all((x == y).all() for x, y in zip(alone.get_state()[:3], gb.get_state()[:3]))
+    assert b.info().peak_resident_bytes <= budget
+    alone.close()
+    gb.close()
+    b.close()
+
+
 def test_request_larger_than_budget_is_refused():
     d = synth.random_system(50000, 3, outdeg=(4, 16))
     g = libsnp.System(d, deferred=True)
