@@ -329,7 +329,7 @@ def main():
             with open(prof) as f:
                 pj = json.load(f)
             from paper_2408_04343_gb300 import build as B2
-            if pj.get("kernel_sources_hash") == B2.sources_hash():
+            if pj.get("kernel_sources_hash") == B2.engine_sources_hash(args.engine):
                 traffic = pj.get("dram_bytes_per_launch")
         except Exception:
             traffic = None

@@ -73,15 +73,37 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
 
 
-def sources_hash() -> str:
-    """Digest of every kernel and host source of libsnp (ties profiles to code)."""
+# The files one engine's step kernel is built and launched from: its
+# translation unit, the device headers, the packer that lays out its inputs
+# and the host code that launches it.  A DRAM-traffic record taken with ncu
+# stays valid while these files are unchanged.
+ENGINE_SOURCES = {
+    "tiled": ["kernels_tiled.cu", "device_common.cuh", "kernels.h", "snp_internal.h", "system.h", "pack.cpp",
+              "api.cu"],
+    "launch": ["kernels_step.cu", "device_common.cuh", "kernels.h", "snp_internal.h", "system.h", "pack.cpp",
+               "api.cu"],
+}
+
+
+def _digest(paths) -> str:
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))):
+    for p in sorted(paths):
         h.update(os.path.basename(p).encode())
         with open(p, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def sources_hash() -> str:
+    """Digest of every kernel and host source of libsnp."""
+    return _digest(sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")))
+
+
+def engine_sources_hash(engine: str) -> str:
+    """Digest of the files one engine's step kernel depends on (ties an ncu
+    traffic record to the code it was taken on)."""
+    return _digest([os.path.join(CSRC, n) for n in ENGINE_SOURCES[engine]])
 
 
 if __name__ == "__main__":
