@@ -8,7 +8,8 @@
 //  * ELL pull: each target neuron sums Em_k[r] * p over the (rule, p) pairs
 //    of its in-ELL column (the transpose of M^s_Pi's +p rows, Sec. 3);
 //  * ELL push: each emitting rule walks its column of M^s_Pi and adds p into
-//    every open target with warp-aggregated atomics (Alg. 4's direction);
+//    every open target with warp-aggregated atomics (Alg. 4's direction),
+//    the columns dealt to warps in equal runs (push_balanced.cuh);
 //  * dense: each neuron walks its column of M_Pi over all m rules and adds
 //    Em_k[r] * M[r, j] (Alg. 3's direction); the (row block x neuron tile)
 //    partial sums meet in an in-flow vector, and the select launch applies it.
@@ -18,6 +19,7 @@
 
 #include "device_common.cuh"
 #include "kernels.h"
+#include "push_balanced.cuh"
 
 namespace snp {
 
@@ -118,31 +120,34 @@ __global__ void __launch_bounds__(256) k_ell_select(DevSys s, EllSys e, int32_t 
     if (SELECT) raise_step_activity(fl, ks, active);
 }
 
-// ELL push of step kg = base + t: a warp per 32 consecutive rules.
-__global__ void __launch_bounds__(256) k_ell_push(DevSys s, EllSys e, int32_t t) {
+// ELL push of step kg = base + t: per-rule columns of (target, p) pairs in
+// slices of 32 consecutive rules; each warp takes an equal run of their
+// columns (push_balanced.cuh).
+struct PushEllSrc {
+    using Ent = int2;
+    const uint8_t* Em;
+    int64_t m;
+    __device__ __forceinline__ Ent pad() const { return make_int2(-1, 0); }
+    __device__ __forceinline__ int32_t value(int32_t slice, int lane) const {
+        const int64_t r = (int64_t)slice * kSlice + lane;
+        return r < m && Em[r] ? 1 : 0;
+    }
+    __device__ __forceinline__ int32_t target(Ent e) const { return e.x; }
+    __device__ __forceinline__ int32_t amount(Ent e, int32_t) const { return e.y; }
+};
+
+constexpr int kEllPushBlocksPerSm = 6;
+
+__global__ void __launch_bounds__(256, kEllPushBlocksPerSm) k_ell_push(DevSys s, EllSys e, int32_t t) {
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
     if (step_blocked(fl, s.step, kg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 1ull) % 3ull)] = 0u;
-    const int lane = threadIdx.x & 31;
-    const int64_t rs = (int64_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int64_t nrs = (e.m + kSlice - 1) / kSlice;
-    if (rs >= nrs) return;  // warp-uniform
-    const int64_t r = rs * kSlice + lane;
-    const bool on = r < e.m && SNP_PICK(e.Em, kg)[r];
-    const int32_t b = __ldg(e.out_ptr + rs);
-    const int32_t w = __ldg(e.out_ptr + rs + 1) - b;
-    const int2* __restrict__ p = e.out_ent + (size_t)b * kSlice + lane;
-    for (int32_t col = 0; col < w; ++col) {
-        int2 a = on ? __ldg(p + col * kSlice) : make_int2(-1, 0);
-        if (a.x >= 0 && (s.st[a.x] >> kPendShift) != 0u) a.x = -1;  // closed target: lost
-        const unsigned grp = __match_any_sync(0xffffffffu, a.x);
-        const unsigned add = __reduce_add_sync(grp, a.x >= 0 ? (unsigned)a.y : 0u);
-        if (a.x >= 0 && (__ffs(grp) - 1) == lane) {
-            const int old = atomicAdd(s.C + a.x, (int)add);
-            if ((long long)old + (long long)add > 2147483647ll) atomicOr(fl + kFlagOverflow, 1u);
-        }
-    }
+    PushEllSrc src;
+    src.Em = SNP_PICK(e.Em, kg);
+    src.m = e.m;
+    const int32_t nrs = (int32_t)((e.m + kSlice - 1) / kSlice);
+    push_scatter_balanced<8>(src, e.out_ptr, nrs, e.out_ent, s.C, s.st, fl + kFlagOverflow);
 }
 
 // Dense accumulation of step kg = base + t: CTA (bx, by) covers neurons
@@ -218,7 +223,7 @@ cudaError_t launch_ell_push(const DevSys& s, const EllSys& e, int32_t t, cudaStr
         k_ell_push<<<1, 32, 0, st>>>(s, e, t);  // still settles the halt test
         return cudaGetLastError();
     }
-    k_ell_push<<<(unsigned)((nrs + 7) / 8), 256, 0, st>>>(s, e, t);
+    k_ell_push<<<push_blocks(kEllPushBlocksPerSm, nrs), 256, 0, st>>>(s, e, t);
     return cudaGetLastError();
 }
 

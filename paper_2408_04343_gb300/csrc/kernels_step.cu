@@ -13,7 +13,8 @@
 //
 // Push form (SNP_PROP_PUSH) follows Alg. 5's direction: a select launch, then
 // every emitter adds p into each open target with atomics aggregated across
-// the warp (lanes that hit the same target add once).
+// the warp (lanes that hit the same target add once), the out-list's columns
+// dealt to warps in equal runs so hub sources do not serialise a warp.
 //
 // Fixed point: a select pass raises a per-step activity word when any neuron
 // is pending or selected.  A gather launch that finds its step's word clear
@@ -22,6 +23,7 @@
 
 #include "device_common.cuh"
 #include "kernels.h"
+#include "push_balanced.cuh"
 
 namespace snp {
 
@@ -84,30 +86,33 @@ __global__ void __launch_bounds__(256) k_step_pull(DevSys s, int32_t t) {
     if (SELECT) raise_step_activity(fl, ks, active);
 }
 
-// Push propagation of step kg = base + t: select already ran for kg.
-__global__ void __launch_bounds__(256) k_push_scatter(DevSys s, int32_t t) {
+// Push propagation of step kg = base + t: select already ran for kg.  The
+// optimized form's out-lists (Sy_Pi as sliced ELL by source, pad -1); each
+// warp takes an equal run of their columns (push_balanced.cuh).
+struct PushOptSrc {
+    using Ent = int32_t;
+    const int32_t* E;
+    int32_t q;
+    __device__ __forceinline__ Ent pad() const { return -1; }
+    __device__ __forceinline__ int32_t value(int32_t slice, int lane) const {
+        const int32_t slot = slice * kSlice + lane;
+        return slot < q ? E[slot] : 0;
+    }
+    __device__ __forceinline__ int32_t target(Ent e) const { return e; }
+    __device__ __forceinline__ int32_t amount(Ent, int32_t v) const { return v; }
+};
+
+constexpr int kPushBlocksPerSm = 8;
+
+__global__ void __launch_bounds__(256, kPushBlocksPerSm) k_push_scatter(DevSys s, int32_t t) {
     uint32_t* fl = s.flags;
     const unsigned long long kg = s.step[kStepBase] + (unsigned long long)t;
     if (step_blocked(fl, s.step, kg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) fl[kFlagAct0 + (int)((kg + 1ull) % 3ull)] = 0u;
-    const int lane = threadIdx.x & 31;
-    const int32_t slice = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (slice >= s.nslices) return;  // warp-uniform
-    const int32_t slot = slice * kSlice + lane;
-    const int32_t emit = slot < s.q ? SNP_PICK(s.E, kg)[slot] : 0;
-    const int32_t b = __ldg(s.out_ptr + slice);
-    const int32_t w = __ldg(s.out_ptr + slice + 1) - b;
-    const int32_t* __restrict__ p = s.out_idx + (size_t)b * kSlice + lane;
-    for (int32_t col = 0; col < w; ++col) {
-        int32_t tg = emit > 0 ? __ldg(p + col * kSlice) : -1;
-        if (tg >= 0 && (s.st[tg] >> kPendShift) != 0u) tg = -1;  // closed target: spikes lost
-        const unsigned grp = __match_any_sync(0xffffffffu, tg);
-        const unsigned add = __reduce_add_sync(grp, tg >= 0 ? (unsigned)emit : 0u);
-        if (tg >= 0 && (__ffs(grp) - 1) == lane) {
-            const int old = atomicAdd(s.C + tg, (int)add);
-            if ((long long)old + (long long)add > 2147483647ll) atomicOr(fl + kFlagOverflow, 1u);
-        }
-    }
+    PushOptSrc src;
+    src.E = SNP_PICK(s.E, kg);
+    src.q = s.q;
+    push_scatter_balanced<8>(src, s.out_ptr, s.nslices, s.out_idx, s.C, s.st, fl + kFlagOverflow);
 }
 
 // Select-only launch for the push form: step kg = base + t.
@@ -210,7 +215,7 @@ cudaError_t launch_push_step(const DevSys& s, int32_t t, cudaStream_t st, bool c
         else
             k_select_push<false, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, t);
     }
-    k_push_scatter<<<grid, 256, 0, st>>>(s, t);
+    k_push_scatter<<<push_blocks(kPushBlocksPerSm, s.nslices), 256, 0, st>>>(s, t);
     return cudaGetLastError();
 }
 
