@@ -224,8 +224,12 @@ int snp_get_status(const snp_system* sys, int32_t* out, int64_t len);
 /* Pending delayed rule per neuron (global rule id) or -1.                 */
 int snp_get_pending(const snp_system* sys, int32_t* out, int64_t len);
 /* Checkpoint: (C, D, P) as above plus the absolute step counter k.  Any
- * of C, D, P may be NULL.  set_state validates ranges (pending rule must
- * belong to its neuron; D > 0 only with a pending rule).                  */
+ * of C, D, P may be NULL for get_state.  set_state takes all three, in host
+ * (pageable or pinned) or device memory, and validates them on the device
+ * (C >= 0; 0 <= D <= 65535; a pending rule must belong to its neuron; D > 0
+ * only with a pending rule): SNP_ERR_INVALID names the smallest offending
+ * neuron and leaves C, D, P and k unchanged.  Either way the spiking vector
+ * then reads all -1.                                                       */
 int snp_get_state(const snp_system* sys, int32_t* C, int32_t* D, int32_t* P, int64_t len,
                   uint64_t* step);
 int snp_set_state(snp_system* sys, const int32_t* C, const int32_t* D, const int32_t* P,

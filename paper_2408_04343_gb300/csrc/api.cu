@@ -726,55 +726,59 @@ int snp_get_state(const snp_system* s, int32_t* C, int32_t* D, int32_t* P, int64
     return SNP_OK;
 }
 
-static int fetch_host(const int32_t* src, int64_t q, std::vector<int32_t>& dst, snp_system* s) {
-    dst.resize((size_t)q);
-    if (is_device_ptr(src)) {
-        if (cudaMemcpyAsync(dst.data(), src, sizeof(int32_t) * (size_t)q, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
-            cudaStreamSynchronize(s->stream) != cudaSuccess)
-            return cuda_fail("state fetch");
-    } else {
-        std::memcpy(dst.data(), src, sizeof(int32_t) * (size_t)q);
-    }
-    return SNP_OK;
+// The message for the first invalid neuron the import check found; its
+// three values are read back from the caller's arrays (host or device).
+static int import_error(const snp_system* s, int32_t i, const int32_t* C, const int32_t* D, const int32_t* P) {
+    int32_t c = 0, d = 0, p = 0;
+    if (cudaMemcpy(&c, C + i, 4, cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(&d, D + i, 4, cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(&p, P + i, 4, cudaMemcpyDefault) != cudaSuccess)
+        return cuda_fail("state read-back");
+    const std::string at = " at neuron " + std::to_string(i);
+    if (c < 0) return fail(SNP_ERR_INVALID, "negative spike count" + at);
+    if (d < 0 || d > kMaxDelay) return fail(SNP_ERR_INVALID, "D out of range" + at);
+    if (p == -1) return fail(SNP_ERR_INVALID, "D > 0 without a pending rule" + at);
+    return fail(SNP_ERR_INVALID, "pending rule does not belong to neuron " + std::to_string(i));
 }
 
+// Imports (C, D, P) on the device: the three arrays are copied (from host or
+// device memory) into buffers whose contents set_state discards anyway (the
+// spiking vectors and the export scratch), checked by one launch, and only
+// if every neuron passes written in slot order by a second.
 int snp_set_state(snp_system* s, const int32_t* C, const int32_t* D, const int32_t* P, int64_t len, uint64_t step) {
     if (!s || !C || !D || !P) return fail(SNP_ERR_INVALID, "NULL argument");
     if (s->busy.load()) return fail(SNP_ERR_BUSY, "system is owned by an unfinished batch");
     if (int rc_ = materialize(s)) return rc_;
     if (len < s->q) return fail(SNP_ERR_INVALID, "state shorter than q");
-    std::vector<int32_t> hc, hd, hpv;
-    int rc;
-    if ((rc = fetch_host(C, s->q, hc, s)) || (rc = fetch_host(D, s->q, hd, s)) || (rc = fetch_host(P, s->q, hpv, s)))
-        return rc;
-    std::vector<int32_t> c_slot((size_t)s->q);
-    std::vector<uint32_t> st_slot((size_t)s->q);
-    for (int32_t slot = 0; slot < s->q; ++slot) {
-        const int32_t i = s->perm[slot];
-        if (hc[i] < 0) return fail(SNP_ERR_INVALID, "negative spike count at neuron " + std::to_string(i));
-        if (hd[i] < 0 || hd[i] > kMaxDelay) return fail(SNP_ERR_INVALID, "D out of range at neuron " + std::to_string(i));
-        uint32_t w = 0;
-        if (hpv[i] == -1) {
-            if (hd[i] != 0) return fail(SNP_ERR_INVALID, "D > 0 without a pending rule at neuron " + std::to_string(i));
-        } else {
-            const int64_t r0 = s->rule_offsets[i], r1 = s->rule_offsets[i + 1];
-            if (hpv[i] < r0 || hpv[i] >= r1)
-                return fail(SNP_ERR_INVALID, "pending rule does not belong to neuron " + std::to_string(i));
-            w = ((uint32_t)(hpv[i] - r0 + 1) << kPendShift) | (uint32_t)hd[i];
-        }
-        c_slot[slot] = hc[i];
-        st_slot[slot] = w;
+    cudaStream_t st = s->stream;
+    const size_t bytes = sizeof(int32_t) * (size_t)s->q;
+    int32_t* sc = s->scratch;
+    int32_t* sd = s->dev.S[0];
+    int32_t* sp = s->dev.S[1];
+    uint32_t bad = 0xffffffffu;
+    if (cudaMemcpyAsync(sc, C, bytes, cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaMemcpyAsync(sd, D, bytes, cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaMemcpyAsync(sp, P, bytes, cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaMemsetAsync(s->dev.flags + kFlagImport, 0xff, sizeof(uint32_t), st) != cudaSuccess ||
+        launch_import(s->dev, s->d_rule_base, sc, sd, sp, false, st) != cudaSuccess ||
+        cudaMemcpyAsync(&bad, s->dev.flags + kFlagImport, sizeof(bad), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_fail("state upload");
+    if (bad == 0xffffffffu && launch_import(s->dev, s->d_rule_base, sc, sd, sp, true, st) != cudaSuccess)
+        return cuda_fail("state import");
+    // the spiking vectors held the staged D and P: all -1 again either way
+    if (cudaMemsetAsync(s->dev.S[0], 0xff, bytes, st) != cudaSuccess ||
+        cudaMemsetAsync(s->dev.S[1], 0xff, bytes, st) != cudaSuccess)
+        return cuda_fail("state upload");
+    if (bad != 0xffffffffu) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail("state upload");
+        return import_error(s, (int32_t)bad, C, D, P);
     }
-    std::vector<int32_t> sm((size_t)s->q, -1);
     unsigned long long steps[kNumStepWords] = {step, step, 0ull, 0ull};
     uint32_t fz[kNumFlags] = {0};
-    if (cudaMemcpyAsync(s->dev.C, c_slot.data(), sizeof(int32_t) * c_slot.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-        cudaMemcpyAsync(s->dev.st, st_slot.data(), sizeof(uint32_t) * st_slot.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-        cudaMemcpyAsync(s->dev.S[0], sm.data(), sizeof(int32_t) * sm.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-        cudaMemcpyAsync(s->dev.S[1], sm.data(), sizeof(int32_t) * sm.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-        cudaMemcpyAsync(s->dev.step, steps, sizeof(steps), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-        cudaMemcpyAsync(s->dev.flags, fz, sizeof(fz), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-        cudaStreamSynchronize(s->stream) != cudaSuccess)
+    if (cudaMemcpyAsync(s->dev.step, steps, sizeof(steps), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(s->dev.flags, fz, sizeof(fz), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
         return cuda_fail("state upload");
     return SNP_OK;
 }

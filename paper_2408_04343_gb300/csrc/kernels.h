@@ -19,6 +19,12 @@ cudaError_t launch_advance(const DevSys& s, int32_t count, cudaStream_t st);
 cudaError_t launch_finish(const DevSys& s, int32_t tail, cudaStream_t st);
 cudaError_t launch_export(const DevSys& s, const int32_t* rule_base, int what, int32_t* out, int parity,
                           cudaStream_t st, bool compact = true);
+// State import (snp_set_state): C, D, P in the caller's neuron order, already
+// on the device.  check: records the smallest neuron id whose values are out
+// of range in flags[kFlagImport] (which the caller sets to 0xffffffff first);
+// commit: writes C and the status words in slot order.
+cudaError_t launch_import(const DevSys& s, const int32_t* rule_base, const int32_t* C, const int32_t* D,
+                          const int32_t* P, bool commit, cudaStream_t st);
 
 // CTA-resident engine (kernels_resident.cu): each CTA takes whole systems
 // from `work` (largest first as listed) and runs all their steps.

@@ -258,6 +258,41 @@ __global__ void k_export(const DevSys s, const int32_t* __restrict__ rule_base, 
     out[nid] = v;
 }
 
+// State import: the caller's C, D, P (neuron order, on the device) checked
+// neuron by neuron with the ranges snp_set_state documents, then written in
+// slot order (spikes, and the status word: 1 + local pending rule above D).
+template <bool COMMIT>
+__global__ void k_import(DevSys s, const int32_t* __restrict__ rule_base, const int32_t* __restrict__ C,
+                         const int32_t* __restrict__ D, const int32_t* __restrict__ P) {
+    const int32_t slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= s.q) return;
+    const uint32_t i = neuron_id(s, slot);
+    const int32_t c = C[i], d = D[i], p = P[i];
+    const int32_t r0 = rule_base[slot];
+    if (!COMMIT) {
+        bool ok = c >= 0 && d >= 0 && d <= kMaxDelay;
+        if (p == -1)
+            ok = ok && d == 0;
+        else
+            ok = ok && p >= r0 && p - r0 < rule_hi(s, slot) - rule_lo(s, slot);
+        if (!ok) atomicMin(s.flags + kFlagImport, i);
+        return;
+    }
+    s.C[slot] = c;
+    s.st[slot] = p == -1 ? 0u : ((uint32_t)(p - r0 + 1) << kPendShift) | (uint32_t)d;
+}
+
+cudaError_t launch_import(const DevSys& s, const int32_t* rule_base, const int32_t* C, const int32_t* D,
+                          const int32_t* P, bool commit, cudaStream_t st) {
+    if (s.q == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((s.q + 255) / 256);
+    if (commit)
+        k_import<true><<<grid, 256, 0, st>>>(s, rule_base, C, D, P);
+    else
+        k_import<false><<<grid, 256, 0, st>>>(s, rule_base, C, D, P);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_export(const DevSys& s, const int32_t* rule_base, int what, int32_t* out, int parity,
                           cudaStream_t st, bool compact) {
     if (s.q == 0) return cudaSuccess;

@@ -33,6 +33,7 @@ enum Flag : int {
     kFlagOverflow = 4, // a spike count left the int32 range (sticky until reported)
     kFlagTimeout = 5,  // a bounded wait gave up
     kFlagChoice = 6,   // a forced choice index was out of range (snp_set_choices)
+    kFlagImport = 7,   // smallest neuron whose imported state is invalid (snp_set_state)
     kNumFlags = 8
 };
 // Device step counters of one system (uint64).

@@ -226,6 +226,83 @@ def test_checkpoint_resume_is_bit_exact():
     assert ref[3] == got[3] == 60
 
 
+@pytest.mark.parametrize("where", ["numpy", "pinned", "device"])
+@pytest.mark.parametrize("kw", [dict(engine=libsnp.SNP_ENGINE_LAUNCH), dict(engine=libsnp.SNP_ENGINE_TILED),
+                                dict(engine=libsnp.SNP_ENGINE_RESIDENT), dict(prop=libsnp.SNP_PROP_PUSH),
+                                dict(form=libsnp.SNP_FORM_ELL)], ids=["launch", "tiled", "resident", "push", "ell"])
+def test_set_state_from_host_and_device_memory(kw, where):
+    """snp_set_state checks and permutes the state on the device: resuming
+    from a checkpoint held in pageable, pinned or device memory continues
+    bit for bit on every engine and form."""
+    d = synth.random_system(6000, 13, outdeg=(4, 16), rules=(3, 4), d_range=(0, 5), spikes=(0, 20))
+    a = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=5)
+    a.step(40)
+    ref = a.get_state()
+    ref_S = a.spiking()
+    b = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=5)
+    b.step(17)
+    C, D, P, k = b.get_state()
+    if where == "pinned":
+        C, D, P = (torch.from_numpy(x).pin_memory() for x in (C, D, P))
+    elif where == "device":
+        C, D, P = (torch.from_numpy(x).cuda() for x in (C, D, P))
+    c = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=5, **kw)
+    c.step(3)
+    c.set_state(C, D, P, k)
+    assert (c.spiking() == -1).all()
+    got0 = c.get_state()
+    assert all((np.asarray(x.cpu() if hasattr(x, "cpu") else x) == y).all() for x, y in zip((C, D, P), got0[:3]))
+    assert got0[3] == 17
+    assert c.step(23) == 23
+    got = c.get_state()
+    for x, y in zip(ref[:3], got[:3]):
+        assert (x == y).all()
+    assert ref[3] == got[3] == 40
+    assert (c.spiking() == ref_S).all()
+    for g in (a, b, c):
+        g.close()
+
+
+def test_set_state_rejects_bad_values_and_keeps_the_state():
+    d = synth.random_system(3000, 14, outdeg=(4, 16), rules=(3, 3), d_range=(1, 5), spikes=(0, 20))
+    g = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=9)
+    g.step(11)
+    C, D, P, k = g.get_state()
+    pend = np.flatnonzero(P >= 0)
+    idle = np.flatnonzero(P == -1)
+    assert len(pend) and len(idle)
+    i, j = int(pend[len(pend) // 2]), int(idle[len(idle) // 2])
+    r_other = int(d.rule_offsets[j])   # a rule of another neuron
+    bad_cases = [("C", j, -1, "negative spike count at neuron %d" % j),
+                 ("D", i, 70000, "D out of range at neuron %d" % i),
+                 ("D", j, 2, "D > 0 without a pending rule at neuron %d" % j),
+                 ("P", i, r_other, "pending rule does not belong to neuron %d" % i)]
+    for name, at, val, msg in bad_cases:
+        arrs = {"C": C.copy(), "D": D.copy(), "P": P.copy()}
+        arrs[name][at] = val
+        with pytest.raises(libsnp.SnpError) as ei:
+            g.set_state(arrs["C"], arrs["D"], arrs["P"], 99)
+        assert ei.value.status == libsnp.SNP_ERR_INVALID
+        assert msg in str(ei.value)
+        C2, D2, P2, k2 = g.get_state()
+        assert (C2 == C).all() and (D2 == D).all() and (P2 == P).all() and k2 == k
+    # two bad neurons: the smaller id is reported
+    lo, hi = sorted((i, j))
+    arrs = {"C": C.copy(), "D": D.copy(), "P": P.copy()}
+    arrs["C"][lo] = -3
+    arrs["C"][hi] = -4
+    with pytest.raises(libsnp.SnpError) as ei:
+        g.set_state(arrs["C"], arrs["D"], arrs["P"], 99)
+    assert "at neuron %d" % lo in str(ei.value)
+    # still steps exactly like an untouched copy
+    h = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=9)
+    h.step(11)
+    assert g.step(9) == h.step(9)
+    assert all((x == y).all() for x, y in zip(g.get_state()[:3], h.get_state()[:3]))
+    g.close()
+    h.close()
+
+
 def test_device_outputs_and_stream():
     d = synth.random_system(3000, 8, outdeg=(4, 16), rules=(3, 4), d_range=(0, 5), spikes=(0, 20))
     s = torch.cuda.Stream()
