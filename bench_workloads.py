@@ -22,6 +22,10 @@ families -- Sec. 6's families: the sort system on worst-case inputs
           20,000: per n the device memory of each form against the paper's
           element-count formulas, and the time of a run (sort: to its fixed
           point, checked sorted; subset-sum-shaped: 200 Philox steps).
+engines -- the 1,048,576-neuron workload of the headline bench on every
+          engine and form (tiled, L2 gather, push, ELL pull, ELL push): one
+          system each, 8 untimed steps, then one timed snp_step(192) call;
+          the final configurations must agree.
 tree   -- computation-tree exploration of the subset-sum-shaped stand-in
           (n = 14: 2^14 branches when the choice neurons fire): branches per
           second explored breadth first with the batched branch step (one
@@ -45,7 +49,8 @@ def run(args, ws, rank, local):
     if rank == 0:
         B.build()
     torch.cuda.set_device(local)
-    fn = {"batch": batch, "serve": serve, "skewed": skewed, "families": families, "tree": tree_workload}[args.workload]
+    fn = {"batch": batch, "serve": serve, "skewed": skewed, "families": families, "tree": tree_workload,
+          "engines": engines}[args.workload]
     line = fn(args, libsnp, synth)
     line.update({"n_gpus": ws, "data": "synthetic", "dtype": "int32", "higher_is_better": True})
     if rank == 0:
@@ -208,6 +213,32 @@ def skewed(args, libsnp, synth):
     return {"metric": "synaptic updates/s", "workload": "skewed", "value": res["auto"].get("syn_updates_per_s"),
             "unit": "synaptic updates/s", "engines": res,
             "config": {"q": d.q, "num_syn": d.num_syn, "steps": nsteps, "dense_copy_q": dd.q, "dense_copy_m": dd.m}}
+
+
+def engines(args, libsnp, synth):
+    import hashlib
+    import torch
+    d, _, _ = synth.large_1m()
+    res, digests = {}, set()
+    for name, kw in [("tiled", dict(engine=libsnp.SNP_ENGINE_TILED)),
+                     ("l2_gather", dict(engine=libsnp.SNP_ENGINE_LAUNCH)),
+                     ("push", dict(prop=libsnp.SNP_PROP_PUSH)),
+                     ("ell_pull", dict(form=libsnp.SNP_FORM_ELL)),
+                     ("ell_push", dict(form=libsnp.SNP_FORM_ELL, prop=libsnp.SNP_PROP_PUSH))]:
+        g = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=d.seed, **kw)
+        g.step(8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = g.step(192)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        digests.add(hashlib.sha256(g.config().tobytes()).hexdigest())
+        res[name] = {"us_per_step": dt / max(done, 1) * 1e6, "syn_updates_per_s": d.num_syn * done / dt,
+                     "device_mb": g.info().device_bytes / 1e6}
+        g.close()
+    return {"metric": "synaptic updates/s", "workload": "engines", "value": res["tiled"]["syn_updates_per_s"],
+            "unit": "synaptic updates/s", "engines": res, "same_final_configuration": len(digests) == 1,
+            "config": {"q": d.q, "num_syn": d.num_syn, "timed_steps": 192}}
 
 
 def families(args, libsnp, synth):

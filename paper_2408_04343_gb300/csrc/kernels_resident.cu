@@ -21,6 +21,18 @@
 
 namespace snp {
 
+// Occupancy of the resident kernel.  The kernel is bound by the latency of
+// its global loads (a warp per slice, one dependent chain per slice), so
+// resident warps matter most: at most 512 threads per CTA and 3 CTAs per SM
+// hold it to 40 registers (48 warps per SM, which is also what a 65,536-
+// neuron system's packed emissions leave room for in shared memory), where
+// the unbounded form used 64 registers and fit 32 warps.  Measured on the
+// 8,192-system batch: 3.67e11 -> 4.22e11 synaptic updates/s, 4.44e11 with
+// 2-bit emissions; 2 CTAs of 1,024 threads at 32 registers tie with it but
+// spill more.
+constexpr int kResMaxThreads = 512;
+constexpr int kResMinBlocks = 3;
+
 template <int EB>
 __device__ __forceinline__ int32_t e_get(const uint32_t* __restrict__ e, int32_t i) {
     if (EB == 32) return (int32_t)e[i];
@@ -138,7 +150,7 @@ __device__ void run_resident(const DevSys& s, long long n, uint32_t* esm) {
 }
 
 template <bool COMPACT, int SEL, int EB>
-__global__ void __launch_bounds__(1024) k_resident(const DevSys* __restrict__ systems,
+__global__ void __launch_bounds__(kResMaxThreads, kResMinBlocks) k_resident(const DevSys* __restrict__ systems,
                                                    const long long* __restrict__ nsteps, int nsys,
                                                    unsigned int* work) {
     extern __shared__ uint32_t esm[];
@@ -288,10 +300,12 @@ cudaError_t launch_branch_step(const DevSys& s, const int32_t* rule_base, int e_
 #define SNP_BR(CC, EE) \
     return launch_branch_t<CC, EE>(s, rule_base, nb, C0, D0, P0, ch, C1, D1, P1, ex, bad, counts, st)
     if (compact) {
+        if (e_bits == 2) SNP_BR(true, 2);
         if (e_bits == 4) SNP_BR(true, 4);
         if (e_bits == 8) SNP_BR(true, 8);
         SNP_BR(true, 16);
     }
+    if (e_bits == 2) SNP_BR(false, 2);
     if (e_bits == 4) SNP_BR(false, 4);
     if (e_bits == 8) SNP_BR(false, 8);
     SNP_BR(false, 16);
@@ -299,6 +313,7 @@ cudaError_t launch_branch_step(const DevSys& s, const int32_t* rule_base, int e_
 }
 
 int resident_e_bits(int max_p) {
+    if (max_p < 4) return 2;
     if (max_p < 16) return 4;
     if (max_p < 256) return 8;
     return 16;
@@ -323,7 +338,21 @@ static cudaError_t launch_res_t(const DevSys* d_systems, const long long* d_nste
     auto fn = k_resident<C, S, EB>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
     if (e != cudaSuccess) return e;
-    fn<<<plan.ctas, plan.threads, plan.smem, st>>>(d_systems, d_nsteps, nsys, d_work);
+    const int threads = plan.threads < kResMaxThreads ? plan.threads : kResMaxThreads;
+    int ctas = plan.ctas;
+    if (ctas > 1) {
+        // persistent grid: exactly the CTAs that are resident at once
+        // (registers, shared memory and threads all counted)
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, plan.smem) == cudaSuccess &&
+            sms > 0 && per_sm > 0)
+            ctas = sms * per_sm;
+        else
+            cudaGetLastError();
+    }
+    fn<<<ctas, threads, plan.smem, st>>>(d_systems, d_nsteps, nsys, d_work);
     return cudaGetLastError();
 }
 
@@ -331,6 +360,7 @@ template <bool C, int S>
 static cudaError_t launch_res_eb(const DevSys* d_systems, const long long* d_nsteps, int nsys, unsigned int* d_work,
                                  const ResidentPlan& plan, cudaStream_t st) {
     switch (plan.e_bits) {
+        case 2: return launch_res_t<C, S, 2>(d_systems, d_nsteps, nsys, d_work, plan, st);
         case 4: return launch_res_t<C, S, 4>(d_systems, d_nsteps, nsys, d_work, plan, st);
         case 8: return launch_res_t<C, S, 8>(d_systems, d_nsteps, nsys, d_work, plan, st);
         case 16: return launch_res_t<C, S, 16>(d_systems, d_nsteps, nsys, d_work, plan, st);
