@@ -66,7 +66,7 @@ constexpr int64_t kRoundSteps = 64;          // steps per round and system
 // synaptic updates per second is used.  With SNP_AUTOTUNE_CACHE naming a
 // file, choices are read at batch creation and written back at destroy.
 struct Autotune {
-    static constexpr int kCand[3] = {256, 384, 512};  // the resident kernel takes at most 512
+    static constexpr int kCand[3] = {256, 512, 1024};
     struct Stat {
         double work[3] = {0, 0, 0};
         double secs[3] = {0, 0, 0};

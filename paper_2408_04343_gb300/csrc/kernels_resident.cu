@@ -23,15 +23,14 @@ namespace snp {
 
 // Occupancy of the resident kernel.  The kernel is bound by the latency of
 // its global loads (a warp per slice, one dependent chain per slice), so
-// resident warps matter most: at most 512 threads per CTA and 3 CTAs per SM
-// hold it to 40 registers (48 warps per SM, which is also what a 65,536-
-// neuron system's packed emissions leave room for in shared memory), where
-// the unbounded form used 64 registers and fit 32 warps.  Measured on the
-// 8,192-system batch: 3.67e11 -> 4.22e11 synaptic updates/s, 4.44e11 with
-// 2-bit emissions; 2 CTAs of 1,024 threads at 32 registers tie with it but
-// spill more.
-constexpr int kResMaxThreads = 512;
-constexpr int kResMinBlocks = 3;
+// resident warps matter most: 2 CTAs of up to 1,024 threads per SM hold it
+// to 32 registers (64 warps per SM; a few spilled values stay in L1), where
+// the unbounded form used 64 registers and fit 32 warps.  CTAs of 1,024
+// threads stay available because a batch's largest systems run one CTA each
+// and set its critical path: capping CTAs at 512 threads (40 registers, 48
+// warps) matched this on 8,192 systems but lost 40% on 1,024.
+constexpr int kResMaxThreads = 1024;
+constexpr int kResMinBlocks = 2;
 
 template <int EB>
 __device__ __forceinline__ int32_t e_get(const uint32_t* __restrict__ e, int32_t i) {
