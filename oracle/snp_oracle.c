@@ -45,6 +45,16 @@
  *                      (k mod 2^32, i, k >> 32, 0) and key (seed mod 2^32,
  *                      seed >> 32);
  *            FORCED -- A_i[forced[i]] (used to enumerate branches).
+ *
+ * Pins (tests/test_oracle.py): Tables 1-3 and the sorting system of Sec. 6,
+ * C_{k+1} = C_k + S_k . M_Pi on delay-free systems, spike bookkeeping with
+ * delays, hand-written delay traces, brute-force enumeration of SV_k on tiny
+ * systems, NVIDIA's host-side Philox generator.  Parity unpinned: the
+ * delay-timing reading itself (a delayed rule consumes at t, keeps its
+ * neuron closed for t .. t+d-1 and emits at t+d, against Alg. 4/5 read
+ * literally, which consume and emit at t and close afterwards); no
+ * implementation of the paper is available to confirm it, and the hand
+ * traces pin this oracle to the reading, not to the paper's code.
  */
 #include <stdint.h>
 #include <stdlib.h>
