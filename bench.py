@@ -14,8 +14,9 @@ round-robin, so a system's data has been evicted by the time it is stepped
 again.  value = |syn| x executed SNP steps / device time of the K timed
 steps (CUDA events on the systems' stream, max over ranks, summed work).
 
---impl reference times the CPU oracle (test infrastructure, plain C, one
-thread) on the same workload: each step is one SNP step of the same system.
+--impl reference times the CPU oracle (test infrastructure, plain C) in its
+parallel pull form, one OpenMP thread per host core, on the same workload:
+each step is one SNP step of the same system.
 """
 from __future__ import annotations
 

@@ -362,17 +362,23 @@ int64_t snp_paper_format_elements(int32_t form, int64_t q, int64_t m, int64_t z)
  * GPU which loads the library holds until the process exits, which caps q
  * at SNP_NOALLOC_MAX_Q; larger q returns SNP_ERR_INVALID.  The first call
  * on a device looks up that array's device address (cudaGetSymbolAddress,
- * with the device current); make that first call before any stream capture.
+ * with the device current) and keeps it for the life of the process; make
+ * that first call before any stream capture.  A process that resets a
+ * device (cudaDeviceReset) must not call snp_step_noalloc on it afterwards:
+ * the kept address belonged to the destroyed context.
  * All calls share the one array and the next call overwrites it (the flag
  * words are cleared at the start of every call), so calls whose work
  * overlaps on the GPU, from any thread or stream, race and must be
  * serialised by the caller.  Work is ordered on `stream`; with steps_done
  * non-NULL the call waits for it and reports the executed step count,
  * SNP_ERR_OVERFLOW, or SNP_ERR_INVALID if the kernels found an index in the
- * device arrays out of range, a neuron with more than 32,766 rules, or a
+ * device arrays out of range, a neuron with more than 32,766 rules, a
+ * state outside snp_set_state's ranges (C >= 0, 0 <= D <= 65535, P = -1 or
+ * a rule of its neuron, D = 0 when P = -1), or a
  * rule that a step fires with a field outside snp_desc's ranges (k, j,
  * c >= 0; p, d in [0, 65535]; d = 0 when p = 0); such a neuron is treated as
- * idle for the rest of the call.                                           */
+ * idle for the rest of the call.  n is at most 2^31 - 1 (SNP_ERR_INVALID
+ * beyond).                                                                 */
 #define SNP_NOALLOC_MAX_Q 262144
 typedef struct snp_device_system {
     int32_t q;

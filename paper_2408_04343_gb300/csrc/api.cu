@@ -47,6 +47,28 @@ static void sys_free_all(snp_system* s) {
     s->device_bytes = 0;
 }
 
+// Short-lived device buffers of one call (staging of host arrays): from the
+// caller's allocator when the system has one, else stream-ordered cudaMalloc.
+static void* stage_alloc(snp_system* s, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (s->alloc.alloc) return s->alloc.alloc(s->alloc.ctx, bytes, (void*)s->stream);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void stage_free(snp_system* s, void* p, size_t bytes) {
+    if (!p) return;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (s->alloc.release)
+        s->alloc.release(s->alloc.ctx, p, bytes, (void*)s->stream);
+    else
+        cudaFreeAsync(p, s->stream);
+}
+
 static int cuda_fail(const char* what) {
     cudaError_t e = cudaGetLastError();
     return fail(SNP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -586,6 +608,23 @@ int snp_step(snp_system* s, int64_t n, int64_t* steps_done) {
     return SNP_OK;
 }
 
+// The message for the first invalid neuron a state check found; its three
+// values are read back from the caller's arrays (host or device).
+static int state_error(const snp_system* s, int32_t i, const int32_t* C, const int32_t* D, const int32_t* P,
+                       const std::string& where = std::string()) {
+    (void)s;
+    int32_t c = 0, d = 0, p = 0;
+    if (cudaMemcpy(&c, C + i, 4, cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(&d, D + i, 4, cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(&p, P + i, 4, cudaMemcpyDefault) != cudaSuccess)
+        return cuda_fail("state read-back");
+    const std::string at = " at neuron " + std::to_string(i);
+    if (c < 0) return fail(SNP_ERR_INVALID, where + "negative spike count" + at);
+    if (d < 0 || d > kMaxDelay) return fail(SNP_ERR_INVALID, where + "D out of range" + at);
+    if (p == -1) return fail(SNP_ERR_INVALID, where + "D > 0 without a pending rule" + at);
+    return fail(SNP_ERR_INVALID, where + "pending rule does not belong to neuron " + std::to_string(i));
+}
+
 int snp_branch_step(snp_system* s, int32_t nb, const int32_t* C, const int32_t* D, const int32_t* P,
                     const int32_t* choices, int32_t* C_out, int32_t* D_out, int32_t* P_out, int32_t* executed,
                     int32_t* bad, int32_t* counts) {
@@ -600,7 +639,8 @@ int snp_branch_step(snp_system* s, int32_t nb, const int32_t* C, const int32_t* 
         return fail(SNP_ERR_UNSUPPORTED, "branch steps need the optimized form with in-lists and q <= 8192");
     const size_t n = (size_t)nb * (size_t)s->q;
     cudaStream_t st = s->stream;
-    // host buffers are staged through stream-ordered device copies
+    // Host buffers are staged on the device in one block from the system's
+    // allocator, together with the word the input check reports into.
     struct Buf {
         const void* user;
         void* dev;
@@ -612,23 +652,46 @@ int snp_branch_step(snp_system* s, int32_t nb, const int32_t* C, const int32_t* 
                     {C_out, nullptr, n * 4, false, false}, {D_out, nullptr, n * 4, false, false},
                     {P_out, nullptr, n * 4, false, false}, {executed, nullptr, (size_t)nb * 4, false, false},
                     {bad, nullptr, (size_t)nb * 4, false, false}, {counts, nullptr, n * 4, false, false}};
-    int rc = SNP_OK;
+    size_t stage = 256;  // the first 256 bytes hold the check's word
     for (Buf& b : bufs) {
         if (!b.user) continue;  // counts is optional
         b.host = !is_device_ptr(b.user);
+        if (b.host) stage += (b.bytes + 255) & ~(size_t)255;
+    }
+    char* block = (char*)stage_alloc(s, stage);
+    if (!block) return fail(SNP_ERR_OOM, "staging buffer for snp_branch_step");
+    unsigned long long* d_first_bad = (unsigned long long*)block;
+    size_t off = 256;
+    int rc = SNP_OK;
+    for (Buf& b : bufs) {
+        if (!b.user) continue;
         if (!b.host) {
             b.dev = const_cast<void*>(b.user);
             continue;
         }
-        if (cudaMallocAsync(&b.dev, std::max<size_t>(b.bytes, 4), st) != cudaSuccess) {
-            b.dev = nullptr;
-            rc = fail(SNP_ERR_OOM, "staging buffer");
-            break;
-        }
+        b.dev = block + off;
+        off += (b.bytes + 255) & ~(size_t)255;
         if (b.in && cudaMemcpyAsync(b.dev, b.user, b.bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
             rc = cuda_fail("staging copy");
             break;
         }
+    }
+    // The input check runs, and is read back, before the step kernel is
+    // launched: a configuration out of range never reaches k_branch_step.
+    unsigned long long first_bad = ~0ull;
+    if (!rc && (cudaMemsetAsync(d_first_bad, 0xff, sizeof(unsigned long long), st) != cudaSuccess ||
+                launch_branch_check(s->dev, s->d_rule_base, nb, (const int32_t*)bufs[0].dev,
+                                    (const int32_t*)bufs[1].dev, (const int32_t*)bufs[2].dev, d_first_bad,
+                                    st) != cudaSuccess ||
+                cudaMemcpyAsync(&first_bad, d_first_bad, sizeof(first_bad), cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess))
+        rc = cuda_fail("branch input check");
+    if (!rc && first_bad != ~0ull) {
+        const unsigned long long b = first_bad / (unsigned long long)s->q;
+        const int32_t i = (int32_t)(first_bad % (unsigned long long)s->q);
+        rc = state_error(s, i, C + b * (unsigned long long)s->q, D + b * (unsigned long long)s->q,
+                         P + b * (unsigned long long)s->q, "configuration " + std::to_string(b) + ": ");
     }
     if (!rc && launch_branch_step(s->dev, s->d_rule_base, resident_e_bits(s->max_p), s->compact, nb,
                                   (const int32_t*)bufs[0].dev, (const int32_t*)bufs[1].dev, (const int32_t*)bufs[2].dev,
@@ -637,15 +700,16 @@ int snp_branch_step(snp_system* s, int32_t nb, const int32_t* C, const int32_t* 
                                   (int32_t*)bufs[9].dev, st) != cudaSuccess)
         rc = cuda_fail("branch step");
     for (Buf& b : bufs) {
-        if (!b.host || !b.dev) continue;
-        if (!rc && !b.in && cudaMemcpyAsync(const_cast<void*>(b.user), b.dev, b.bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        if (!b.host || !b.dev || b.in || rc) continue;
+        if (cudaMemcpyAsync(const_cast<void*>(b.user), b.dev, b.bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             rc = cuda_fail("staging copy");
-        cudaFreeAsync(b.dev, st);
     }
     uint32_t over = 0;
-    if (cudaMemcpyAsync(&over, s->dev.flags + kFlagOverflow, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return rc ? rc : cuda_fail("branch step");
+    const bool synced = cudaMemcpyAsync(&over, s->dev.flags + kFlagOverflow, 4, cudaMemcpyDeviceToHost, st) ==
+                            cudaSuccess &&
+                        cudaStreamSynchronize(st) == cudaSuccess;
+    stage_free(s, block, stage);
+    if (!synced) return rc ? rc : cuda_fail("branch step");
     if (rc) return rc;
     if (over) {
         const uint32_t zero = 0;
@@ -726,21 +790,6 @@ int snp_get_state(const snp_system* s, int32_t* C, int32_t* D, int32_t* P, int64
     return SNP_OK;
 }
 
-// The message for the first invalid neuron the import check found; its
-// three values are read back from the caller's arrays (host or device).
-static int import_error(const snp_system* s, int32_t i, const int32_t* C, const int32_t* D, const int32_t* P) {
-    int32_t c = 0, d = 0, p = 0;
-    if (cudaMemcpy(&c, C + i, 4, cudaMemcpyDefault) != cudaSuccess ||
-        cudaMemcpy(&d, D + i, 4, cudaMemcpyDefault) != cudaSuccess ||
-        cudaMemcpy(&p, P + i, 4, cudaMemcpyDefault) != cudaSuccess)
-        return cuda_fail("state read-back");
-    const std::string at = " at neuron " + std::to_string(i);
-    if (c < 0) return fail(SNP_ERR_INVALID, "negative spike count" + at);
-    if (d < 0 || d > kMaxDelay) return fail(SNP_ERR_INVALID, "D out of range" + at);
-    if (p == -1) return fail(SNP_ERR_INVALID, "D > 0 without a pending rule" + at);
-    return fail(SNP_ERR_INVALID, "pending rule does not belong to neuron " + std::to_string(i));
-}
-
 // Imports (C, D, P) on the device: the three arrays are copied (from host or
 // device memory) into buffers whose contents set_state discards anyway (the
 // spiking vectors and the export scratch), checked by one launch, and only
@@ -772,7 +821,7 @@ int snp_set_state(snp_system* s, const int32_t* C, const int32_t* D, const int32
         return cuda_fail("state upload");
     if (bad != 0xffffffffu) {
         if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail("state upload");
-        return import_error(s, (int32_t)bad, C, D, P);
+        return state_error(s, (int32_t)bad, C, D, P);
     }
     unsigned long long steps[kNumStepWords] = {step, step, 0ull, 0ull};
     uint32_t fz[kNumFlags] = {0};

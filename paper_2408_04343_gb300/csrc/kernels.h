@@ -42,6 +42,12 @@ cudaError_t launch_resident(const DevSys* d_systems, const long long* d_nsteps, 
 int resident_max_smem();
 // One forced step of nb configurations of one system (computation-tree
 // exploration); see k_branch_step.
+// Range check of the nb configurations a branch step is given (C >= 0,
+// 0 <= D <= 65535, P = -1 or a rule of its neuron, D > 0 only with P):
+// atomicMin of the offending index b*q + neuron into *first_bad.
+cudaError_t launch_branch_check(const DevSys& s, const int32_t* rule_base, int nb, const int32_t* C0,
+                                const int32_t* D0, const int32_t* P0, unsigned long long* first_bad,
+                                cudaStream_t st);
 size_t branch_smem_bytes(int q, int e_bits);
 cudaError_t launch_branch_step(const DevSys& s, const int32_t* rule_base, int e_bits, bool compact, int nb,
                                const int32_t* C0, const int32_t* D0, const int32_t* P0, const int32_t* ch,

@@ -270,6 +270,45 @@ __global__ void __launch_bounds__(256) k_branch_step(DevSys s, const int32_t* __
     }
 }
 
+// Input check of snp_branch_step, run before k_branch_step reads anything:
+// configuration b's neuron i (caller's order, at b*q + i) must hold C >= 0,
+// 0 <= D <= 65535, P = -1 or one of neuron i's rules, and D > 0 only with a
+// pending rule -- the rules snp_set_state's import applies.  The smallest
+// offending index b*q + i goes to *first_bad (set to ~0 by the caller).
+// Every array read here is in range for any values of C, D and P.
+__global__ void k_branch_check(DevSys s, const int32_t* __restrict__ rule_base, long long total,
+                               const int32_t* __restrict__ C0, const int32_t* __restrict__ D0,
+                               const int32_t* __restrict__ P0, unsigned long long* first_bad) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        const long long b = idx / s.q;
+        const int32_t slot = (int32_t)(idx - b * s.q);
+        const unsigned long long at = (unsigned long long)b * (unsigned long long)s.q + neuron_id(s, slot);
+        const int32_t c = C0[at], d = D0[at], p = P0[at];
+        const int32_t r0 = rule_base[slot];
+        bool ok = c >= 0 && d >= 0 && d <= kMaxDelay;
+        if (p == -1)
+            ok = ok && d == 0;
+        else
+            ok = ok && p >= r0 && p - r0 < rule_hi(s, slot) - rule_lo(s, slot);
+        if (!ok) atomicMin(first_bad, at);
+    }
+}
+
+cudaError_t launch_branch_check(const DevSys& s, const int32_t* rule_base, int nb, const int32_t* C0,
+                                const int32_t* D0, const int32_t* P0, unsigned long long* first_bad,
+                                cudaStream_t st) {
+    const long long total = (long long)nb * s.q;
+    if (total <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (total + 255) / 256;
+    const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)std::max(1, sms) * 8));
+    k_branch_check<<<grid, 256, 0, st>>>(s, rule_base, total, C0, D0, P0, first_bad);
+    return cudaGetLastError();
+}
+
 size_t branch_smem_bytes(int q, int e_bits) {
     const long long nslices = ((long long)q + 31) / 32;
     const long long words = ((nslices * 32 + 32) * e_bits + 31) / 32;

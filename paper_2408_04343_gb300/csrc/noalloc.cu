@@ -179,13 +179,15 @@ __global__ void __launch_bounds__(256) k_na_step(NaSys s, int32_t t) {
     bool active = false;
     if (j < s.q) {
         int32_t r0 = s.rule_off[j], r1 = s.rule_off[j + 1];
-        bool ok = r0 >= 0 && r0 <= r1 && (long long)r1 <= s.m && r1 - r0 <= kMaxRulesPerNeuron;
         int32_t c = s.C[j];
+        bool ok = r0 >= 0 && r0 <= r1 && (long long)r1 <= s.m && r1 - r0 <= kMaxRulesPerNeuron && c >= 0;
         const int32_t P = s.P[j], D = s.D[j];
         uint32_t st = 0u;
         if (P != -1) {
             ok = ok && P >= r0 && P < r1 && D >= 0 && D <= (int32_t)kDMask;
             st = ((uint32_t)(P - r0 + 1) << kPendShift) | ((uint32_t)D & kDMask);
+        } else {
+            ok = ok && D == 0;  // a neuron can only be closed by a pending rule
         }
         if (!ok) {
             atomicOr(fl + kNaInvalid, 1u);
@@ -273,7 +275,9 @@ static void na_launch(const NaSys& s, int32_t t, int sel, cudaStream_t st) {
         k_na_step<G, S, SNP_SELECT_PHILOX><<<grid, 256, 0, st>>>(s, t);
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device.  The
+// cached address belongs to the device's primary context: cudaDeviceReset
+// makes it stale, which the library cannot detect (documented in snp.h).
 static std::mutex g_na_mu;
 static uint32_t* g_na_ptr[64] = {nullptr};
 
@@ -313,7 +317,7 @@ extern "C" int snp_step_noalloc(const snp_device_system* d, int32_t select, uint
         !d->in_offsets || (d->num_in > 0 && !d->in_sources) || !d->C || !d->D || !d->P || !d->S)
         return fail(SNP_ERR_INVALID, "NULL array");
     if (select != SNP_SELECT_FIRST && select != SNP_SELECT_PHILOX) return fail(SNP_ERR_INVALID, "bad select");
-    if (n < 0) return fail(SNP_ERR_INVALID, "n < 0");
+    if (n < 0 || n > INT32_MAX) return fail(SNP_ERR_INVALID, "n must be in [0, 2^31 - 1]");
     if (n == 0) return SNP_OK;
     uint32_t* scratch = nullptr;
     int rc = na_scratch(&scratch);

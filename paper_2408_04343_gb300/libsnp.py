@@ -392,12 +392,18 @@ def paper_format_elements(form: int, q: int, m: int, z: int) -> int:
 # ---- stepping without allocation -------------------------------------------
 
 def snp_step_noalloc(q, m, rule_offsets, rule_k, rule_j, rule_c, rule_p, rule_d, in_offsets, in_sources,
-                     C, D, P, S, *, select=SNP_SELECT_FIRST, seed=0, step=0, n=1, stream=None, wait=True):
+                     C, D, P, S, *, num_in=None, select=SNP_SELECT_FIRST, seed=0, step=0, n=1, stream=None,
+                     wait=True):
     """snp_step_noalloc over caller-owned device buffers (torch CUDA tensors
     or raw pointers, int32).  For callers that cannot allocate device memory:
     the library uses its fixed static scratch (q <= SNP_NOALLOC_MAX_Q).
-    Returns the executed step count when wait, else None."""
-    num_in = in_sources.numel() if hasattr(in_sources, "numel") else 0
+    num_in is the length of in_sources; it is taken from a tensor and must be
+    given when in_sources is a raw pointer.  Returns the executed step count
+    when wait, else None."""
+    if num_in is None:
+        if not hasattr(in_sources, "numel"):
+            raise TypeError("num_in must be given when in_sources is not a tensor")
+        num_in = in_sources.numel()
     d = snp_device_system(int(q), int(m), int(num_in), _ptr(rule_offsets), _ptr(rule_k), _ptr(rule_j),
                           _ptr(rule_c), _ptr(rule_p), _ptr(rule_d), _ptr(in_offsets), _ptr(in_sources),
                           _ptr(C), _ptr(D), _ptr(P), _ptr(S))

@@ -149,3 +149,82 @@ def test_branch_step_matches_oracle_on_many_configurations():
         assert (C1[b] == s2[0]).all() and (D1[b] == s2[1]).all() and (P1[b] == s2[2]).all(), b
         assert (cnt[b] == oracle.count_choices(d, s2)).all(), b
     gs.close()
+
+
+@pytest.mark.parametrize("field", ["C", "D", "P_other", "P_high", "D_without_P"])
+def test_branch_step_rejects_bad_configurations(field):
+    """A configuration outside the state's ranges (C < 0, D outside
+    0..65535, a pending rule of another neuron or beyond m, D > 0 with no
+    pending rule) is refused with SNP_ERR_INVALID naming the configuration
+    and neuron; the check runs before the step kernel, so nothing is
+    written.  A good call afterwards still matches the oracle."""
+    d = synth.random_system(1500, 41, outdeg=(2, 8), rules=(3, 4), d_range=(0, 3), spikes=(0, 12))
+    gs = libsnp.System(d, select=libsnp.SNP_SELECT_FIRST)
+    st = oracle.initial_state(d)
+    oracle.run(d, st, 3, oracle.PHILOX, 5)
+    nb = 6
+    C = np.stack([st[0]] * nb); D = np.stack([st[1]] * nb); P = np.stack([st[2]] * nb)
+    ch = np.zeros_like(C)
+    b, i = 4, 777
+    Cb, Db, Pb = C.copy(), D.copy(), P.copy()
+    if field == "C":
+        Cb[b, i] = -3
+    elif field == "D":
+        Pb[b, i] = int(d.rule_offsets[i]); Db[b, i] = 70000
+    elif field == "P_other":
+        Pb[b, i] = int(d.rule_offsets[i + 1]); Db[b, i] = 1      # first rule of neuron i+1
+    elif field == "P_high":
+        Pb[b, i] = int(d.rule_offsets[-1]) + 5; Db[b, i] = 1
+    else:
+        Pb[b, i] = -1; Db[b, i] = 2
+    sentinel = np.full_like(C, 12345)
+    C1, D1, P1 = sentinel.copy(), sentinel.copy(), sentinel.copy()
+    ex = np.full(nb, 7, np.int32); bad = np.full(nb, 7, np.int32)
+    lib = libsnp.load()
+    rc = lib.snp_branch_step(gs.handle, nb, libsnp._ptr(Cb), libsnp._ptr(Db), libsnp._ptr(Pb), libsnp._ptr(ch),
+                             libsnp._ptr(C1), libsnp._ptr(D1), libsnp._ptr(P1), libsnp._ptr(ex), libsnp._ptr(bad),
+                             None)
+    assert rc == libsnp.SNP_ERR_INVALID
+    msg = lib.snp_last_error().decode()
+    assert f"configuration {b}" in msg and str(i) in msg, msg
+    assert (C1 == 12345).all() and (D1 == 12345).all() and (P1 == 12345).all()
+    assert (ex == 7).all() and (bad == 7).all()
+    # a good call afterwards
+    C1, D1, P1, ex, bad, cnt = gs.branch_step(C, D, P, ch)
+    s2 = tuple(x.copy() for x in st)
+    oracle.step(d, s2, 3, oracle.FORCED, forced=np.zeros(d.q, np.int32))
+    assert (ex == 1).all() and (bad == 0).all()
+    for k in range(nb):
+        assert (C1[k] == s2[0]).all() and (D1[k] == s2[1]).all() and (P1[k] == s2[2]).all()
+    gs.close()
+
+
+def test_branch_step_stages_through_the_callers_allocator():
+    """With a caller allocator, the host arrays of a branch step are staged
+    in memory the allocator hands out (and returns), not in the library's."""
+    import ctypes as ct
+    d = synth.random_system(600, 43, outdeg=(2, 8), rules=(3, 4), d_range=(0, 3), spikes=(0, 12))
+    live, calls = {}, {"alloc": 0, "release": 0}
+
+    def alloc(ctx, nbytes, stream):
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        calls["alloc"] += 1
+        return t.data_ptr()
+
+    def release(ctx, ptr, nbytes, stream):
+        calls["release"] += 1
+        live.pop(ptr, None)
+
+    a = libsnp.snp_allocator(libsnp.ALLOC_FN(alloc), libsnp.RELEASE_FN(release), None)
+    gs = libsnp.System(d, select=libsnp.SNP_SELECT_FIRST, allocator=a)
+    before = dict(calls)
+    st = oracle.initial_state(d)
+    C, D, P = (np.stack([x] * 3) for x in st)
+    C1, D1, P1, ex, bad, cnt = gs.branch_step(C, D, P, np.zeros_like(C))
+    assert calls["alloc"] == before["alloc"] + 1 and calls["release"] == before["release"] + 1
+    s2 = tuple(x.copy() for x in st)
+    oracle.step(d, s2, 0, oracle.FORCED, forced=np.zeros(d.q, np.int32))
+    assert (C1[2] == s2[0]).all() and (P1[2] == s2[2]).all()
+    gs.close()
+    del a
