@@ -276,6 +276,20 @@ def serving_requests(rate_per_s: float, count: int, seed: int = 5005,
     return [Request(float(a), int(qv), int(sv), int(sd)) for a, qv, sv, sd in zip(t, qs, st, seeds)]
 
 
+def _request_member(req: Request) -> SystemDesc:
+    return req.system()
+
+
+def serving_systems(reqs, processes: int = 0):
+    """The system of every request, drawn in a spawned process pool when
+    processes > 1 (same systems: each is seeded on its own)."""
+    if processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.map(_request_member, reqs, chunksize=1)
+    return [_request_member(r) for r in reqs]
+
+
 def subset_sum_shaped(n: int, seed: int = 6006, v=None) -> SystemDesc:
     """A stand-in with the sizes of Sec. 6's subset-sum family (the
     construction itself is not in the paper): for n numbers v_i drawn from
