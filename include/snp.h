@@ -142,12 +142,13 @@ typedef struct snp_options {
  *                      any term's language.  rule_k and rule_j are then not
  *                      read and may be NULL.  rule_term_offsets[0] = 0,
  *                      monotone, at least one term per rule; term_k, term_j
- *                      >= 0.  The step runs unions through compiled
- *                      per-neuron applicability tables only, so snp_create
- *                      returns SNP_ERR_UNSUPPORTED unless every neuron has
- *                      at most 4 rules, c < 64, p < 32, d < 32 and
- *                      K + L <= 14, with K = 1 + the largest term_k or c of
- *                      the neuron and L the lcm of its non-zero term_j.
+ *                      >= 0.  When every neuron has at most 4 rules,
+ *                      c < 64, p < 32, d < 32 and K + L <= 14 (K = 1 + the
+ *                      largest term_k or c of the neuron, L the lcm of its
+ *                      non-zero term_j) the step reads one compiled 16-byte
+ *                      applicability table per neuron; otherwise it tests
+ *                      each rule's terms (any number of rules and terms,
+ *                      the ranges above).
  *                      Zero-initialise the struct so that callers unaware
  *                      of these fields leave them NULL.                  */
 typedef struct snp_desc {

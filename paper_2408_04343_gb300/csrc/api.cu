@@ -149,6 +149,7 @@ void build_plan(snp_system* s, std::vector<Piece>& plan) {
         tl.e_bits = tp.e_bits;
         tl.G = tp.G;
         tl.acc_words = tp.acc_words;
+        tl.rin_words = tp.rin_words;
         tl.src_bits = tp.src_bits;
         tl.pairs = tp.pairs;
         tl.rle = tp.rle;
@@ -462,13 +463,10 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
         delete s;
         return st;
     }
-    // union expressions step through the compiled records only (on every form)
+    // union expressions step through the compiled records when every neuron
+    // fits one, else through union records in the general rule table
     s->unions = desc->rule_term_offsets != nullptr;
-    if (s->unions && hp.rec.empty()) {
-        delete s;
-        return fail(SNP_ERR_UNSUPPORTED,
-                    "rules given as unions need <= 4 rules per neuron, c < 64, p < 32, d < 32 and K + L <= 14");
-    }
+
     if (want_tiled) {
         int dev = 0, sms = 0, optin = 0;
         cudaGetDevice(&dev);

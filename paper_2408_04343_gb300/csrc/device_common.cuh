@@ -130,6 +130,34 @@ __device__ __forceinline__ bool rule_applies(int32_t n, const RuleF& f) {
     return divides((uint32_t)(n - f.k), (uint32_t)f.j);
 }
 
+// Rule r of a rule table applies to n spikes.  In the general (4-word)
+// table a rule whose expression is a union of terms has the top bit of word
+// 0 set: the low bits index its first (k, j) term record (8-byte units from
+// the start of the table), word 1 counts its terms, and the rule applies
+// when n >= c and n is in any term's language (see pack_union_rules).
+template <bool COMPACT>
+__device__ __forceinline__ bool rule_applies_at(const uint32_t* __restrict__ rules, int32_t r, int32_t n) {
+    if (COMPACT) return rule_applies(n, load_rule<true>(rules, r));
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(rules) + r);
+    if ((w.x & 0x80000000u) == 0u) {
+        RuleF f;
+        f.k = (int32_t)w.x;
+        f.j = (int32_t)w.y;
+        f.c = (int32_t)w.z;
+        f.p = 0;
+        f.d = 0;
+        return rule_applies(n, f);
+    }
+    if (n < (int32_t)w.z) return false;
+    const uint2* term = reinterpret_cast<const uint2*>(rules) + (w.x & 0x7fffffffu);
+    for (uint32_t u = 0; u < w.y; ++u) {
+        const uint2 kj = __ldg(term + u);
+        const int32_t k = (int32_t)kj.x;
+        if (n >= k && (kj.y == 0u ? n == k : divides((uint32_t)(n - k), kj.y))) return true;
+    }
+    return false;
+}
+
 // Rule range of a slot and the caller's id of a slot.
 __device__ __forceinline__ int32_t rule_lo(const DevSys& s, int32_t slot) {
     return s.rules_per_neuron > 0 ? slot * s.rules_per_neuron : __ldg(s.rule_off + slot);
@@ -228,7 +256,7 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
     }
     if (SEL == SNP_SELECT_FIRST) {
         for (int32_t r = r0; r < r1; ++r) {
-            if (rule_applies(n, load_rule<COMPACT>(rules, r))) {
+            if (rule_applies_at<COMPACT>(rules, r, n)) {
                 pick = r;
                 break;
             }
@@ -238,7 +266,7 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
         // the idx-th set bit
         uint32_t mask = 0u;
         for (int32_t r = r0; r < r1; ++r)
-            if (rule_applies(n, load_rule<COMPACT>(rules, r))) mask |= 1u << (r - r0);
+            if (rule_applies_at<COMPACT>(rules, r, n)) mask |= 1u << (r - r0);
         const int32_t cnt = __popc(mask);
         if (cnt == 1) {
             pick = r0 + __ffs(mask) - 1;
@@ -252,7 +280,7 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
     } else {
         int32_t cnt = 0, first = -1;
         for (int32_t r = r0; r < r1; ++r) {
-            if (rule_applies(n, load_rule<COMPACT>(rules, r))) {
+            if (rule_applies_at<COMPACT>(rules, r, n)) {
                 if (cnt == 0) first = r;
                 ++cnt;
             }
@@ -264,7 +292,7 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
                                             (uint32_t)(seed >> 32));
             int32_t idx = (int32_t)(((unsigned long long)x.v[0] * (unsigned long long)cnt) >> 32);
             for (int32_t r = first; r < r1; ++r) {
-                if (rule_applies(n, load_rule<COMPACT>(rules, r))) {
+                if (rule_applies_at<COMPACT>(rules, r, n)) {
                     if (idx == 0) {
                         pick = r;
                         break;
@@ -322,15 +350,40 @@ __device__ __forceinline__ uint32_t compiled_mask(const uint4& rec, int32_t n) {
     return e < 8u ? (rec.x >> (4u * e)) & 15u : (rec.y >> (4u * (e - 8u))) & 15u;
 }
 
+// The same with the constants of x / L read from a table in shared memory
+// (tab[L] = {kMod32.m[L], kMod32.sh[L]}, see fill_mod_table): lanes with
+// different L then read different words of one small table, where an
+// indexed __constant__ read is serialised over the warp's distinct addresses.
+__device__ __forceinline__ uint32_t compiled_mask_tab(const uint4& rec, int32_t n, const uint2* __restrict__ tab) {
+    const uint32_t K = (rec.y >> 24) & 15u, L = rec.y >> 28;
+    uint32_t e = (uint32_t)n;
+    if (e >= K) {
+        const uint32_t x = e - K;
+        const uint2 mg = tab[L];
+        const uint32_t qq = __umulhi(x, mg.x) >> mg.y;
+        e = K + (L > 1u ? x - qq * L : 0u);
+    }
+    return e < 8u ? (rec.x >> (4u * e)) & 15u : (rec.y >> (4u * (e - 8u))) & 15u;
+}
+
+// Fills tab[0..15] for compiled_mask_tab (threads 0..15 of the block; the
+// caller publishes it with a barrier).
+__device__ __forceinline__ void fill_mod_table(uint2* tab) {
+    const uint32_t l = threadIdx.x;
+    if (l < 16u) tab[l] = l >= 2u ? make_uint2(kMod32.m[l], kMod32.sh[l]) : make_uint2(0u, 0u);
+}
+
 // The 16-bit (c, p, d) field of rule t of a compiled record.
 __device__ __forceinline__ uint32_t compiled_field(const uint4& rec, uint32_t t) {
     return ((t < 2u ? rec.z : rec.w) >> (16u * (t & 1u))) & 0xffffu;
 }
 
 // RK: take the Philox round keys from rk (else derive them from seed).
+// tab: the shared-memory table of compiled_mask_tab, or NULL.
 template <int SEL, bool RK = false>
 __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, uint32_t st, unsigned long long k,
-                                                  uint32_t nid, uint64_t seed, const uint32_t* rk = nullptr) {
+                                                  uint32_t nid, uint64_t seed, const uint32_t* rk = nullptr,
+                                                  const uint2* tab = nullptr) {
     SelOut o;
     o.c_after = n;
     o.emit = 0;
@@ -348,7 +401,7 @@ __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, ui
     }
     o.st = 0u;
     o.active = false;
-    uint32_t mask = compiled_mask(rec, n);
+    uint32_t mask = tab ? compiled_mask_tab(rec, n, tab) : compiled_mask(rec, n);
     if (mask == 0u) return o;
     if (SEL == SNP_SELECT_PHILOX && (mask & (mask - 1u)) != 0u) {
         const uint32_t cnt = (uint32_t)__popc(mask);
@@ -374,6 +427,169 @@ __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, ui
     return o;
 }
 
+// select_compiled without data-dependent branches except around the Philox
+// draw (taken when any lane of the warp needs it): the pending, closed,
+// idle and selecting cases are all computed and the result picked by
+// selects, so the lanes of a warp stay converged.  Same results as
+// select_compiled<SEL, true> with the round keys rk and the table tab.
+template <int SEL>
+__device__ __forceinline__ SelOut select_compiled_flat(const uint4 rec, int32_t n, uint32_t st, unsigned long long k,
+                                                       uint32_t nid, const uint32_t* rk, const uint2* tab) {
+    const uint32_t pend = st >> kPendShift;
+    const bool closed = pend != 0u;
+    const bool completing = closed && (st & kDMask) == 0u;
+    uint32_t mask = closed ? 0u : compiled_mask_tab(rec, n, tab);
+    if (SEL == SNP_SELECT_PHILOX) {
+        const bool draw = (mask & (mask - 1u)) != 0u;
+        if (__any_sync(__activemask(), draw)) {
+            const uint32_t cnt = (uint32_t)__popc(mask);
+            const Philox4 x = philox4x32_10_rk((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, rk);
+            uint32_t idx = draw ? (uint32_t)(((unsigned long long)x.v[0] * cnt) >> 32) : 0u;  // < cnt <= 4
+            mask = idx > 0u ? mask & (mask - 1u) : mask;
+            mask = idx > 1u ? mask & (mask - 1u) : mask;
+            mask = idx > 2u ? mask & (mask - 1u) : mask;
+        }
+    }
+    const bool selected = mask != 0u;
+    const uint32_t t = (uint32_t)(__ffs(mask) - 1);          // the chosen rule (FIRST: the lowest)
+    const uint32_t f = compiled_field(rec, completing ? pend - 1u : t);
+    const int32_t c = (int32_t)(f & 63u), p = (int32_t)((f >> 6) & 31u), d = (int32_t)(f >> 11);
+    SelOut o;
+    o.active = closed || selected;
+    o.s = selected ? (int32_t)t : -1;
+    o.c_after = selected ? n - c : n;
+    o.emit = (completing || (selected && d == 0)) ? p : 0;
+    o.st = closed ? (completing ? 0u : st - 1u)
+                  : ((selected && d > 0) ? ((t + 1u) << kPendShift) | (uint32_t)(d - 1) : 0u);
+    return o;
+}
+
+// ---- the select of one slot from its compiled record, for the fused step --
+// Philox4x32-10 at counter (k mod 2^32, nid, k >> 32, 0): only word 1 of the
+// counter (the neuron) differs between the neurons of one step, so in rounds
+// 1 to 3 most products and XORs are the same for every neuron.  PhiloxHead
+// holds those parts (computed once per step), philox_x0 finishes the ten
+// rounds from them and returns output word 0 -- the same value as
+// philox4x32_10_rk(k, nid, k >> 32, 0, rk).v[0].
+struct PhiloxHead {
+    uint32_t u1;    // round 1: c0 = u1 ^ nid
+    uint32_t u4k;   // round 2: c2 = hi(A c0) ^ u4k
+    uint32_t u6k;   // round 3: c0 = hi(B c2) ^ u6k
+    uint32_t w;     // round 3: c2 = w ^ lo(A c0 of round 2)
+    uint32_t loA3;  // round 3: c3
+};
+
+__device__ __forceinline__ PhiloxHead philox_head(unsigned long long k, const uint32_t* rk) {
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    const uint32_t k0 = (uint32_t)k, k1 = (uint32_t)(k >> 32);
+    // round 1 on (k0, nid, k1, 0)
+    const unsigned long long pA1 = (unsigned long long)kMulA * k0, pB1 = (unsigned long long)kMulB * k1;
+    const uint32_t u1 = (uint32_t)(pB1 >> 32) ^ rk[0];  // c0 = u1 ^ nid
+    const uint32_t u2 = (uint32_t)pB1;                   // c1
+    const uint32_t u3 = (uint32_t)(pA1 >> 32) ^ rk[1];   // c2
+    const uint32_t u4 = (uint32_t)pA1;                   // c3
+    // round 2: B c2 does not depend on nid
+    const unsigned long long pB2 = (unsigned long long)kMulB * u3;
+    const uint32_t u5 = (uint32_t)(pB2 >> 32) ^ u2 ^ rk[2];  // c0
+    const uint32_t u6 = (uint32_t)pB2;                        // c1
+    // round 3: A c0 does not depend on nid
+    const unsigned long long pA3 = (unsigned long long)kMulA * u5;
+    PhiloxHead h;
+    h.u1 = u1;
+    h.u4k = u4 ^ rk[3];
+    h.u6k = u6 ^ rk[4];
+    h.w = (uint32_t)(pA3 >> 32) ^ rk[5];
+    h.loA3 = (uint32_t)pA3;
+    return h;
+}
+
+__device__ __forceinline__ uint32_t philox_x0(const PhiloxHead& h, uint32_t nid, const uint32_t* rk) {
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    // rounds 2 and 3: the parts that depend on nid
+    const unsigned long long pA2 = (unsigned long long)kMulA * (h.u1 ^ nid);
+    const uint32_t c2r2 = (uint32_t)(pA2 >> 32) ^ h.u4k, c3r2 = (uint32_t)pA2;
+    const unsigned long long pB3 = (unsigned long long)kMulB * c2r2;
+    uint32_t c0 = (uint32_t)(pB3 >> 32) ^ h.u6k, c1 = (uint32_t)pB3, c2 = h.w ^ c3r2, c3 = h.loA3;
+#pragma unroll
+    for (int r = 3; r < 10; ++r) {
+        const unsigned long long pA = (unsigned long long)kMulA * c0;
+        const unsigned long long pB = (unsigned long long)kMulB * c2;
+        const uint32_t n0 = (uint32_t)(pB >> 32) ^ c1 ^ rk[2 * r];
+        const uint32_t n2 = (uint32_t)(pA >> 32) ^ c3 ^ rk[2 * r + 1];
+        c0 = n0;
+        c1 = (uint32_t)pB;
+        c2 = n2;
+        c3 = (uint32_t)pA;
+    }
+    return c0;
+}
+
+// The compiled applicability mask without branches: the period's remainder
+// is computed for every n (discarded below K), and the table of K + L
+// four-bit masks is read as one 64-bit value.  tab as for compiled_mask_tab.
+__device__ __forceinline__ uint32_t compiled_mask_flat(const uint4& rec, int32_t n, const uint2* __restrict__ tab) {
+    const uint32_t K = (rec.y >> 24) & 15u, L = rec.y >> 28;
+    const uint32_t x = (uint32_t)n - K;
+    const uint2 mg = tab[L];
+    const uint32_t r = x - (__umulhi(x, mg.x) >> mg.y) * L;  // x mod L when n >= K and L >= 2
+    const uint32_t e = (uint32_t)n < K ? (uint32_t)n : K + (L > 1u ? r : 0u);
+    const unsigned long long t64 = ((unsigned long long)rec.y << 32) | rec.x;
+    return (uint32_t)(t64 >> (4u * e)) & 15u;
+}
+
+// pick[mask | idx << 4] = the position of the idx-th (0-based) set bit of a
+// four-bit mask (0 where idx >= popc(mask)); threads 0..63 fill it.
+__device__ __forceinline__ void fill_pick_table(uint8_t* pick) {
+    const uint32_t i = threadIdx.x;
+    if (i < 64u) {
+        uint32_t m = i & 15u, idx = i >> 4, pos = 0u;
+        for (uint32_t b = 0; b < 4u; ++b) {
+            if (m & (1u << b)) {
+                if (idx == 0u) {
+                    pos = b;
+                    break;
+                }
+                --idx;
+            }
+        }
+        pick[i] = (uint8_t)pos;
+    }
+}
+
+// The select of a slot from its compiled record (same result as
+// select_compiled): every case computed without data-dependent branches
+// except the Philox draw, which runs when any lane of the warp draws.
+template <int SEL>
+__device__ __forceinline__ SelOut select_rec_flat(const uint4 rec, int32_t n, uint32_t st, uint32_t nid,
+                                                  const PhiloxHead& ph, const uint32_t* rk,
+                                                  const uint2* __restrict__ tab, const uint8_t* __restrict__ pick) {
+    const uint32_t pend = st >> kPendShift;
+    const bool closed = pend != 0u;
+    const bool completing = closed && (st & kDMask) == 0u;
+    const uint32_t mask = closed ? 0u : compiled_mask_flat(rec, n, tab);
+    uint32_t idx = 0u;
+    if (SEL == SNP_SELECT_PHILOX) {
+        const bool draw = (mask & (mask - 1u)) != 0u;
+        if (__any_sync(__activemask(), draw)) {
+            const uint32_t x0 = philox_x0(ph, nid, rk);
+            idx = draw ? (uint32_t)(((unsigned long long)x0 * (uint32_t)__popc(mask)) >> 32) : 0u;  // < popc <= 4
+        }
+    }
+    const bool selected = mask != 0u;
+    const uint32_t t = pick[mask | (idx << 4)];
+    const uint32_t fi = completing ? pend - 1u : t;
+    const uint32_t f = (uint32_t)((((unsigned long long)rec.w << 32) | rec.z) >> (16u * fi)) & 0xffffu;
+    const int32_t c = (int32_t)(f & 63u), p = (int32_t)((f >> 6) & 31u), d = (int32_t)(f >> 11);
+    SelOut o;
+    o.active = closed || selected;
+    o.s = selected ? (int32_t)t : -1;
+    o.c_after = selected ? n - c : n;
+    o.emit = (completing || (selected && d == 0)) ? p : 0;
+    o.st = closed ? (completing ? 0u : st - 1u)
+                  : ((selected && d > 0) ? ((t + 1u) << kPendShift) | (uint32_t)(d - 1) : 0u);
+    return o;
+}
+
 // ---- forced choices (computation-tree exploration) ----------------------
 // Applicable rules of an idle neuron with n spikes, in index order: bit t of
 // the result (up to 32 rules) and the count.
@@ -381,7 +597,7 @@ template <bool COMPACT>
 __device__ __forceinline__ int32_t count_applicable(const uint32_t* __restrict__ rules, int32_t r0, int32_t r1,
                                                     int32_t n) {
     int32_t cnt = 0;
-    for (int32_t r = r0; r < r1; ++r) cnt += rule_applies(n, load_rule<COMPACT>(rules, r)) ? 1 : 0;
+    for (int32_t r = r0; r < r1; ++r) cnt += rule_applies_at<COMPACT>(rules, r, n) ? 1 : 0;
     return cnt;
 }
 
@@ -465,7 +681,7 @@ __device__ SelOut select_forced_idx(const DevSys& s, int32_t slot, int32_t n, ui
     }
     int32_t pick = -1;
     for (int32_t r = r0; r < r1 && pick < 0; ++r)
-        if (rule_applies(n, load_rule<COMPACT>(s.rules, r)) && idx-- == 0) pick = r;
+        if (rule_applies_at<COMPACT>(s.rules, r, n) && idx-- == 0) pick = r;
     const RuleF f = load_rule<COMPACT>(s.rules, pick);
     o.active = true;
     o.s = pick - r0;

@@ -57,6 +57,7 @@ cudaError_t launch_branch_step(const DevSys& s, const int32_t* rule_base, int e_
 // Tiled engine (kernels_tiled.cu): device view of a TiledPack.
 struct TiledSys {
     int32_t P, part_words, e_bits, G, acc_words, src_bits, pairs, rle;
+    int32_t rin_words;      // > 0: the partner's in-flow arrives in a shared buffer (see k_tiled_step)
     const int32_t* tstart;  // run-length layout: first target of each thread's run, [G][kTiledThreads]
     const int32_t* sub;     // [G][kTiledMaxSub+1] window starts (words, multiples of 4); CTA g*P+h
     const uint32_t* ent;    // (dst_local << src_bits) | src_local

@@ -143,25 +143,30 @@ __device__ __forceinline__ void pairs_merge(const uint32_t* __restrict__ Esm, ui
     cur = a1;
 }
 
-// Run-length step: when the advance d is non-zero, add the run to the
-// accumulator at shared address a and start a new run (returns 0), else
-// return the run.  One predicate serves the reduction and the reset.
+// Run-length step: when the advance d is non-zero, store the run as the
+// in-flow of the target at shared address a (the thread owns that target:
+// runs are cut at target boundaries) and start a new run (returns 0), else
+// return the run.  One predicate serves the store and the reset.
 __device__ __forceinline__ uint32_t run_flush(uint32_t a, uint32_t run, uint32_t d) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.u32 p, %2, 0;\n\t"
-        "@p red.shared.add.u32 [%1], %3;\n\t"
+        "@p st.shared.u32 [%1], %3;\n\t"
         "selp.u32 %0, 0, %3, p;\n\t}"
         : "=r"(r)
         : "r"(a), "r"(d), "r"(run));
     return r;
 }
 
+__device__ __forceinline__ void st_shared_u32(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
+
 // Run-length layout, one 16-byte load: five 24-bit entries b << db | d,
 // where b is the source's bit index in the packed emissions (source x EB)
 // and d the target advance.  Each entry first advances the thread's target
-// by d -- adding the run of the previous target to its accumulator when
+// by d -- storing the run of the previous target in its accumulator when
 // d > 0 -- then adds its emission to the run: word b / 32 of Esm, rotated
 // by b mod 32 (the funnel shift takes its count mod 32).  `cur` is the
 // shared address of the current target's accumulator.
@@ -324,7 +329,12 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
     const int32_t s0 = base + tid * n - max(0, tid - r);          // sorted index of the first
     const uint4* col = reinterpret_cast<const uint4*>(tl.ent) + base + tid;
     uint4 qa[D], qb[D];
-    load_batch(qa, col, 0, nt);
+    if constexpr (LAYOUT == kLayoutRle) {
+        qa[0] = ld_stream_v4(col);  // unguarded: see the gather loop below
+        qa[1] = ld_stream_v4(col + kTiledThreads);
+    } else {
+        load_batch(qa, col, 0, nt);
+    }
     const int32_t tstart = LAYOUT == kLayoutRle ? __ldg(tl.tstart + (size_t)blockIdx.x * kTiledThreads + tid) : 0;
     if (threadIdx.x < 4) Esm[tl.part_words + threadIdx.x] = 0u;
     if (threadIdx.x == 0) mbar_init(ebar);
@@ -362,11 +372,27 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
         if (!landed) mbar_wait0(ebar, kWaitPolls);  // let the copy land before the shared memory goes away
         return kPhaseTimeout;
     }
+    // paired and run-length layouts: the target being summed and its sum so far
+    uint32_t cur = acc0 + (LAYOUT == kLayoutRle ? (uint32_t)tstart * 4u : 0u), run = 0u;
+    if constexpr (LAYOUT == kLayoutRle) {
+        // one vector per iteration, loads two vectors ahead; no per-vector
+        // guard: the loads past a thread's last vector read the slack rows
+        // at the end of the entry buffer (or another thread's vectors) and
+        // are never added
+        uint4 x0 = qa[0], x1 = qa[1];
+        for (int32_t u = 0; u < nt; ++u) {
+            const uint4 v = x0;
+            x0 = x1;
+            x1 = ld_stream_v4(col + (size_t)(u + 2) * kTiledThreads);
+            rle_vector<EB>(Esm, v, db, cur, run);
+        }
+        st_shared_u32(cur, run);  // the last target of the run (the dummy slot for an empty run)
+        __syncthreads();
+        return kPhaseOk;
+    }
     // two batches in flight: the next batch loads while this one is added
     int k = 0;
     while (k + 1 < kTiledMaxSub && s0 >= wb[k + 1]) ++k;
-    // paired and run-length layouts: the target being summed and its sum so far
-    uint32_t cur = acc0 + (LAYOUT == kLayoutRle ? (uint32_t)tstart * 4u : 0u), run = 0u;
     for (int32_t u = 0;;) {
         load_batch(qb, col, u + D, nt);
         gather_batch<EB, LAYOUT, D>(qa, u, nt, s0, wb, k, Esm, acc0, db, wmask, sbits, cur, run);
@@ -431,6 +457,14 @@ __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t a) {
     return v;
 }
 
+__device__ __forceinline__ uint4 ld_cluster_v4(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a));
+    return v;
+}
+
 // Finish of step kg and select of step kg+1 for one slice, from its in-flow.
 template <int SEL, int EB>
 __device__ __forceinline__ void finish_select_slice(const DevSys& s, bool select, bool compact, int32_t* Sk,
@@ -468,21 +502,56 @@ __device__ __forceinline__ void finish_select_slice(const DevSys& s, bool select
     if (select) pk_put_slice<EB>(Ek, slice, lane, emit);
 }
 
+// ---- select phase of the fused step, four slots per lane ----------------
+// A warp takes 128 consecutive slots of the CTA's share at a time, lane l
+// slots 4l .. 4l+3: C, the status words, the spiking vector and the in-flow
+// move as 16-byte vectors, the compiled records as four 16-byte loads, and
+// the lane packs its four emissions into 4 x EB bits.  The in-flow of a
+// slot is at most (in-degree x largest p) <= INT32_MAX (checked when the
+// tiled layout is built), so it and C + in-flow are exact in 32 bits.
+
+// Split cluster barrier: arrive (release) and wait (acquire) apart, so a CTA
+// can announce that it started and later check that its partner did.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t a, const uint4& v) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
 // One SNP step in one launch (partitions P <= kTiledMaxCluster): the P CTAs
 // of a slice range form a thread-block cluster.  Each gathers its partition
-// into its shared accumulators; after a cluster barrier every CTA finishes
-// step kg and selects step kg+1 (SELECT) for its share of the range, reading
-// the in-flow of a slot as the sum of the P accumulators through distributed
-// shared memory; a second cluster barrier keeps every accumulator alive until
-// the other CTAs have read it.  Each warp loads the next slice's state while
-// it works on the current one.
+// into its shared accumulators; then every CTA finishes step kg and selects
+// step kg+1 (SELECT) for its share of the range, the in-flow of a slot being
+// the sum of the P accumulators.
+//  * Two partitions with room for it (tl.rin_words > 0): after its gather a
+//    CTA stores its accumulators of the partner's share into the partner's
+//    in-flow buffer through distributed shared memory, and one cluster
+//    barrier publishes them; the select phase then reads only its own
+//    shared memory, so no barrier follows it.  The CTA announces at its
+//    start that it runs (the buffer it writes into exists), and checks the
+//    partner's announcement before its remote stores.
+//  * Otherwise the select phase reads the other CTAs' accumulators through
+//    distributed shared memory between two cluster barriers.
 template <int EB, int LAYOUT, int SEL>
 __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, int32_t t, int select, int compact) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int32_t wb[kTiledMaxSub + 1];
     __shared__ __align__(8) unsigned long long bar;
+    __shared__ uint2 s_mod[16];    // constants of x / L for the compiled masks
+    __shared__ uint8_t s_pick[64];  // the idx-th applicable rule of a mask
+    fill_mod_table(s_mod);          // both published by the gather phase's barriers
+    fill_pick_table(s_pick);
+    const bool push = tl.rin_words > 0;  // two partitions, in-flow pushed to the partner (uniform)
+    if (push) cluster_arrive_relaxed();  // this CTA runs: its shared memory may be written
     uint32_t* Esm = smem;
     int* acc = reinterpret_cast<int*>(smem + tl.part_words + 4);
+    int* rin = acc + tl.acc_words;       // the partner's in-flow of this CTA's share (push)
     const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
     const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
     const int32_t share = (hi - lo + tl.P - 1) / tl.P;
@@ -500,11 +569,28 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
     }
     unsigned long long kg;
     const int ph = tiled_gather_phase<EB, LAYOUT>(s, tl, t, Esm, acc, wb, &bar, kg);
-    if (ph == kPhaseBlocked) return;  // every CTA of the cluster returns here, before any cluster barrier
+    if (ph == kPhaseBlocked) {  // the same answer in every CTA of the cluster
+        if (push) cluster_wait();  // complete the start barrier's phase before leaving
+        return;
+    }
+    const uint32_t acc0 = smem_u32(acc);
+    const uint32_t me = cluster_rank();
+    if (push) {
+        cluster_wait();  // the partner runs
+        if (ph == kPhaseOk) {
+            // this CTA's accumulators of the partner's share, into its buffer
+            const int hp = h ^ 1;
+            const int32_t p_lo = min(hi, lo + hp * share), p_hi = min(hi, lo + (hp + 1) * share);
+            const uint32_t rbase = cluster_map(smem_u32(rin), me ^ 1u);
+            const int32_t n4 = (p_hi - p_lo) * (kSlice / 4);
+            const int32_t a0 = (p_lo - lo) * kSlice;
+            for (int32_t i = threadIdx.x; i < n4; i += blockDim.x)
+                st_cluster_v4(rbase + (uint32_t)i * 16u, *reinterpret_cast<const uint4*>(acc + a0 + 4 * i));
+        }
+    }
     cluster_sync();
     const unsigned long long ks = kg + 1ull;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t acc0 = smem_u32(acc);
     const bool has_rec = s.rec != nullptr;
     bool active = false;
     if (ph == kPhaseOk) {
@@ -517,49 +603,110 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
         }
         int32_t* const Sk = SNP_PICK(s.S, ks);
         uint32_t* const Ek = SNP_PICK(tl.Eg, ks);
-        // the partner's accumulators when the cluster has two CTAs (the
-        // common case), mapped once
-        const uint32_t me = cluster_rank();
-        const uint32_t pbase = tl.P == 2 ? cluster_map(acc0, me ^ 1u) : 0u;
-        struct Stage {
-            int32_t c;
-            uint32_t st;
-            long long in;
-            uint4 rec;
-        };
-        // the state and the in-flow (summed over the cluster) of slice slc
-        auto load = [&](int32_t slc, Stage& g) {
-            const int32_t slot = slc * kSlice + lane;
-            if (slc < my_hi && slot < s.q) {
-                g.c = s.C[slot];
-                g.st = s.st[slot];
-                if (select && has_rec) g.rec = __ldg(reinterpret_cast<const uint4*>(s.rec) + slot);
-                const int32_t li = (slc - lo) * kSlice + lane;
-                g.in = acc[li];
-                if (tl.P == 2) {
-                    g.in += (int32_t)ld_cluster_u32(pbase + (uint32_t)li * 4u);
+        // the partner's accumulators when they are read remotely (two CTAs
+        // without the buffer), mapped once
+        const uint32_t pbase = (!push && tl.P == 2) ? cluster_map(acc0, me ^ 1u) : 0u;
+        const int32_t share_end = my_hi * kSlice;   // this CTA's share: slots [my_lo * 32, share_end)
+        const int32_t qend = min(share_end, s.q);
+        const PhiloxHead phx = philox_head(ks, s.philox_rk);
+        // a warp takes 128 slots at a time, lane l slots 4l .. 4l+3 (one
+        // 32-slot slice never straddles the share's bounds)
+        for (int32_t base = my_lo * kSlice + warp * 128; base < share_end; base += nw * 128) {
+            const int32_t slot0 = base + 4 * lane;
+            const bool mine = slot0 < share_end;
+            const bool live = slot0 < qend;
+            int4 c4 = make_int4(0, 0, 0, 0);
+            uint4 st4 = make_uint4(0u, 0u, 0u, 0u), in4 = st4;
+            const uint4* rp = reinterpret_cast<const uint4*>(s.rec) + slot0;
+            if (live) {
+                c4 = *reinterpret_cast<const int4*>(s.C + slot0);
+                st4 = *reinterpret_cast<const uint4*>(s.st + slot0);
+                const int32_t li = slot0 - lo * kSlice;
+                in4 = *reinterpret_cast<const uint4*>(acc + li);
+                uint4 pv = make_uint4(0u, 0u, 0u, 0u);
+                if (push) {
+                    pv = *reinterpret_cast<const uint4*>(rin + (slot0 - my_lo * kSlice));
+                } else if (tl.P == 2) {
+                    pv = ld_cluster_v4(pbase + (uint32_t)li * 4u);
                 } else {
-                    for (int r = 0; r < tl.P; ++r)
-                        if ((uint32_t)r != me)
-                            g.in += (int32_t)ld_cluster_u32(cluster_map(acc0 + (uint32_t)li * 4u, (uint32_t)r));
+                    for (int r = 0; r < tl.P; ++r) {
+                        if ((uint32_t)r == me) continue;
+                        const uint4 rv = ld_cluster_v4(cluster_map(acc0 + (uint32_t)li * 4u, (uint32_t)r));
+                        pv.x += rv.x;
+                        pv.y += rv.y;
+                        pv.z += rv.z;
+                        pv.w += rv.w;
+                    }
+                }
+                in4.x += pv.x;
+                in4.y += pv.y;
+                in4.z += pv.z;
+                in4.w += pv.w;
+            }
+            unsigned long long packed = 0ull;
+            int4 s4 = make_int4(-1, -1, -1, -1);
+            bool dirty = false, ovf = false;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int32_t slot = slot0 + j;
+                const bool v = slot < qend;
+                int32_t c = (&c4.x)[j];
+                const uint32_t st = (&st4.x)[j];
+                // an open neuron receives; a count above INT32_MAX is clamped
+                // and reported
+                const uint32_t nc = (uint32_t)c + (&in4.x)[j];
+                const bool open = v && (st >> kPendShift) == 0u;
+                ovf |= open && nc > 2147483647u;
+                c = open ? (int32_t)min(nc, 2147483647u) : c;
+                if (select && v) {
+                    const uint32_t nid = neuron_id(s, slot);
+                    SelOut o;
+                    if (has_rec)
+                        o = select_rec_flat<SEL>(__ldg(rp + j), c, st, nid, phx, s.philox_rk, s_mod, s_pick);
+                    else if (compact)
+                        o = select_neuron<true, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks, nid,
+                                                     s.seed);
+                    else
+                        o = select_neuron<false, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks, nid,
+                                                      s.seed);
+                    c = o.c_after;
+                    active |= o.active;
+                    packed |= (unsigned long long)(uint32_t)o.emit << (EB * j);
+                    (&s4.x)[j] = o.s;
+                    dirty |= o.st != st;
+                    (&st4.x)[j] = o.st;
+                }
+                (&c4.x)[j] = c;
+            }
+            if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(s.flags + kFlagOverflow, 1u);
+            if (live) {
+                *reinterpret_cast<int4*>(s.C + slot0) = c4;
+                if (select) {
+                    *reinterpret_cast<int4*>(Sk + slot0) = s4;
+                    if (dirty) *reinterpret_cast<uint4*>(s.st + slot0) = st4;  // most quads stay open
                 }
             }
-        };
-        Stage a = {0, 0u, 0, make_uint4(0u, 0u, 0u, 0u)}, b = a;
-        int32_t sl = my_lo + warp;
-        load(sl, a);
-        for (; sl < my_hi; sl += 2 * nw) {  // two stages, alternating roles
-            load(sl + nw, b);
-            finish_select_slice<SEL, EB>(s, select != 0, compact != 0, Sk, Ek, sl, lane, a.c, a.st, a.rec, a.in, ks,
-                                         active);
-            if (sl + nw >= my_hi) break;
-            load(sl + 2 * nw, a);
-            finish_select_slice<SEL, EB>(s, select != 0, compact != 0, Sk, Ek, sl + nw, lane, b.c, b.st, b.rec, b.in,
-                                         ks, active);
+            if (select) {  // the lane's 4 x EB bits into the packed E_{k+1}
+                if constexpr (EB == 2) {
+                    uint32_t w = (uint32_t)packed << (8u * (uint32_t)(lane & 3));
+                    w |= __shfl_xor_sync(0xffffffffu, w, 1);
+                    w |= __shfl_xor_sync(0xffffffffu, w, 2);
+                    if (mine && (lane & 3) == 0) Ek[slot0 >> 4] = w;
+                } else if constexpr (EB == 4) {
+                    uint32_t w = (uint32_t)packed << (16u * (uint32_t)(lane & 1));
+                    w |= __shfl_xor_sync(0xffffffffu, w, 1);
+                    if (mine && (lane & 1) == 0) Ek[slot0 >> 3] = w;
+                } else if constexpr (EB == 8) {
+                    if (mine) Ek[slot0 >> 2] = (uint32_t)packed;
+                } else {
+                    if (mine) *reinterpret_cast<uint2*>(Ek + (slot0 >> 1)) =
+                                  make_uint2((uint32_t)packed, (uint32_t)(packed >> 32));
+                }
+            }
         }
     }
     if (select) raise_step_activity(s.flags, ks, active);
-    cluster_sync();
+    if (!push) cluster_sync();  // the other CTAs read this CTA's accumulators until here
 }
 
 // Finishes step kg (GATHER: adds the in-flow to open neurons) and selects

@@ -116,6 +116,43 @@ void pack_in_lists(const snp_desc* d, HostPack* hp) {
     }
 }
 
+// Rules given as unions that the compiled records cannot hold are stepped
+// through the general (4-word) rule table.  A union rule's record keeps c
+// and (p, d) in words 2 and 3 as any rule does; word 0 holds 0x80000000 |
+// the index of its first term record and word 1 the number of terms.  The
+// term records, two words (k, j) each, follow the 4m rule words in the same
+// buffer, in slot order of their rules, so the index in word 0 counts
+// 8-byte records from the start of the buffer (the first one is 2m).
+static int pack_union_rules(const snp_desc* d, HostPack* hp) {
+    const int32_t q = hp->q;
+    const int64_t m = hp->m;
+    const int64_t T = d->rule_term_offsets[m];
+    if (2 * m + T >= ((int64_t)1 << 31))
+        return fail(SNP_ERR_UNSUPPORTED, "too many rules and union terms for the rule table");
+    hp->compact = false;
+    hp->rules.assign((size_t)(4 * m + 2 * T), 0u);
+    int64_t next = 2 * m;  // the next term record (8-byte units)
+    for (int32_t s = 0; s < q; ++s) {
+        const int32_t i = hp->perm[s];
+        const int64_t r0 = d->rule_offsets[i];
+        const int32_t R = hp->rule_off[s + 1] - hp->rule_off[s];
+        for (int32_t t = 0; t < R; ++t) {
+            const int64_t r = r0 + t, dst = hp->rule_off[s] + t;
+            const int64_t u0 = d->rule_term_offsets[r], u1 = d->rule_term_offsets[r + 1];
+            uint32_t* w = hp->rules.data() + dst * 4;
+            w[0] = 0x80000000u | (uint32_t)next;
+            w[1] = (uint32_t)(u1 - u0);
+            w[2] = (uint32_t)d->rule_c[r];
+            w[3] = (uint32_t)d->rule_p[r] | ((uint32_t)d->rule_d[r] << 16);
+            for (int64_t u = u0; u < u1; ++u, ++next) {
+                hp->rules[(size_t)next * 2] = (uint32_t)d->term_k[u];
+                hp->rules[(size_t)next * 2 + 1] = (uint32_t)d->term_j[u];
+            }
+        }
+    }
+    return SNP_OK;
+}
+
 int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int window, HostPack* hp) {
     const int32_t q = d->q;
     const int64_t m = d->rule_offsets[q];
@@ -243,7 +280,10 @@ int pack_system(const snp_desc* d, bool want_out_lists, bool want_in_lists, int 
         }
     }
 
-    compile_rules(d, hp);
+    if (!compile_rules(d, hp) && d->rule_term_offsets) {
+        const int st = pack_union_rules(d, hp);
+        if (st) return st;
+    }
 
     hp->C0.resize(q);
     for (int32_t s = 0; s < q; ++s) hp->C0[s] = d->init_spikes[hp->perm[s]];
@@ -421,7 +461,7 @@ int tiled_e_bits(int max_p) {
 }
 
 size_t tiled_smem_bytes(const TiledPack& tp) {
-    return (size_t)tp.part_words * 4 + 16 + (size_t)tp.acc_words * 4;
+    return (size_t)tp.part_words * 4 + 16 + (size_t)tp.acc_words * 4 + (size_t)tp.rin_words * 4;
 }
 
 static int bits_for(int64_t n) {  // bits to hold 0..n
@@ -516,6 +556,16 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     tp->max_slices = max_slices;
     tp->acc_words = acc_words;
     tp->src_bits = src_bits;
+    // With two partitions each CTA can receive the partner's in-flow for its
+    // share in a buffer of its own (the fused step then needs no barrier
+    // after its select phase) when that buffer fits beside the rest.
+    {
+        const int64_t share_words = ((int64_t)(max_slices + 1) / 2) * kSlice;
+        tp->rin_words = (P == 2 && (size_t)part_words * 4 + 16 + (size_t)acc_words * 4 + (size_t)share_words * 4 <=
+                                       smem_budget)
+                            ? (int)share_words
+                            : 0;
+    }
     tp->cta_lo = cta_lo;
     const int db = 32 - src_bits;
     // run-length layout when a source's bit index in the packed emissions
@@ -550,7 +600,10 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
         const uint32_t max_delta = (1u << rle_db) - 1u;
         const uint32_t rle_pad = (pad * (uint32_t)eb) << rle_db;  // the zero word, no advance
         std::vector<std::pair<uint32_t, uint32_t>> seq;  // (target local to the range, source local to the partition)
-        std::vector<std::vector<uint32_t>> runs(T);
+        std::vector<int64_t> bnd;                          // run t = seq[bnd[t] .. bnd[t+1])
+        std::vector<int64_t> gstart;                       // first entry of each target group
+        std::vector<std::vector<std::pair<uint32_t, int64_t>>> tmpl(T);  // per run: (advance, seq index or -1)
+        const uint32_t dummy = (uint32_t)max_slots;       // the accumulator no slot reads
         for (int g = 0; g < NR; ++g) {
             for (int h = 0; h < P; ++h) {
                 const int c = g * P + h;
@@ -565,35 +618,142 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
                     const uint32_t local = (uint32_t)(s - (int64_t)cta_lo[g] * kSlice);
                     for (int64_t x = x0; x < x1; ++x) seq.push_back({local, (uint32_t)(isrc[(size_t)x] - lo_src)});
                 }
-                // cut into T runs of nearly equal length and encode each
+                // Cut into T runs of nearly equal length at target boundaries:
+                // all in-edges of a target from this partition fall in one
+                // run, so the thread of that run owns the target's
+                // accumulator and writes it with a plain store.
                 const int64_t n_e = (int64_t)seq.size();
+                // target groups and what each costs in a run after another
+                // group (its entries plus the pad entries of a long gap)
+                gstart.clear();
+                for (int64_t x = 0; x < n_e; ++x)
+                    if (x == 0 || seq[x].first != seq[x - 1].first) gstart.push_back(x);
+                gstart.push_back(n_e);
+                const int64_t ng = (int64_t)gstart.size() - 1;
+                auto cost = [&](int64_t k, bool first) {
+                    const int64_t sz = gstart[k + 1] - gstart[k];
+                    if (first || k == 0) return sz;
+                    const int64_t d = (int64_t)seq[gstart[k]].first - (int64_t)seq[gstart[k - 1]].first;
+                    return sz + (d + max_delta - 1) / max_delta - 1;
+                };
+                // the smallest longest run: whole groups, at most T runs
+                auto fits = [&](int64_t cap, bool cut) {
+                    int64_t t = 0, len = 0;
+                    if (cut) bnd[0] = 0;
+                    for (int64_t k = 0; k < ng; ++k) {
+                        int64_t c_ = cost(k, len == 0);
+                        if (len > 0 && len + c_ > cap) {
+                            if (++t >= T) return false;
+                            if (cut) bnd[t] = gstart[k];
+                            len = 0;
+                            c_ = cost(k, true);
+                        }
+                        len += c_;
+                    }
+                    if (cut)
+                        for (int64_t r = t + 1; r <= T; ++r) bnd[r] = n_e;
+                    return true;
+                };
+                bnd.assign((size_t)T + 1, n_e);
+                int64_t lo_c = 1, hi_c = 1;
+                for (int64_t k = 0; k < ng; ++k) {
+                    lo_c = std::max(lo_c, cost(k, true));
+                    hi_c += cost(k, false);
+                }
+                lo_c = std::max(lo_c, (n_e + T - 1) / T);
+                while (lo_c < hi_c) {
+                    const int64_t mid = (lo_c + hi_c) / 2;
+                    if (fits(mid, false))
+                        hi_c = mid;
+                    else
+                        lo_c = mid + 1;
+                }
+                fits(lo_c, true);
+                // the positions of every run: the advance of each entry and the
+                // target group whose source goes there (-1: a pad entry)
                 size_t nvec = 0;
                 for (int64_t t = 0; t < T; ++t) {
-                    const int64_t a = n_e * t / T, b = n_e * (t + 1) / T;
-                    std::vector<uint32_t>& run = runs[t];
-                    run.clear();
-                    uint32_t cur = a < b ? seq[a].first : 0u;
+                    std::vector<std::pair<uint32_t, int64_t>>& pos = tmpl[t];
+                    pos.clear();
+                    const int64_t a0 = bnd[t], a1 = bnd[t + 1];
+                    uint32_t cur = a0 < a1 ? seq[a0].first : dummy;
                     tp->tstart[(size_t)c * T + t] = (int32_t)cur;
-                    for (int64_t x = a; x < b; ++x) {
+                    for (int64_t x = a0; x < a1; ++x) {
                         uint32_t d = seq[x].first - cur;
                         while (d > max_delta) {  // a long gap: advance with pad entries
-                            run.push_back(rle_pad | max_delta);
+                            pos.push_back({max_delta, -1});
                             d -= max_delta;
                         }
-                        run.push_back(((seq[x].second * (uint32_t)eb) << rle_db) | d);
+                        pos.push_back({d, x});
                         cur = seq[x].first;
                     }
-                    while (run.size() % 5) run.push_back(rle_pad);  // zero delta, zero emission
-                    nvec = std::max(nvec, run.size() / 5);
+                    while (pos.size() % 5) pos.push_back({0u, -1});  // zero delta, zero emission
+                    nvec = std::max(nvec, pos.size() / 5);
+                }
+                // Sources within a target's group may go in any order (the sum
+                // does not depend on it).  The lanes of a warp read position u
+                // of their runs in the same shared-memory load, so each
+                // position takes, lane by lane, the group's remaining source
+                // whose bank the warp's other lanes use least there (a word
+                // already read at that position costs nothing: broadcast).
+                std::vector<int32_t> srcs(seq.size());
+                for (size_t x = 0; x < seq.size(); ++x) srcs[x] = (int32_t)seq[x].second;
+                const size_t npos = nvec * 5;
+                for (int64_t t = 0; t < T; ++t) tmpl[t].resize(npos, {0u, -1});
+                const uint32_t pad_word = (pad * (uint32_t)eb) >> 5;
+                for (int64_t w0 = 0; w0 < T; w0 += 32) {
+                    for (size_t p = 0; p < npos; ++p) {
+                        int bank_n[32] = {0};
+                        uint32_t words[32];
+                        int nwords = 0;
+                        auto take = [&](uint32_t word) {
+                            for (int i = 0; i < nwords; ++i)
+                                if (words[i] == word) return;
+                            words[nwords++] = word;
+                            ++bank_n[word & 31u];
+                        };
+                        // forced lanes first (a pad, or one source left in the group)
+                        for (int pass = 0; pass < 2; ++pass) {
+                            for (int64_t t = w0; t < std::min<int64_t>(T, w0 + 32); ++t) {
+                                const int64_t x = tmpl[t][p].second;
+                                if (x < 0) {
+                                    if (pass == 0) take(pad_word);
+                                    continue;
+                                }
+                                // remaining sources of this group: srcs[x .. group end)
+                                int64_t e = x + 1;
+                                while (e < bnd[t + 1] && seq[e].first == seq[x].first) ++e;
+                                if ((pass == 0) != (e - x == 1)) continue;
+                                int64_t best = x;
+                                int best_cost = 1 << 30;
+                                for (int64_t y = x; y < e; ++y) {
+                                    const uint32_t word = ((uint32_t)srcs[y] * (uint32_t)eb) >> 5;
+                                    int cost = bank_n[word & 31u];
+                                    for (int i = 0; i < nwords; ++i)
+                                        if (words[i] == word) cost = 0;
+                                    if (cost < best_cost) {
+                                        best_cost = cost;
+                                        best = y;
+                                    }
+                                }
+                                std::swap(srcs[x], srcs[best]);
+                                take(((uint32_t)srcs[x] * (uint32_t)eb) >> 5);
+                            }
+                        }
+                    }
                 }
                 const size_t base = tp->ent.size() / 4;
                 sb[0] = (int32_t)(base * 4);
                 tp->ent.resize((base + nvec * T) * 4, 0u);
                 for (int64_t t = 0; t < T; ++t) {
-                    std::vector<uint32_t>& run = runs[t];
-                    while (run.size() < nvec * 5) run.push_back(rle_pad);  // every thread the same count
+                    const std::vector<std::pair<uint32_t, int64_t>>& pos = tmpl[t];
                     for (size_t u = 0; u < nvec; ++u) {
-                        const uint32_t* e = run.data() + u * 5;
+                        uint32_t e[5];
+                        for (int i = 0; i < 5; ++i) {
+                            const auto& ps = pos[u * 5 + (size_t)i];
+                            e[i] = (ps.second < 0 ? rle_pad : (((uint32_t)srcs[ps.second] * (uint32_t)eb) << rle_db)) |
+                                   ps.first;
+                        }
                         uint32_t* w = tp->ent.data() + (base + u * T + (size_t)t) * 4;
                         w[0] = e[0] | (e[1] << 24);
                         w[1] = (e[1] >> 8) | (e[2] << 16);
@@ -609,6 +769,9 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
         // layout only when it is clearly smaller
         if ((double)tp->ent.size() <= 0.9 * other_words) {
             tp->pairs = 0;
+            // slack: the gather loads two vectors ahead of the one it adds,
+            // so the last CTA's threads read up to two rows past its block
+            tp->ent.resize(tp->ent.size() + (size_t)2 * T * 4, rle_pad);
             return SNP_OK;
         }
         tp->rle = 0;

@@ -90,7 +90,7 @@ struct HostPack {
     std::vector<int32_t> perm;        // slot -> neuron
     std::vector<int32_t> inv;         // neuron -> slot
     std::vector<int32_t> rule_off;    // [q+1] slot order
-    std::vector<uint32_t> rules;      // compact: m words; general: 4m words
+    std::vector<uint32_t> rules;      // compact: m words; general: 4m words (+ 2 per union term)
     std::vector<int32_t> rule_base;   // [q] caller's id of the slot's first rule
     std::vector<int32_t> slice_ptr;   // [nslices+1]
     std::vector<int32_t> in_idx;
@@ -181,6 +181,7 @@ struct TiledPack {
     int src_bits = 0;        // low bits of an entry holding the source (0..part_size)
     int pairs = 0;           // 1: paired layout (every aligned word pair has one target)
     int rle = 0;             // 1: run-length layout (24-bit entries, see below)
+    int rin_words = 0;       // > 0 (two partitions): words of the partner's in-flow buffer in shared memory
     std::vector<int32_t> tstart;  // run-length layout: [G][kTiledThreads] first target of each thread's run
     std::vector<int32_t> sub;     // [G][kTiledMaxSub+1] window starts in ent (CTA g*P+h: range g, partition h)
     std::vector<uint32_t> ent;    // entries

@@ -128,9 +128,10 @@ def test_rejects_malformed_systems():
 
 
 def test_union_descriptions_are_checked():
-    """Union expressions: malformed term arrays are SNP_ERR_INVALID; unions
-    the compiled applicability table cannot hold are SNP_ERR_UNSUPPORTED
-    (both refused on the host, before any device work)."""
+    """Union expressions: malformed term arrays are SNP_ERR_INVALID, refused
+    on the host before any device work.  Unions the compiled applicability
+    table cannot hold (K + L > 14, more than 4 rules) are packed as union
+    records of the general rule table: 4 words per rule plus 2 per term."""
     import dataclasses
     base = synth.random_system(40, 9, outdeg=(1, 5), rules=(2, 3))
     u = synth.with_unions(base, 3)
@@ -141,13 +142,18 @@ def test_union_descriptions_are_checked():
     _bad(dataclasses.replace(u, rule_term_offsets=None))             # terms without offsets
     for tk_big, tj_big in ((20, 0), (2, 13)):                        # K + L > 14 (K >= 2)
         tk = u.term_k.copy(); tj = u.term_j.copy(); tk[0] = tk_big; tj[0] = tj_big
-        with pytest.raises(libsnp.SnpError) as ei:
-            libsnp.System(dataclasses.replace(u, term_k=tk, term_j=tj))
-        assert ei.value.status == libsnp.SNP_ERR_UNSUPPORTED
+        g = libsnp.System(dataclasses.replace(u, term_k=tk, term_j=tj), deferred=True)
+        inf = g.info()
+        assert inf.compiled_rules == 0 and inf.compact_rules == 0
+        assert inf.rule_words == 4 * u.m + 2 * int(u.rule_term_offsets[-1])
+        g.close()
     five = synth.with_unions(synth.random_system(40, 9, outdeg=(1, 5), rules=(5, 5)), 3)   # 5 rules per neuron
-    with pytest.raises(libsnp.SnpError) as ei:
-        libsnp.System(five)
-    assert ei.value.status == libsnp.SNP_ERR_UNSUPPORTED
+    g = libsnp.System(five, deferred=True)
+    assert g.info().compiled_rules == 0 and g.info().rule_words == 4 * five.m + 2 * int(five.rule_term_offsets[-1])
+    g.close()
+    small = libsnp.System(u, deferred=True)                          # fits the record: compiled
+    assert small.info().compiled_rules == 1
+    small.close()
 
 
 def test_strerror_names_every_status():

@@ -3,6 +3,7 @@ against the oracle: every form and engine, both selections, forced choices,
 branch steps and batches.  rule_k/rule_j hold decoys that would make no rule
 applicable, so a kernel that read the plain (k, j) instead of the union
 would differ at once."""
+import dataclasses
 import itertools
 
 import numpy as np
@@ -33,9 +34,9 @@ def union_system(q, seed, rules=(2, 4), terms=(1, 3), outdeg=(1, 8)):
     return synth.with_unions(base, seed + 1, terms=terms)
 
 
-def compare(desc, nsteps, mode, seed, chunks=(1, 3, 7), **kw):
+def compare(desc, nsteps, mode, seed, chunks=(1, 3, 7), compiled=1, **kw):
     gs = libsnp.System(desc, select=SEL[mode], seed=seed, **kw)
-    assert gs.info().compiled_rules == 1
+    assert gs.info().compiled_rules == compiled
     st = oracle.initial_state(desc)
     k, ci, last_S = 0, 0, np.full(desc.q, -1, np.int32)
     while k < nsteps:
@@ -156,6 +157,110 @@ def test_unions_in_a_batch():
         C, D, P, k = systems[i].get_state()
         assert done[i] == ex and k == ex
         assert (C == st[0]).all() and (D == st[1]).all() and (P == st[2]).all(), i
+    b.close()
+    for g in systems:
+        g.close()
+
+
+def beyond_record(kind, q, seed):
+    """Unions outside what a 16-byte compiled record holds, one limit each:
+    more than 4 rules; a neuron whose term periods have lcm 35; c >= 64;
+    p >= 32; d >= 32; periods and offsets of a few hundred (the divisibility
+    test's generic path)."""
+    rng = np.random.default_rng(seed)
+    if kind == "rules6":
+        return union_system(q, seed, rules=(5, 7))
+    if kind == "lcm35":
+        d = union_system(q, seed, rules=(2, 4), terms=(2, 3))
+        tj = np.asarray(d.term_j).copy()
+        tj[:] = np.where(np.arange(tj.size) % 2 == 0, 5, 7)       # every rule mixes j = 5 and j = 7
+        return dataclasses.replace(d, term_j=tj.astype(np.int32))
+    if kind == "c64":
+        base = synth.random_system(q, seed, outdeg=(1, 8), rules=(2, 4), k_range=(60, 90), d_range=(0, 3),
+                                   spikes=(40, 200))
+        return synth.with_unions(base, seed + 1, terms=(1, 3), k_max=90, j_max=6)
+    if kind == "p32":
+        base = synth.random_system(q, seed, outdeg=(1, 8), rules=(2, 4), p_range=(20, 60), d_range=(0, 3),
+                                   spikes=(0, 10))
+        return synth.with_unions(base, seed + 1, terms=(1, 3))
+    if kind == "d32":
+        base = synth.random_system(q, seed, outdeg=(1, 8), rules=(2, 4), d_range=(0, 45), spikes=(0, 10))
+        return synth.with_unions(base, seed + 1, terms=(1, 3))
+    if kind == "j300":
+        d = union_system(q, seed, rules=(2, 4), terms=(1, 3))
+        T = np.asarray(d.term_j).size
+        tj = rng.integers(1, 4, size=T).astype(np.int32)      # small periods keep rules applying
+        big = rng.random(T) < 0.5
+        tj[big] = rng.integers(250, 400, size=int(big.sum()))
+        tk = rng.integers(0, 6, size=T).astype(np.int32)
+        bk = rng.random(T) < 0.3
+        tk[bk] = rng.integers(200, 300, size=int(bk.sum()))
+        return dataclasses.replace(d, term_j=tj, term_k=tk,
+                                   init_spikes=rng.integers(0, 320, size=q).astype(np.int32))
+    raise ValueError(kind)
+
+
+LIMITS = ["rules6", "lcm35", "c64", "p32", "d32", "j300"]
+
+
+@pytest.mark.parametrize("kind", LIMITS)
+@pytest.mark.parametrize("engine", ["launch", "resident", "tiled", "auto"])
+def test_unions_beyond_the_record_every_engine(kind, engine):
+    """Unions no compiled record holds run through the rule table's union
+    records on every engine, element by element equal to the oracle."""
+    q = 3001
+    d = beyond_record(kind, q, 1200 + LIMITS.index(kind))
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        k, info = compare(d, 40, mode, 17, compiled=0, engine=ENGINES[engine])
+        assert k > 0
+        assert info.compact_rules == 0
+
+
+@pytest.mark.parametrize("kind", LIMITS)
+@pytest.mark.parametrize("form,prop", [("ell", "pull"), ("ell", "push"), ("dense", "pull"), ("opt", "push")])
+def test_unions_beyond_the_record_every_form(kind, form, prop):
+    forms = {"opt": libsnp.SNP_FORM_OPT, "ell": libsnp.SNP_FORM_ELL, "dense": libsnp.SNP_FORM_DENSE}
+    props = {"pull": libsnp.SNP_PROP_PULL, "push": libsnp.SNP_PROP_PUSH}
+    d = beyond_record(kind, 700, 1300 + LIMITS.index(kind))
+    for mode in (oracle.FIRST, oracle.PHILOX):
+        compare(d, 30, mode, 5, compiled=0, form=forms[form], prop=props[prop])
+
+
+@pytest.mark.parametrize("kind", ["rules6", "lcm35", "c64"])
+def test_unions_beyond_the_record_counts_branch_and_batch(kind):
+    d = beyond_record(kind, 2000, 1400 + LIMITS.index(kind))
+    gs = libsnp.System(d, select=libsnp.SNP_SELECT_FIRST)
+    assert gs.info().compiled_rules == 0
+    st = oracle.initial_state(d)
+    gs.step(3)
+    oracle.run(d, st, 3)
+    assert (gs.count_choices() == oracle.count_choices(d, st)).all()
+    states, s_ = [], oracle.initial_state(d)
+    for k in range(24):
+        oracle.run(d, s_, 1, oracle.PHILOX, 3, step0=k)
+        states.append(tuple(x.copy() for x in s_))
+    C = np.stack([x[0] for x in states]); D = np.stack([x[1] for x in states]); P = np.stack([x[2] for x in states])
+    rng = np.random.default_rng(2)
+    cnt0 = np.stack([oracle.count_choices(d, x) for x in states])
+    ch = (rng.integers(0, 1 << 30, size=cnt0.shape) % np.maximum(cnt0, 1)).astype(np.int32)
+    C1, D1, P1, ex, bad, cnt = gs.branch_step(C, D, P, ch)
+    for b, x in enumerate(states):
+        s2 = tuple(v.copy() for v in x)
+        if not oracle.is_halted(d, s2[0], s2[2]):
+            oracle.step(d, s2, 0, oracle.FORCED, forced=ch[b])
+        assert (C1[b] == s2[0]).all() and (D1[b] == s2[1]).all() and (P1[b] == s2[2]).all(), b
+        assert (cnt[b] == oracle.count_choices(d, s2)).all(), b
+    gs.close()
+    descs = [beyond_record(kind, int(qq), 1500 + i) for i, qq in enumerate([64, 900, 7000, 30000])]
+    systems = [libsnp.System(x, select=libsnp.SNP_SELECT_PHILOX, seed=i) for i, x in enumerate(descs)]
+    b = libsnp.Batch()
+    done = b.wait(b.submit(systems, [50] * len(systems)))
+    for i, x in enumerate(descs):
+        st = oracle.initial_state(x)
+        ex_, _ = oracle.run(x, st, 50, oracle.PHILOX, i)
+        Cg, Dg, Pg, kg = systems[i].get_state()
+        assert done[i] == ex_ and kg == ex_
+        assert (Cg == st[0]).all() and (Dg == st[1]).all() and (Pg == st[2]).all(), i
     b.close()
     for g in systems:
         g.close()
