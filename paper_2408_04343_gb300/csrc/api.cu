@@ -150,6 +150,8 @@ void build_plan(snp_system* s, std::vector<Piece>& plan) {
         tl.G = tp.G;
         tl.acc_words = tp.acc_words;
         tl.rin_words = tp.rin_words;
+        tl.acc8 = tp.acc8;
+        tl.rin_esm = tp.rin_esm;
         tl.src_bits = tp.src_bits;
         tl.pairs = tp.pairs;
         tl.rle = tp.rle;
@@ -481,14 +483,17 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
         // the other engines carry any in-flow to the overflow check)
         if ((int64_t)hp.max_in * (int64_t)hp.max_p > (int64_t)INT32_MAX)
             st = fail(SNP_ERR_UNSUPPORTED, "in-degree x p can exceed the tiled engine's 32-bit accumulators");
-        else
-            st = pack_tiled(desc, hp, sms, (size_t)optin - 2048, &im.tp);
+        else {
+            // clusters of P CTAs with about the largest shared memory per CTA
+            int cpw[kTiledMaxCluster + 1] = {0};
+            for (int P = 1; P <= kTiledMaxCluster; ++P) cpw[P] = tiled_clusters_per_wave(P, (size_t)optin - 2048);
+            st = pack_tiled(desc, hp, sms, (size_t)optin - 2048, &im.tp, cpw);
+        }
         // Under AUTO the tiled engine must pay for itself: every CTA copies a
         // whole emission partition into shared memory each step.  With one
         // wave of CTAs that copy overlaps the entry stream; with several
-        // waves (large, low-degree systems: many partitions) it can move more
-        // bytes than the gathers it replaces (2M-neuron Zipf(2.1) system:
-        // 60 MB of copies for 34 MB of entries, slower than the L2 gather).
+        // waves (large, low-degree systems with 32-bit accumulators: many
+        // partitions) it can move more bytes than the gathers it replaces.
         // Keep it when it is one wave or the copies stay under half the
         // entry stream.
         if (st == SNP_OK && o.engine == SNP_ENGINE_AUTO && im.tp.G > sms &&

@@ -57,7 +57,9 @@ cudaError_t launch_branch_step(const DevSys& s, const int32_t* rule_base, int e_
 // Tiled engine (kernels_tiled.cu): device view of a TiledPack.
 struct TiledSys {
     int32_t P, part_words, e_bits, G, acc_words, src_bits, pairs, rle;
-    int32_t rin_words;      // > 0: the partner's in-flow arrives in a shared buffer (see k_tiled_step)
+    int32_t rin_words;      // > 0: the partners' in-flows arrive in a shared buffer (see k_tiled_step)
+    int32_t acc8;           // 1: byte accumulators
+    int32_t rin_esm;        // 1: the partner buffer is the emissions' region (written after the gathers)
     const int32_t* tstart;  // run-length layout: first target of each thread's run, [G][kTiledThreads]
     const int32_t* sub;     // [G][kTiledMaxSub+1] window starts (words, multiples of 4); CTA g*P+h
     const uint32_t* ent;    // (dst_local << src_bits) | src_local
@@ -68,6 +70,8 @@ struct TiledSys {
 };
 cudaError_t launch_tiled(const DevSys& s, const TiledSys& tl, int kind, int32_t t, cudaStream_t st, bool compact,
                          int sel, size_t smem, int threads);
+// Clusters of P CTAs of the fused step the device runs at once (0 if unknown).
+int tiled_clusters_per_wave(int P, size_t smem);
 // One CTA waits at most `polls` polls on a barrier nothing completes; *out = 1
 // if the wait completed, 2 if it gave up.
 cudaError_t launch_wait_check(int polls, uint32_t* out, cudaStream_t st);

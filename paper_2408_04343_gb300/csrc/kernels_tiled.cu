@@ -163,6 +163,24 @@ __device__ __forceinline__ void st_shared_u32(uint32_t a, uint32_t v) {
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v));
 }
 
+// The same for byte accumulators (the in-flow of a target from one
+// partition is at most 255 there).
+__device__ __forceinline__ uint32_t run_flush8(uint32_t a, uint32_t run, uint32_t d) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u8 [%1], %3;\n\t"
+        "selp.u32 %0, 0, %3, p;\n\t}"
+        : "=r"(r)
+        : "r"(a), "r"(d), "r"(run));
+    return r;
+}
+
+__device__ __forceinline__ void st_shared_u8(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v));
+}
+
 // Run-length layout, one 16-byte load: five 24-bit entries b << db | d,
 // where b is the source's bit index in the packed emissions (source x EB)
 // and d the target advance.  Each entry first advances the thread's target
@@ -170,7 +188,7 @@ __device__ __forceinline__ void st_shared_u32(uint32_t a, uint32_t v) {
 // d > 0 -- then adds its emission to the run: word b / 32 of Esm, rotated
 // by b mod 32 (the funnel shift takes its count mod 32).  `cur` is the
 // shared address of the current target's accumulator.
-template <int EB>
+template <int EB, bool ACC8 = false>
 __device__ __forceinline__ void rle_vector(const uint32_t* __restrict__ Esm, const uint4& q, int db,
                                            uint32_t& cur, uint32_t& run) {
     constexpr uint32_t M = 0xFFFFFFu;
@@ -182,12 +200,17 @@ __device__ __forceinline__ void rle_vector(const uint32_t* __restrict__ Esm, con
         const uint32_t word = Esm[e[i] >> (db + 5)];
         const uint32_t v = __funnelshift_r(word, word, e[i] >> db) & ((1u << EB) - 1u);
         const uint32_t d = e[i] & dmask;
-        run = run_flush(cur, run, d) + v;
-        cur += d * 4u;
+        if constexpr (ACC8) {
+            run = run_flush8(cur, run, d) + v;
+            cur += d;
+        } else {
+            run = run_flush(cur, run, d) + v;
+            cur += d * 4u;
+        }
     }
 }
 
-enum : int { kLayoutRuns = 0, kLayoutPairs = 1, kLayoutRle = 2 };
+enum : int { kLayoutRuns = 0, kLayoutPairs = 1, kLayoutRle = 2, kLayoutRle8 = 3 };  // Rle8: byte accumulators
 
 // ---- bulk copy of a partition's emissions into shared memory -------------
 __device__ __forceinline__ void mbar_init(uint32_t bar) {
@@ -254,7 +277,7 @@ __device__ __forceinline__ void gather_batch(const uint4 (&x)[D], int32_t u0, in
                                              uint32_t acc0, int db, uint32_t wmask, int sbits, uint32_t& cur,
                                              uint32_t& run) {
     constexpr bool PAIRS = LAYOUT == kLayoutPairs;
-    if constexpr (LAYOUT == kLayoutRle) {  // no target windows: the target is carried in cur
+    if constexpr (LAYOUT == kLayoutRle || LAYOUT == kLayoutRle8) {  // no target windows: the target is carried in cur
 #pragma unroll
         for (int u = 0; u < D; ++u)
             if (u0 + u < nt) rle_vector<EB>(Esm, x[u], db, cur, run);
@@ -329,19 +352,21 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
     const int32_t s0 = base + tid * n - max(0, tid - r);          // sorted index of the first
     const uint4* col = reinterpret_cast<const uint4*>(tl.ent) + base + tid;
     uint4 qa[D], qb[D];
-    if constexpr (LAYOUT == kLayoutRle) {
+    constexpr bool RLE = LAYOUT == kLayoutRle || LAYOUT == kLayoutRle8;
+    constexpr bool ACC8 = LAYOUT == kLayoutRle8;
+    if constexpr (RLE) {
         qa[0] = ld_stream_v4(col);  // unguarded: see the gather loop below
         qa[1] = ld_stream_v4(col + kTiledThreads);
     } else {
         load_batch(qa, col, 0, nt);
     }
-    const int32_t tstart = LAYOUT == kLayoutRle ? __ldg(tl.tstart + (size_t)blockIdx.x * kTiledThreads + tid) : 0;
+    const int32_t tstart = RLE ? __ldg(tl.tstart + (size_t)blockIdx.x * kTiledThreads + tid) : 0;
     if (threadIdx.x < 4) Esm[tl.part_words + threadIdx.x] = 0u;
     if (threadIdx.x == 0) mbar_init(ebar);
     for (int j = threadIdx.x; j < tl.acc_words; j += blockDim.x) acc[j] = 0;
     const int sbits = tl.src_bits;
     // target bits of a 32-bit entry; for run-length entries, the advance's bits
-    const int db = LAYOUT == kLayoutRle ? 24 - sbits - __builtin_ctz((unsigned)EB) : 32 - sbits;
+    const int db = RLE ? 24 - sbits - __builtin_ctz((unsigned)EB) : 32 - sbits;
     constexpr uint32_t per = 32u / EB;
     const uint32_t wmask = ((1u << sbits) - 1u) >> __builtin_ctz(per);
     const uint32_t esm = smem_u32(Esm);
@@ -373,8 +398,8 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
         return kPhaseTimeout;
     }
     // paired and run-length layouts: the target being summed and its sum so far
-    uint32_t cur = acc0 + (LAYOUT == kLayoutRle ? (uint32_t)tstart * 4u : 0u), run = 0u;
-    if constexpr (LAYOUT == kLayoutRle) {
+    uint32_t cur = acc0 + (RLE ? (uint32_t)tstart * (ACC8 ? 1u : 4u) : 0u), run = 0u;
+    if constexpr (RLE) {
         // one vector per iteration, loads two vectors ahead; no per-vector
         // guard: the loads past a thread's last vector read the slack rows
         // at the end of the entry buffer (or another thread's vectors) and
@@ -384,9 +409,13 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
             const uint4 v = x0;
             x0 = x1;
             x1 = ld_stream_v4(col + (size_t)(u + 2) * kTiledThreads);
-            rle_vector<EB>(Esm, v, db, cur, run);
+            rle_vector<EB, ACC8>(Esm, v, db, cur, run);
         }
-        st_shared_u32(cur, run);  // the last target of the run (the dummy slot for an empty run)
+        // the last target of the run (the dummy slot for an empty run)
+        if constexpr (ACC8)
+            st_shared_u8(cur, run);
+        else
+            st_shared_u32(cur, run);
         __syncthreads();
         return kPhaseOk;
     }
@@ -529,13 +558,15 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t a, const uint4& v) {
 // into its shared accumulators; then every CTA finishes step kg and selects
 // step kg+1 (SELECT) for its share of the range, the in-flow of a slot being
 // the sum of the P accumulators.
-//  * Two partitions with room for it (tl.rin_words > 0): after its gather a
-//    CTA stores its accumulators of the partner's share into the partner's
-//    in-flow buffer through distributed shared memory, and one cluster
-//    barrier publishes them; the select phase then reads only its own
-//    shared memory, so no barrier follows it.  The CTA announces at its
-//    start that it runs (the buffer it writes into exists), and checks the
-//    partner's announcement before its remote stores.
+//  * With a partner buffer (tl.rin_words > 0): after its gather a CTA
+//    stores its accumulators of each partner's share into that partner's
+//    in-flow buffer through distributed shared memory -- byte accumulators:
+//    into the segment the partner keeps for this CTA; 32-bit accumulators
+//    (two partitions): the whole buffer -- and one cluster barrier publishes
+//    them; the select phase then reads only its own shared memory, so no
+//    barrier follows it.  A CTA announces at its start that it runs (the
+//    buffer it writes into exists), and checks the partners' announcements
+//    before its remote stores.
 //  * Otherwise the select phase reads the other CTAs' accumulators through
 //    distributed shared memory between two cluster barriers.
 template <int EB, int LAYOUT, int SEL>
@@ -547,11 +578,15 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
     __shared__ uint8_t s_pick[64];  // the idx-th applicable rule of a mask
     fill_mod_table(s_mod);          // both published by the gather phase's barriers
     fill_pick_table(s_pick);
-    const bool push = tl.rin_words > 0;  // two partitions, in-flow pushed to the partner (uniform)
-    if (push) cluster_arrive_relaxed();  // this CTA runs: its shared memory may be written
+    const bool push = tl.rin_words > 0;  // in-flows pushed to the share's owner (uniform)
+    // the partner buffer in the emissions' region: written only after every
+    // gather of the cluster is done; otherwise beside the accumulators,
+    // written as soon as the partners run
+    const bool early = push && !tl.rin_esm;
+    if (early) cluster_arrive_relaxed();  // this CTA runs: its shared memory may be written
     uint32_t* Esm = smem;
     int* acc = reinterpret_cast<int*>(smem + tl.part_words + 4);
-    int* rin = acc + tl.acc_words;       // the partner's in-flow of this CTA's share (push)
+    int* rin = tl.rin_esm ? reinterpret_cast<int*>(smem) : acc + tl.acc_words;  // the partners' in-flows (push)
     const int range = blockIdx.x / tl.P, h = blockIdx.x % tl.P;
     const int32_t lo = __ldg(tl.cta_lo + range), hi = __ldg(tl.cta_lo + range + 1);
     const int32_t share = (hi - lo + tl.P - 1) / tl.P;
@@ -570,12 +605,34 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
     unsigned long long kg;
     const int ph = tiled_gather_phase<EB, LAYOUT>(s, tl, t, Esm, acc, wb, &bar, kg);
     if (ph == kPhaseBlocked) {  // the same answer in every CTA of the cluster
-        if (push) cluster_wait();  // complete the start barrier's phase before leaving
+        if (early) cluster_wait();  // complete the start barrier's phase before leaving
         return;
     }
     const uint32_t acc0 = smem_u32(acc);
     const uint32_t me = cluster_rank();
-    if (push) {
+    constexpr bool ACC8 = LAYOUT == kLayoutRle8;
+    const int32_t seg_bytes = share * kSlice;  // byte accumulators: one sender's segment of a buffer
+    if (push && ACC8) {
+        if (early)
+            cluster_wait();  // the partners run
+        else
+            cluster_sync();  // every gather of the cluster is done: the emissions' regions are free
+        if (ph == kPhaseOk) {
+            // this CTA's byte accumulators of each partner's share, into this
+            // CTA's segment of that partner's buffer
+            const uint8_t* acc8 = reinterpret_cast<const uint8_t*>(acc);
+            for (int r = 0; r < tl.P; ++r) {
+                if (r == h) continue;
+                const int32_t p_lo = min(hi, lo + r * share), p_hi = min(hi, lo + (r + 1) * share);
+                const int seg = h < r ? h : h - 1;
+                const uint32_t rbase = cluster_map(smem_u32(rin), (uint32_t)r) + (uint32_t)(seg * seg_bytes);
+                const int32_t n16 = (p_hi - p_lo) * (kSlice / 16);
+                const int32_t a0 = (p_lo - lo) * kSlice;
+                for (int32_t i = threadIdx.x; i < n16; i += blockDim.x)
+                    st_cluster_v4(rbase + (uint32_t)i * 16u, *reinterpret_cast<const uint4*>(acc8 + a0 + 16 * i));
+            }
+        }
+    } else if (push) {
         cluster_wait();  // the partner runs
         if (ph == kPhaseOk) {
             // this CTA's accumulators of the partner's share, into its buffer
@@ -618,7 +675,23 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
             int4 c4 = make_int4(0, 0, 0, 0);
             uint4 st4 = make_uint4(0u, 0u, 0u, 0u), in4 = st4;
             const uint4* rp = reinterpret_cast<const uint4*>(s.rec) + slot0;
-            if (live) {
+            if (live && ACC8) {
+                c4 = *reinterpret_cast<const int4*>(s.C + slot0);
+                st4 = *reinterpret_cast<const uint4*>(s.st + slot0);
+                // four byte accumulators per word: even and odd bytes summed
+                // in 16-bit halves (at most 8 x 255 each)
+                const uint8_t* acc8 = reinterpret_cast<const uint8_t*>(acc);
+                const uint8_t* rin8 = reinterpret_cast<const uint8_t*>(rin);
+                const uint32_t ow = *reinterpret_cast<const uint32_t*>(acc8 + (slot0 - lo * kSlice));
+                uint32_t ev = ow & 0x00FF00FFu, od = (ow >> 8) & 0x00FF00FFu;
+                for (int r = 0; r + 1 < tl.P; ++r) {
+                    const uint32_t w =
+                        *reinterpret_cast<const uint32_t*>(rin8 + r * seg_bytes + (slot0 - my_lo * kSlice));
+                    ev += w & 0x00FF00FFu;
+                    od += (w >> 8) & 0x00FF00FFu;
+                }
+                in4 = make_uint4(ev & 0xFFFFu, od & 0xFFFFu, ev >> 16, od >> 16);
+            } else if (live) {
                 c4 = *reinterpret_cast<const int4*>(s.C + slot0);
                 st4 = *reinterpret_cast<const uint4*>(s.st + slot0);
                 const int32_t li = slot0 - lo * kSlice;
@@ -848,7 +921,7 @@ static cudaError_t launch_select_t(const DevSys& s, const TiledSys& tl, int32_t 
 template <int EB, int SEL>
 static cudaError_t launch_step_eb(const DevSys& s, const TiledSys& tl, int32_t t, cudaStream_t st, size_t smem,
                                   bool select, bool compact) {
-    auto fn = tl.rle ? k_tiled_step<EB, kLayoutRle, SEL>
+    auto fn = tl.rle ? (tl.acc8 ? k_tiled_step<EB, kLayoutRle8, SEL> : k_tiled_step<EB, kLayoutRle, SEL>)
                      : (tl.pairs ? k_tiled_step<EB, kLayoutPairs, SEL> : k_tiled_step<EB, kLayoutRuns, SEL>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -895,6 +968,34 @@ static cudaError_t launch_tiled_eb(const DevSys& s, const TiledSys& tl, int kind
         default: return cudaErrorInvalidValue;
     }
 #undef SNP_TILED_SEL
+}
+
+// How many thread-block clusters of P CTAs (1,024 threads, smem bytes of
+// dynamic shared memory each) the device runs at once: clusters must fit
+// inside one GPC, so this can be below the SM count / P.  0 on failure.
+int tiled_clusters_per_wave(int P, size_t smem) {
+    auto fn = k_tiled_step<2, kLayoutRle8, SNP_SELECT_PHILOX>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)P);
+    cfg.blockDim = dim3((unsigned)kTiledThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)P;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (const void*)fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 cudaError_t launch_tiled(const DevSys& s, const TiledSys& tl, int kind, int32_t t, cudaStream_t st, bool compact,

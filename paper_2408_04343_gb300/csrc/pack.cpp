@@ -461,7 +461,7 @@ int tiled_e_bits(int max_p) {
 }
 
 size_t tiled_smem_bytes(const TiledPack& tp) {
-    return (size_t)tp.part_words * 4 + 16 + (size_t)tp.acc_words * 4 + (size_t)tp.rin_words * 4;
+    return (size_t)tp.part_words * 4 + 16 + (size_t)tp.acc_words * 4 + (tp.rin_esm ? 0 : (size_t)tp.rin_words * 4);
 }
 
 static int bits_for(int64_t n) {  // bits to hold 0..n
@@ -470,7 +470,8 @@ static int bits_for(int64_t n) {  // bits to hold 0..n
     return b;
 }
 
-int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget, TiledPack* tp) {
+int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget, TiledPack* tp,
+               const int* cpw) {
     const int32_t q = hp.q;
     const int32_t nslices = (q + kSlice - 1) / kSlice;
     const int eb = tiled_e_bits(hp.max_p);
@@ -514,24 +515,51 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     std::vector<int32_t> cta_lo;
     int P = 0, NR = 0, part_size = 0, part_words = 0, src_bits = 0, acc_words = 0, max_slices = 0;
     int64_t max_slots = 0;
-    // one CTA per SM first; more CTAs (several waves) when the accumulators of
-    // fewer, larger ranges would not fit next to a partition's emissions
-    for (int p = 1, gm = 1; gm <= 8 && P == 0; p = (p == 64 ? (++gm, 1) : p + 1)) {
-        const int nr = std::max(1, std::min(nslices, G * gm / p));
+    bool acc8 = false, rin_esm = false;
+    int rin_words = 0;
+    // Byte accumulators when every target's in-flow from one partition fits
+    // a byte (in-degree x largest p <= 255): a range then holds four times the
+    // targets of 32-bit accumulators, and the partitions of a range exchange
+    // their in-flows through per-sender byte buffers (rin); they need the
+    // run-length entries (a bit index of at most 21 bits) and one cluster per
+    // range.  Otherwise 32-bit accumulators.  Either way: one CTA per SM
+    // first, more CTAs (several waves) when the accumulators of fewer, larger
+    // ranges would not fit next to a partition's emissions.
+    const bool acc8_ok = (int64_t)hp.max_in * (int64_t)std::max(1, hp.max_p) <= 255;
+    // One configuration: p partitions, gm waves.  Returns the CTAs of one
+    // wave it would use (0: it does not fit); with commit, takes it.
+    auto try_cfg = [&](int p, int gm, bool a8, bool commit) -> int {
+        // ranges of one wave: the clusters of p CTAs the device holds at once
+        const int per_wave = (cpw && p <= kTiledMaxCluster && cpw[p] > 0) ? std::min(cpw[p], G / p) : G / p;
+        const int nr = std::max(1, std::min(nslices, std::max(1, per_wave) * gm));
         std::vector<int32_t> lo;
         split(nr, lo);
         int32_t ms = 0;
         for (int g = 0; g < nr; ++g) ms = std::max(ms, lo[g + 1] - lo[g]);
         const int64_t slots = (int64_t)ms * kSlice;  // local slot `slots` is the dummy
-        const int aw = (int)((slots + 1 + 3) / 4 * 4);
+        const int aw = a8 ? (int)(((slots + 1 + 3) / 4 + 3) / 4 * 4) : (int)((slots + 1 + 3) / 4 * 4);
         int64_t ps = ((int64_t)q + p - 1) / p;
         ps = (ps + 511) / 512 * 512;
         const int64_t words = ps * eb / 32;
-        const size_t need = (size_t)words * 4 + (size_t)aw * 4;
         const int sb = bits_for(ps);  // sources 0..part_size; part_size reads a zero word
-        const int db = 32 - sb;
-        const int64_t nsub = (slots + ((int64_t)1 << db) - 1) >> db;
-        if (need + 16 <= smem_budget && db >= 5 && nsub <= kTiledMaxSub) {
+        // the partner buffers: (P - 1) senders x the largest share
+        const int64_t share_slots = (int64_t)((ms + p - 1) / p) * kSlice;
+        const int64_t rw = a8 ? (p > 1 ? (int64_t)(p - 1) * share_slots / 4 : 0) : (p == 2 ? share_slots : 0);
+        const size_t need = (size_t)words * 4 + 16 + (size_t)aw * 4;
+        bool ok, in_esm = false;
+        if (a8) {
+            // the partner buffer beside the rest, or else in the emissions'
+            // region (free once the cluster's gathers are done)
+            in_esm = need + (size_t)rw * 4 > smem_budget && rw <= words + 4;
+            ok = (need + (size_t)(in_esm ? 0 : rw) * 4 <= smem_budget) && p <= kTiledMaxCluster &&
+                 sb + __builtin_ctz((unsigned)eb) <= 21;
+        } else {
+            const int db = 32 - sb;
+            const int64_t nsub = (slots + ((int64_t)1 << db) - 1) >> db;
+            ok = need <= smem_budget && db >= 5 && nsub <= kTiledMaxSub;
+        }
+        if (!ok) return 0;
+        if (commit) {
             P = p;
             G = G * gm;
             NR = nr;
@@ -542,9 +570,28 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
             acc_words = aw;
             max_slices = ms;
             max_slots = slots;
-            break;
+            acc8 = a8;
+            // 32-bit accumulators: the partner buffer only where it fits
+            rin_words = (a8 || need + (size_t)rw * 4 <= smem_budget) ? (int)rw : 0;
+            rin_esm = in_esm;
         }
+        return std::min(nr, std::max(1, per_wave)) * p;
+    };
+    if (acc8_ok) {
+        // one wave if any cluster size allows it: the one using the most SMs
+        int best = 0, best_ctas = 0;
+        for (int p = 1; p <= kTiledMaxCluster; ++p) {
+            const int c = try_cfg(p, 1, true, false);
+            if (c > best_ctas) {
+                best_ctas = c;
+                best = p;
+            }
+        }
+        if (best) try_cfg(best, 1, true, true);
     }
+    for (int pass = acc8_ok ? 0 : 1; pass < 2 && P == 0; ++pass)
+        for (int p = 1, gm = 1; gm <= 8 && P == 0; p = (p == 64 ? (++gm, 1) : p + 1))
+            try_cfg(p, gm, pass == 0, true);
     if (P == 0) return fail(SNP_ERR_UNSUPPORTED, "no source partitioning fits shared memory and 32-bit entries");
     G = NR * P;  // CTAs of the launch
 
@@ -556,16 +603,13 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     tp->max_slices = max_slices;
     tp->acc_words = acc_words;
     tp->src_bits = src_bits;
-    // With two partitions each CTA can receive the partner's in-flow for its
-    // share in a buffer of its own (the fused step then needs no barrier
-    // after its select phase) when that buffer fits beside the rest.
-    {
-        const int64_t share_words = ((int64_t)(max_slices + 1) / 2) * kSlice;
-        tp->rin_words = (P == 2 && (size_t)part_words * 4 + 16 + (size_t)acc_words * 4 + (size_t)share_words * 4 <=
-                                       smem_budget)
-                            ? (int)share_words
-                            : 0;
-    }
+    tp->acc8 = acc8 ? 1 : 0;
+    // The partitions' in-flows of a CTA's share arrive in a buffer of its
+    // own (the fused step then needs no barrier after its select phase):
+    // with byte accumulators always, (P - 1) byte segments, one per sender;
+    // with 32-bit accumulators for two partitions when it fits.
+    tp->rin_words = rin_words;
+    tp->rin_esm = rin_esm ? 1 : 0;
     tp->cta_lo = cta_lo;
     const int db = 32 - src_bits;
     // run-length layout when a source's bit index in the packed emissions
@@ -573,7 +617,7 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
     // advance; otherwise the paired layout unless too many (target,
     // partition) groups have an odd number of words
     const int rle_bits = src_bits + __builtin_ctz((unsigned)eb);  // bits of a bit index 0 .. part_size * eb
-    tp->rle = rle_bits <= 21 ? 1 : 0;
+    tp->rle = rle_bits <= 21 ? 1 : 0;  // always so with byte accumulators
     int64_t odd = 0;
     {
         for (int32_t s = 0; s < q; ++s) {
@@ -767,7 +811,7 @@ int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget,
         }
         // short runs spend most of their words on padding: keep the run-length
         // layout only when it is clearly smaller
-        if ((double)tp->ent.size() <= 0.9 * other_words) {
+        if (tp->acc8 || (double)tp->ent.size() <= 0.9 * other_words) {
             tp->pairs = 0;
             // slack: the gather loads two vectors ahead of the one it adds,
             // so the last CTA's threads read up to two rows past its block

@@ -181,7 +181,9 @@ struct TiledPack {
     int src_bits = 0;        // low bits of an entry holding the source (0..part_size)
     int pairs = 0;           // 1: paired layout (every aligned word pair has one target)
     int rle = 0;             // 1: run-length layout (24-bit entries, see below)
-    int rin_words = 0;       // > 0 (two partitions): words of the partner's in-flow buffer in shared memory
+    int rin_words = 0;       // > 0: words of the partners' in-flow buffer in shared memory
+    int acc8 = 0;            // 1: byte accumulators (run-length layout, P <= kTiledMaxCluster)
+    int rin_esm = 0;         // 1: the partner buffer occupies the emissions' region (after the gathers)
     std::vector<int32_t> tstart;  // run-length layout: [G][kTiledThreads] first target of each thread's run
     std::vector<int32_t> sub;     // [G][kTiledMaxSub+1] window starts in ent (CTA g*P+h: range g, partition h)
     std::vector<uint32_t> ent;    // entries
@@ -213,7 +215,10 @@ int pack_dense(const snp_desc* d, const HostPack& hp, std::vector<int32_t>* M);
 int tiled_e_bits(int max_p);
 // Builds the tiled layout; returns SNP_ERR_UNSUPPORTED when no partitioning
 // fits the shared-memory budget and the 32-bit entry encoding.
-int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget, TiledPack* out);
+// cpw[P] (P = 1 .. kTiledMaxCluster, may be NULL): clusters of P CTAs the
+// device runs at once; a wave has that many ranges (else G / P).
+int pack_tiled(const snp_desc* d, const HostPack& hp, int G, size_t smem_budget, TiledPack* out,
+               const int* cpw = nullptr);
 size_t tiled_smem_bytes(const TiledPack& tp);
 
 // Thread-local error text for snp_last_error().

@@ -151,14 +151,20 @@ def test_tiled_run_length_layout(p_max):
 
 
 def test_auto_engine_choice():
-    """AUTO: CTA-resident for small systems, tiled for one wave of tiled
-    CTAs, the L2 gather for large low-degree systems whose emission copies
-    would outweigh the entry stream; every choice matches the oracle."""
+    """AUTO: CTA-resident for small systems; tiled for one wave of tiled
+    clusters (the 2M-neuron Zipf system with byte accumulators in 4-CTA
+    clusters); the L2 gather for a large low-degree system whose in-flows
+    need 32-bit accumulators (p up to 100), where the tiled layout takes
+    several waves whose emission copies outweigh the entry stream; every
+    choice matches the oracle."""
     cases = [(synth.random_system(3000, 61, outdeg=(4, 16), rules=(3, 4), d_range=(0, 5), spikes=(0, 20)),
               libsnp.SNP_ENGINE_RESIDENT),
              (synth.random_system(200000, 62, outdeg=(8, 24), rules=(3, 4), d_range=(0, 5), spikes=(0, 20)),
               libsnp.SNP_ENGINE_TILED),
              (synth.random_system(1 << 21, 63, zipf=(2.1, 1, 4096), rules=(3, 3), d_range=(0, 3), spikes=(0, 20)),
+              libsnp.SNP_ENGINE_TILED),
+             (synth.random_system(1 << 21, 64, zipf=(2.1, 1, 4096), rules=(3, 3), p_range=(1, 100), d_range=(0, 3),
+                                  spikes=(0, 20)),
               libsnp.SNP_ENGINE_LAUNCH)]
     for d, want in cases:
         gs = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=3)
