@@ -235,8 +235,8 @@ def main():
                          "launch vs the plain per-system loop; serve: Poisson request loop; skewed: the "
                          "2M-neuron power-law system and its 16,384-neuron dense copy")
     ap.add_argument("--batch-count", type=int, default=8192)
-    ap.add_argument("--rates", default="10,100,1000,10000")
-    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rates", default="10,30,100,300,1000,3000,10000")
+    ap.add_argument("--requests", type=int, default=1000)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":

@@ -98,36 +98,30 @@ def batch(args, libsnp, synth):
                                             f"{t3 - t2:.2f} s"}}
 
 
-def _request_pool(synth, n, seed=5005):
-    rng = np.random.default_rng(seed)
-    qs = np.floor(np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=n))).astype(int)
-    rules = rng.integers(2, 5, size=n)
-    work = [(int(q), int(r), 77_000 + i) for i, (q, r) in enumerate(zip(qs, rules))]
-    import multiprocessing as mp
-    with mp.get_context("spawn").Pool(_threads()) as pool:
-        return pool.map(_request_system, work)
-
-
-def _request_system(w):
-    from paper_2408_04343_gb300 import synth
-    q, r, s = w
-    return synth.random_system(q, s, outdeg=(2, 32), rules=(r, r), d_range=(0, 5), spikes=(0, 20))
-
-
 def serve(args, libsnp, synth):
+    """The served form at each arrival rate, and the plain loop beside it.
+
+    Every request is its own system (synth.serving_requests: q log-uniform in
+    1e3..1e6, steps log-uniform in 10..1e4, its own seed); the same requests
+    are replayed at every rate, each rate on freshly created (deferred)
+    systems submitted at the request's Poisson arrival time to one batch
+    under a 150 GB budget.  Latency is arrival to completion (ticket polled
+    by the host).  The plain loop steps the same systems one after another,
+    each alone on the grid-wide L2-gather engine (one launch per step)."""
+    import torch
     rates = [float(x) for x in args.rates.split(",")]
     n = args.requests
-    pool = _request_pool(synth, min(n, 48))
-    rng = np.random.default_rng(606)
-    steps = np.floor(np.exp(rng.uniform(np.log(10), np.log(1e4), size=n))).astype(int)
-    seeds = rng.integers(1, 2**62, size=n)
+    base = synth.serving_requests(1.0, n, seed=5005)       # sizes, steps, seeds (arrivals rescaled per rate)
+    descs = synth.serving_systems(base, processes=_threads())
+    sel = libsnp.SNP_SELECT_PHILOX
     per_rate = []
     for lam in rates:
         with ThreadPoolExecutor(_threads()) as ex:
-            gs = list(ex.map(lambda i: libsnp.System(pool[i % len(pool)], select=libsnp.SNP_SELECT_PHILOX,
-                                                     seed=int(seeds[i]), deferred=True), range(n)))
+            gs = list(ex.map(lambda i: libsnp.System(descs[i], select=sel, seed=base[i].seed, deferred=True),
+                             range(n)))
         b = libsnp.Batch(mem_budget=150 << 30)
-        arr = np.cumsum(rng.exponential(1.0 / lam, size=n))
+        arr = np.array([r.arrival_s for r in base]) / lam     # Poisson at rate lam (same order of requests)
+        arr -= arr[0]
         tickets = [None] * n
         start = time.perf_counter()
 
@@ -136,7 +130,7 @@ def serve(args, libsnp, synth):
                 dt = start + arr[i] - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
-                tickets[i] = b.submit([gs[i]], [int(steps[i])])
+                tickets[i] = b.submit([gs[i]], [base[i].steps])
 
         th = threading.Thread(target=submitter)
         th.start()
@@ -147,25 +141,46 @@ def serve(args, libsnp, synth):
                 if tickets[i] is not None and b.poll(tickets[i]):
                     now = time.perf_counter()
                     lat[i] = now - (start + arr[i])
-                    done = b.steps_done(tickets[i], 0)
-                    work += pool[i % len(pool)].num_syn * done
+                    work += descs[i].num_syn * b.steps_done(tickets[i], 0)
                     gs[i].close()
                     left.discard(i)
                     last = now
             time.sleep(0.0005)
         th.join()
-        info = b.info()
+        inf = b.info()
         b.close()
         wall = last - start
         per_rate.append({"rate_per_s": lam, "requests": n, "p50_latency_s": float(np.percentile(lat, 50)),
                          "p99_latency_s": float(np.percentile(lat, 99)), "syn_updates_per_s": work / wall,
-                         "wall_s": wall, "rounds": int(info.rounds),
-                         "peak_device_gb": info.peak_resident_bytes / 1e9})
+                         "wall_s": wall, "arrivals_span_s": float(arr[-1]), "rounds": int(inf.rounds),
+                         "peak_device_gb": inf.peak_resident_bytes / 1e9,
+                         "time_split_s": {"admission_uploads": inf.admit_seconds,
+                                          "queue_grid_wide_steps": inf.launch_seconds,
+                                          "resident_launches_host": inf.resident_seconds,
+                                          "resident_launches_device": inf.resident_device_seconds,
+                                          "wait_grid_wide_after_resident": inf.large_tail_seconds,
+                                          "idle": inf.idle_seconds, "rounds_total": inf.round_seconds}})
+    # the plain loop: one system after another on the grid-wide engine
+    plain = [libsnp.System(descs[i], select=sel, seed=base[i].seed, engine=libsnp.SNP_ENGINE_LAUNCH)
+             for i in range(n)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, g in enumerate(plain):
+        g.step(base[i].steps, wait=False)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    pwork = sum(descs[i].num_syn * plain[i].get_state()[3] for i in range(n))
+    for g in plain:
+        g.close()
+    plain_v = pwork / (t1 - t0)
     best = max(r["syn_updates_per_s"] for r in per_rate)
     return {"metric": "synaptic updates/s", "workload": "serve", "value": best, "unit": "synaptic updates/s",
+            "plain_loop_value": plain_v, "served_vs_plain_loop": best / plain_v, "plain_loop_seconds": t1 - t0,
             "per_rate": per_rate,
-            "config": {"q": "log-uniform 1e3..1e6 (48 distinct systems reused)", "steps": "log-uniform 10..1e4",
-                       "budget_gb": 150, "requests_per_rate": n}}
+            "config": {"requests_per_rate": n, "distinct_systems": n,
+                       "neurons": int(sum(d.q for d in descs)), "synapses": int(sum(d.num_syn for d in descs)),
+                       "q": "log-uniform 1e3..1e6", "steps": "log-uniform 10..1e4", "out_degree": "U{2..32}",
+                       "budget_gb": 150}}
 
 
 def skewed(args, libsnp, synth):

@@ -91,7 +91,9 @@ extern "C" {
 #define SNP_ENGINE_TILED 3
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both
- * callbacks are called on the thread that calls into the library.        */
+ * callbacks are called on the thread that calls into the library, except
+ * for a system that a batch uploads at admission (SNP_FLAG_DEFER_UPLOAD):
+ * its alloc runs on the batch's upload thread.                            */
 typedef struct snp_allocator {
     void* (*alloc)(void* ctx, size_t bytes, void* stream); /* NULL = OOM */
     void (*release)(void* ctx, void* ptr, size_t bytes, void* stream);
@@ -277,7 +279,9 @@ int snp_branch_step(snp_system* sys, int32_t nb, const int32_t* C, const int32_t
 /* ---- batched and served forms ----------------------------------------- */
 /* A batch runs many independent systems in one persistent launch, each
  * system owned by one CTA for all its steps, systems taken largest first
- * from a device work counter.  mem_budget (bytes) bounds the device memory
+ * from a device work counter.  Admitted systems are uploaded by a thread of
+ * the batch while the systems already running keep stepping; they join the
+ * next round once uploaded.  mem_budget (bytes) bounds the device memory
  * of the systems the batch uploaded (created with SNP_FLAG_DEFER_UPLOAD)
  * and that are not yet destroyed; 0 = no bound.  The bound is hard: the
  * first waiting system is admitted only when it fits beside them.  A
@@ -304,7 +308,13 @@ int snp_batch_wait(snp_batch* b, int64_t ticket);
 /* Executed steps of system `index` of a completed ticket.                 */
 int snp_batch_steps_done(snp_batch* b, int64_t ticket, int32_t index, int64_t* steps_done);
 /* Counters of a batch: device bytes of the systems it holds now and at most
- * so far, rounds run, systems admitted / finished / waiting / running.    */
+ * so far, rounds run, systems admitted / finished / waiting / running, and
+ * where its worker's time went since creation (seconds, host clock unless
+ * noted): uploading admitted systems; queueing the grid-wide systems' steps
+ * of each round; the CTA-resident launches of each round from table upload
+ * to results (their device time by CUDA events beside it); waiting for the
+ * grid-wide systems after those launches; idle (nothing admissible and
+ * nothing running); whole rounds.                                         */
 typedef struct snp_batch_info {
     uint64_t budget_bytes;
     uint64_t resident_bytes;
@@ -314,6 +324,13 @@ typedef struct snp_batch_info {
     int64_t finished;
     int64_t waiting;
     int64_t running;
+    double admit_seconds;
+    double launch_seconds;
+    double resident_seconds;
+    double resident_device_seconds;
+    double large_tail_seconds;
+    double idle_seconds;
+    double round_seconds;
 } snp_batch_info;
 int snp_batch_get_info(snp_batch* b, snp_batch_info* info);
 

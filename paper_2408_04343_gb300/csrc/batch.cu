@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
@@ -127,8 +128,11 @@ struct snp_batch {
     int64_t rounds = 0, admitted = 0, finished = 0;
     int64_t next_id = 1;
     bool stop = false;
-    bool admitting = false;        // the worker is uploading a system outside the lock
+    bool admitting = false;        // the uploader is uploading a system outside the lock
+    size_t reserved = 0;           // device bytes of the system being uploaded (within the budget)
+    std::deque<snp::Item*> ready;  // uploaded, waiting for the next round
     std::thread worker;
+    std::thread uploader;
     // device tables of the resident launch, grown on demand
     snp::DevSys* d_sys = nullptr;
     long long* d_nsteps = nullptr;
@@ -140,6 +144,14 @@ struct snp_batch {
     int64_t round = snp::kRoundSteps;
     snp::Autotune tune;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // where the worker's time goes (seconds, host clock unless noted)
+    double t_admit = 0;        // uploading admitted systems
+    double t_launch = 0;       // queueing the grid-wide systems' steps of a round
+    double t_resident = 0;     // the resident launches of a round, tables to results
+    double t_resident_dev = 0; // the resident launches on the device (CUDA events)
+    double t_large_tail = 0;   // waiting for grid-wide systems after the resident launches
+    double t_idle = 0;         // no admissible system and nothing running
+    double t_round = 0;        // whole rounds
 };
 
 namespace snp {
@@ -178,7 +190,7 @@ static int ctas_per_sm(int threads, size_t smem) {
 // One persistent launch over systems that share kernel template parameters;
 // steps[i] each; exec_out receives the executed steps.
 static int run_resident_group(snp_batch* b, std::vector<snp_system*>& sys, std::vector<int64_t>& steps,
-                              std::vector<int64_t>& exec_out) {
+                              std::vector<int64_t>& exec_out, double& dev_seconds) {
     const size_t n = sys.size();
     exec_out.assign(n, 0);
     if (n == 0) return SNP_OK;
@@ -226,9 +238,12 @@ static int run_resident_group(snp_batch* b, std::vector<snp_system*>& sys, std::
             cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return fail(SNP_ERR_CUDA, std::string("batch sync: ") + cudaGetErrorString(cudaGetLastError()));
-    if (cand >= 0) {
+    {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) b->tune.record(key, cand, work, ms * 1e-3);
+        if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) {
+            dev_seconds += ms * 1e-3;
+            if (cand >= 0) b->tune.record(key, cand, work, ms * 1e-3);
+        }
     }
     bool overflow = false;
     for (size_t r = 0; r < n; ++r) {
@@ -245,8 +260,18 @@ static bool batch_resident(const snp_system* s) {
            s->opt.engine != SNP_ENGINE_TILED && s->q <= kBatchResidentMaxQ && resident_fits(s, nullptr);
 }
 
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Where one round's time went (added to the batch's counters under its lock).
+struct RoundTimes {
+    double launch = 0, resident = 0, resident_dev = 0, large_tail = 0, round = 0;
+};
+
 // Runs one round over `items`; on return each item's done/remaining/finished is updated.
-static int run_round(snp_batch* b, std::vector<Item*>& items) {
+static int run_round(snp_batch* b, std::vector<Item*>& items, RoundTimes& tm) {
+    const double t0 = now_s();
     std::map<std::pair<int, int>, std::vector<Item*>> groups;
     std::vector<Item*> large;
     for (Item* it : items) {
@@ -262,6 +287,7 @@ static int run_round(snp_batch* b, std::vector<Item*>& items) {
         large_n[i] = std::min(large[i]->remaining, b->round);
         rc = run_steps(large[i]->sys, large_n[i]);
     }
+    const double t1 = now_s();
     for (auto& g : groups) {
         if (rc) break;
         std::vector<snp_system*> sys;
@@ -270,7 +296,7 @@ static int run_round(snp_batch* b, std::vector<Item*>& items) {
             sys.push_back(it->sys);
             steps.push_back(std::min(it->remaining, b->round));
         }
-        rc = run_resident_group(b, sys, steps, ex);
+        rc = run_resident_group(b, sys, steps, ex, tm.resident_dev);
         if (!rc) {
             for (size_t r = 0; r < g.second.size(); ++r) {
                 Item* it = g.second[r];
@@ -280,6 +306,7 @@ static int run_round(snp_batch* b, std::vector<Item*>& items) {
             }
         }
     }
+    const double t2 = now_s();
     for (size_t i = 0; i < large.size(); ++i) {
         int64_t ex = 0;
         const int r2 = read_flags(large[i]->sys, &ex);
@@ -288,6 +315,11 @@ static int run_round(snp_batch* b, std::vector<Item*>& items) {
         large[i]->remaining -= large_n[i];
         if (ex < large_n[i] || large[i]->remaining <= 0) large[i]->finished = true;
     }
+    const double t3 = now_s();
+    tm.launch = t1 - t0;
+    tm.resident = t2 - t1;
+    tm.large_tail = t3 - t2;
+    tm.round = t3 - t0;
     return rc;
 }
 
@@ -313,79 +345,109 @@ static bool front_fits(const snp_batch* b) {
     if (b->pending.empty()) return false;
     const snp_system* s = b->pending.front()->sys;
     const size_t need = s->materialized ? 0 : s->planned_bytes;
-    return !b->budget || b->resident_bytes + need <= b->budget;
+    return !b->budget || b->resident_bytes + b->reserved + need <= b->budget;
 }
 
 // b->mu held.  Waiting systems that nothing but a destroy can admit: no
-// system runs or is being uploaded, and the first waiting one does not fit.
+// system runs, waits for a round or is being uploaded, and the first waiting
+// one does not fit.
 static bool stalled(const snp_batch* b) {
-    return !b->admitting && b->active.empty() && !b->pending.empty() && !front_fits(b);
+    return !b->admitting && b->active.empty() && b->ready.empty() && !b->pending.empty() && !front_fits(b);
+}
+
+// Admission runs on a thread of its own, so uploads overlap the rounds:
+// first come first served, the first waiting system is uploaded (its stream
+// created, its device memory reserved within the budget, then allocated and
+// copied) while the worker steps the systems already admitted; it joins the
+// round after the upload.  On destroy the uploader stops once nothing that
+// waits fits.
+static void uploader_main(snp_batch* b) {
+    std::unique_lock<std::mutex> lk(b->mu);
+    for (;;) {
+        b->cv.wait(lk, [&] { return b->stop || front_fits(b); });
+        if (!front_fits(b)) return;  // stopping, and nothing that waits fits
+        Item* it = b->pending.front();
+        snp_system* s = it->sys;
+        b->pending.pop_front();
+        const size_t need = s->materialized ? 0 : s->planned_bytes;
+        b->reserved += need;
+        b->admitting = true;
+        lk.unlock();
+        const double a0 = now_s();
+        int rc = SNP_OK;
+        if (!s->stream) {
+            // a stream of its own lets grid-wide systems overlap; a blocking
+            // stream keeps the legacy default stream's ordering
+            cudaStream_t st = nullptr;
+            if (cudaStreamCreate(&st) == cudaSuccess) {
+                s->stream = st;
+                s->own_stream = true;
+            } else {
+                cudaGetLastError();
+            }
+        }
+        const bool upload = !s->materialized;
+        if (upload) rc = materialize(s);
+        const std::string err = rc ? last_error() : "";
+        const double a1 = now_s();
+        lk.lock();
+        b->admitting = false;
+        b->reserved -= need;
+        b->t_admit += a1 - a0;
+        if (!rc && upload) {
+            b->resident_bytes += s->device_bytes;
+            b->peak_bytes = std::max(b->peak_bytes, b->resident_bytes);
+            b->owned.insert(s);
+            s->owner = b;
+        }
+        if (rc)
+            finish_item(b, it, rc, err);
+        else if (it->remaining <= 0)
+            finish_item(b, it, SNP_OK, "");
+        else {
+            b->ready.push_back(it);
+            b->admitted += 1;
+        }
+        b->cv.notify_all();
+    }
 }
 
 static void worker_main(snp_batch* b) {
     std::unique_lock<std::mutex> lk(b->mu);
     for (;;) {
-        // a waiting system that does not fit wakes the worker only when a
-        // destroy returns memory (batch_release notifies)
-        b->cv.wait(lk, [&] { return b->stop || front_fits(b) || !b->active.empty(); });
-        if (b->stop && b->pending.empty() && b->active.empty()) return;
-        if (b->stop && b->active.empty() && !front_fits(b)) {
-            // destroyed while systems wait for memory: release them unrun
+        // work arrives from the uploader; a waiting system that does not fit
+        // wakes the uploader only when a destroy returns memory
+        {
+            const double w0 = now_s();
+            b->cv.wait(lk, [&] {
+                return !b->ready.empty() || !b->active.empty() || (b->stop && !b->admitting && !front_fits(b));
+            });
+            b->t_idle += now_s() - w0;
+        }
+        if (b->ready.empty() && b->active.empty()) {
+            // destroyed: what still waits does not fit; release it unrun
             for (Item* it : b->pending) finish_item(b, it, SNP_ERR_BUSY, "batch destroyed before admission");
             b->pending.clear();
             b->cv.notify_all();
             return;
         }
-        // admission, first come first served, within the memory budget
-        while (front_fits(b)) {
-            Item* it = b->pending.front();
-            snp_system* s = it->sys;
-            b->pending.pop_front();
-            int rc = SNP_OK;
-            if (!s->stream) {
-                // a stream of its own lets grid-wide systems overlap; a blocking
-                // stream keeps the legacy default stream's ordering
-                cudaStream_t st = nullptr;
-                if (cudaStreamCreate(&st) == cudaSuccess) {
-                    s->stream = st;
-                    s->own_stream = true;
-                } else {
-                    cudaGetLastError();
-                }
-            }
-            if (!s->materialized) {
-                b->admitting = true;
-                lk.unlock();
-                rc = materialize(s);
-                std::string err = rc ? last_error() : "";
-                lk.lock();
-                b->admitting = false;
-                if (!rc) {
-                    b->resident_bytes += s->device_bytes;
-                    b->peak_bytes = std::max(b->peak_bytes, b->resident_bytes);
-                    b->owned.insert(s);
-                    s->owner = b;
-                } else {
-                    finish_item(b, it, rc, err);
-                    b->cv.notify_all();
-                    continue;
-                }
-            }
-            if (it->remaining <= 0) {
-                finish_item(b, it, SNP_OK, "");
-                b->cv.notify_all();
-                continue;
-            }
-            b->active.push_back(it);
-            b->admitted += 1;
+        while (!b->ready.empty()) {
+            b->active.push_back(b->ready.front());
+            b->ready.pop_front();
         }
         if (b->active.empty()) continue;
         b->rounds += 1;
         std::vector<Item*> items = b->active;
         lk.unlock();
-        const int rc = run_round(b, items);
+        RoundTimes tm;
+        const int rc = run_round(b, items, tm);
         const std::string err = rc ? last_error() : "";
         lk.lock();
+        b->t_launch += tm.launch;
+        b->t_resident += tm.resident;
+        b->t_resident_dev += tm.resident_dev;
+        b->t_large_tail += tm.large_tail;
+        b->t_round += tm.round;
         std::vector<Item*> still;
         for (Item* it : b->active) {
             if (rc || it->finished)
@@ -444,6 +506,7 @@ int snp_batch_create(const snp_options* opts, size_t mem_budget, snp_batch** out
     cudaEventCreate(&b->ev1);
     b->tune.load(getenv("SNP_AUTOTUNE_CACHE"));
     b->worker = std::thread(worker_main, b);
+    b->uploader = std::thread(uploader_main, b);
     *out = b;
     return SNP_OK;
 }
@@ -455,6 +518,7 @@ int snp_batch_destroy(snp_batch* b) {
         b->stop = true;
     }
     b->cv.notify_all();
+    if (b->uploader.joinable()) b->uploader.join();
     if (b->worker.joinable()) b->worker.join();
     cudaStreamSynchronize(b->stream);
     {
@@ -552,6 +616,13 @@ int snp_batch_get_info(snp_batch* b, snp_batch_info* info) {
     info->finished = b->finished;
     info->waiting = (int64_t)b->pending.size();
     info->running = (int64_t)b->active.size();
+    info->admit_seconds = b->t_admit;
+    info->launch_seconds = b->t_launch;
+    info->resident_seconds = b->t_resident;
+    info->resident_device_seconds = b->t_resident_dev;
+    info->large_tail_seconds = b->t_large_tail;
+    info->idle_seconds = b->t_idle;
+    info->round_seconds = b->t_round;
     return SNP_OK;
 }
 

@@ -71,7 +71,11 @@ class snp_device_system(ct.Structure):
 class snp_batch_info(ct.Structure):
     _fields_ = [("budget_bytes", ct.c_uint64), ("resident_bytes", ct.c_uint64),
                 ("peak_resident_bytes", ct.c_uint64), ("rounds", ct.c_int64), ("admitted", ct.c_int64),
-                ("finished", ct.c_int64), ("waiting", ct.c_int64), ("running", ct.c_int64)]
+                ("finished", ct.c_int64), ("waiting", ct.c_int64), ("running", ct.c_int64),
+                ("admit_seconds", ct.c_double), ("launch_seconds", ct.c_double),
+                ("resident_seconds", ct.c_double), ("resident_device_seconds", ct.c_double),
+                ("large_tail_seconds", ct.c_double), ("idle_seconds", ct.c_double),
+                ("round_seconds", ct.c_double)]
 
 
 SNP_NOALLOC_MAX_Q = 262144
