@@ -294,6 +294,7 @@ bool resident_fits(const snp_system* s, ResidentPlan* plan) {
         plan->smem = smem;
         plan->threads = s->opt.threads > 0 ? s->opt.threads : 1024;
         plan->ctas = 1;
+        plan->big = plan->threads == 1024;  // one CTA per system: the 64-register instance
     }
     return true;
 }

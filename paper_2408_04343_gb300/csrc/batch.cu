@@ -60,25 +60,32 @@ struct Ticket {
 
 constexpr int64_t kRoundSteps = 64;          // steps per round and system
 
-// Online autotuner of the resident launch's CTA size.  Launches are grouped
-// by (bits per emission, log2 of the largest system); for each group every
-// candidate CTA size is tried on one real round (the work is not wasted:
-// results do not depend on the CTA size), then the fastest by measured
+// Online autotuner of the resident launch.  A candidate is a CTA size
+// (256, 512 or 1,024 threads) and whether the round's largest systems --
+// those holding at least one CTA's share of the round's work -- get a
+// launch of their own: one 1,024-thread CTA each with up to 64 registers,
+// beside the persistent 32-register launch for the rest.  Launches are
+// grouped by (bits per emission, log2 of the largest system); for each group
+// every candidate is tried on one real round (the work is not wasted:
+// results do not depend on the candidate), then the fastest by measured
 // synaptic updates per second is used.  With SNP_AUTOTUNE_CACHE naming a
 // file, choices are read at batch creation and written back at destroy.
 struct Autotune {
-    static constexpr int kCand[3] = {256, 512, 1024};
+    static constexpr int kN = 6;
+    static constexpr int kThreads[3] = {256, 512, 1024};
+    static int threads_of(int c) { return kThreads[c % 3]; }
+    static bool split_of(int c) { return c >= 3; }
     struct Stat {
-        double work[3] = {0, 0, 0};
-        double secs[3] = {0, 0, 0};
+        double work[kN] = {0, 0, 0, 0, 0, 0};
+        double secs[kN] = {0, 0, 0, 0, 0, 0};
     };
     std::map<std::pair<int, int>, Stat> stats;
     int pick(const std::pair<int, int>& key) {
         Stat& st = stats[key];
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < kN; ++c)
             if (st.secs[c] == 0.0) return c;
         int best = 0;
-        for (int c = 1; c < 3; ++c)
+        for (int c = 1; c < kN; ++c)
             if (st.work[c] / st.secs[c] > st.work[best] / st.secs[best]) best = c;
         return best;
     }
@@ -93,21 +100,21 @@ struct Autotune {
         int eb, lq, c;
         double w, t;
         while (fscanf(f, "%d %d %d %lf %lf", &eb, &lq, &c, &w, &t) == 5)
-            if (c >= 0 && c < 3) record({eb, lq}, c, w, t);
+            if (c >= 0 && c < kN) record({eb, lq}, c, w, t);
         fclose(f);
     }
     void save(const char* path) const {
         FILE* f = path ? fopen(path, "w") : nullptr;
         if (!f) return;
         for (const auto& kv : stats)
-            for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < kN; ++c)
                 if (kv.second.secs[c] > 0.0)
                     fprintf(f, "%d %d %d %.6g %.6g\n", kv.first.first, kv.first.second, c, kv.second.work[c],
                             kv.second.secs[c]);
         fclose(f);
     }
 };
-constexpr int Autotune::kCand[3];
+constexpr int Autotune::kThreads[3];
 constexpr int kBatchResidentMaxQ = 65536;    // larger systems run grid-wide
 
 }  // namespace snp
@@ -144,6 +151,8 @@ struct snp_batch {
     int64_t round = snp::kRoundSteps;
     snp::Autotune tune;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t stream2 = nullptr;        // the largest systems' launch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // where the worker's time goes (seconds, host clock unless noted)
     double t_admit = 0;        // uploading admitted systems
     double t_launch = 0;       // queueing the grid-wide systems' steps of a round
@@ -212,25 +221,57 @@ static int run_resident_group(snp_batch* b, std::vector<snp_system*>& sys, std::
     }
     ResidentPlan plan;
     plan.e_bits = resident_e_bits(max_p);
-    plan.max_q = max_q;
-    plan.smem = resident_smem_bytes(max_q, plan.e_bits);
     int lq = 0;
     while ((1 << lq) < max_q) ++lq;
     const std::pair<int, int> key{plan.e_bits, lq};
     const int cand = b->threads > 0 ? -1 : b->tune.pick(key);
-    plan.threads = cand < 0 ? b->threads : Autotune::kCand[cand];
+    plan.threads = cand < 0 ? b->threads : Autotune::threads_of(cand);
+    const bool split = cand >= 0 && Autotune::split_of(cand);
     const bool compact = sys[0]->compact;
     const int sel = sys[0]->opt.select;
-    plan.ctas = b->sms * ctas_per_sm(plan.threads, plan.smem);
+    std::vector<double> wk(n);
     double work = 0.0;
-    for (size_t r = 0; r < n; ++r) work += (double)(sys[order[r]]->nsyn + sys[order[r]]->q) * ns[r];
+    for (size_t r = 0; r < n; ++r) {
+        wk[r] = (double)(sys[order[r]]->nsyn + sys[order[r]]->q) * ns[r];
+        work += wk[r];
+    }
+    // the largest systems (largest first in the table): each holds at least
+    // one CTA's share of the round's work
+    size_t nbig = 0;
+    if (split) {
+        plan.smem = resident_smem_bytes(max_q, plan.e_bits);
+        const double share = work / (double)(b->sms * ctas_per_sm(plan.threads, plan.smem));
+        while (nbig < n && nbig < (size_t)b->sms && wk[nbig] >= share) ++nbig;
+    }
+    int max_q_rest = 0;
+    for (size_t r = nbig; r < n; ++r) max_q_rest = std::max(max_q_rest, sys[order[r]]->q);
+    plan.max_q = max_q_rest;
+    plan.smem = resident_smem_bytes(max_q_rest, plan.e_bits);
+    plan.ctas = b->sms * ctas_per_sm(plan.threads, plan.smem);
     if (cudaMemcpyAsync(b->d_sys, tab.data(), n * sizeof(DevSys), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
         cudaMemcpyAsync(b->d_nsteps, ns.data(), n * sizeof(long long), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-        cudaMemsetAsync(b->d_work, 0, sizeof(unsigned int), b->stream) != cudaSuccess)
+        cudaMemsetAsync(b->d_work, 0, 2 * sizeof(unsigned int), b->stream) != cudaSuccess)
         return fail(SNP_ERR_CUDA, "batch table upload");
     cudaEventRecord(b->ev0, b->stream);
-    if (launch_resident(b->d_sys, b->d_nsteps, (int)n, b->d_work, plan, compact, sel, b->stream) != cudaSuccess)
+    if (nbig) {
+        ResidentPlan pb = plan;
+        pb.big = true;
+        pb.threads = 1024;
+        pb.max_q = max_q;
+        pb.smem = resident_smem_bytes(max_q, plan.e_bits);
+        pb.ctas = (int)nbig;
+        if (cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(b->stream2, b->ev_fork, 0) != cudaSuccess ||
+            launch_resident(b->d_sys, b->d_nsteps, (int)nbig, b->d_work + 1, pb, compact, sel, b->stream2) !=
+                cudaSuccess ||
+            cudaEventRecord(b->ev_join, b->stream2) != cudaSuccess)
+            return fail(SNP_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(cudaGetLastError()));
+    }
+    if (n > nbig && launch_resident(b->d_sys + nbig, b->d_nsteps + nbig, (int)(n - nbig), b->d_work, plan, compact,
+                                    sel, b->stream) != cudaSuccess)
         return fail(SNP_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(cudaGetLastError()));
+    if (nbig && cudaStreamWaitEvent(b->stream, b->ev_join, 0) != cudaSuccess)
+        return fail(SNP_ERR_CUDA, "batch stream join");
     cudaEventRecord(b->ev1, b->stream);
     std::vector<unsigned long long> ex(n * 3);
     if (launch_gather_results(b->d_sys, (int)n, b->d_res, b->stream) != cudaSuccess ||
@@ -366,6 +407,24 @@ static void uploader_main(snp_batch* b) {
     for (;;) {
         b->cv.wait(lk, [&] { return b->stop || front_fits(b); });
         if (!front_fits(b)) return;  // stopping, and nothing that waits fits
+        // systems already on the device need no upload: admit every one that
+        // leads the queue at once, so they start in the same round
+        bool moved = false;
+        while (front_fits(b) && b->pending.front()->sys->materialized && b->pending.front()->sys->stream) {
+            Item* it = b->pending.front();
+            b->pending.pop_front();
+            if (it->remaining <= 0) {
+                finish_item(b, it, SNP_OK, "");
+            } else {
+                b->ready.push_back(it);
+                b->admitted += 1;
+            }
+            moved = true;
+        }
+        if (moved) {
+            b->cv.notify_all();
+            continue;
+        }
         Item* it = b->pending.front();
         snp_system* s = it->sys;
         b->pending.pop_front();
@@ -496,14 +555,18 @@ int snp_batch_create(const snp_options* opts, size_t mem_budget, snp_batch** out
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaMalloc(&b->d_work, sizeof(unsigned int)) != cudaSuccess) {
+    if (cudaMalloc(&b->d_work, 2 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
+        cudaFree(b->d_work);
         if (b->own_stream) cudaStreamDestroy(b->stream);
         delete b;
         return fail(SNP_ERR_OOM, "device allocation failed");
     }
     cudaEventCreate(&b->ev0);
     cudaEventCreate(&b->ev1);
+    cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     b->tune.load(getenv("SNP_AUTOTUNE_CACHE"));
     b->worker = std::thread(worker_main, b);
     b->uploader = std::thread(uploader_main, b);
@@ -527,8 +590,12 @@ int snp_batch_destroy(snp_batch* b) {
         b->owned.clear();
     }
     b->tune.save(getenv("SNP_AUTOTUNE_CACHE"));
+    cudaStreamSynchronize(b->stream2);
     cudaEventDestroy(b->ev0);
     cudaEventDestroy(b->ev1);
+    cudaEventDestroy(b->ev_fork);
+    cudaEventDestroy(b->ev_join);
+    cudaStreamDestroy(b->stream2);
     cudaFree(b->d_sys);
     cudaFree(b->d_nsteps);
     cudaFree(b->d_res);

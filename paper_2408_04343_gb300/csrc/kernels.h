@@ -34,6 +34,7 @@ struct ResidentPlan {
     int max_q;       // largest system of the launch
     int ctas;        // grid size
     size_t smem;     // dynamic shared memory per CTA
+    bool big = false;  // the 64-register instance, one 1,024-thread CTA per system
 };
 int resident_e_bits(int max_p);
 size_t resident_smem_bytes(int max_q, int e_bits);

@@ -148,10 +148,12 @@ __device__ void run_resident(const DevSys& s, long long n, uint32_t* esm) {
     }
 }
 
-template <bool COMPACT, int SEL, int EB>
-__global__ void __launch_bounds__(kResMaxThreads, kResMinBlocks) k_resident(const DevSys* __restrict__ systems,
-                                                   const long long* __restrict__ nsteps, int nsys,
-                                                   unsigned int* work) {
+// BIG: the instance for a batch's largest systems, one 1,024-thread CTA per
+// SM with up to 64 registers (no spills on their long critical path).
+template <bool COMPACT, int SEL, int EB, bool BIG>
+__global__ void __launch_bounds__(kResMaxThreads, BIG ? 1 : kResMinBlocks)
+    k_resident(const DevSys* __restrict__ systems, const long long* __restrict__ nsteps, int nsys,
+               unsigned int* work) {
     extern __shared__ uint32_t esm[];
     __shared__ int s_id;
     for (;;) {
@@ -373,7 +375,14 @@ int resident_max_smem() {
 template <bool C, int S, int EB>
 static cudaError_t launch_res_t(const DevSys* d_systems, const long long* d_nsteps, int nsys, unsigned int* d_work,
                                 const ResidentPlan& plan, cudaStream_t st) {
-    auto fn = k_resident<C, S, EB>;
+    if (plan.big) {  // one 1,024-thread CTA per system, 64 registers
+        auto fb = k_resident<C, S, EB, true>;
+        cudaError_t e = cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+        if (e != cudaSuccess) return e;
+        fb<<<nsys, kResMaxThreads, plan.smem, st>>>(d_systems, d_nsteps, nsys, d_work);
+        return cudaGetLastError();
+    }
+    auto fn = k_resident<C, S, EB, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
     if (e != cudaSuccess) return e;
     const int threads = plan.threads < kResMaxThreads ? plan.threads : kResMaxThreads;
