@@ -334,6 +334,48 @@ typedef struct snp_batch_info {
 } snp_batch_info;
 int snp_batch_get_info(snp_batch* b, snp_batch_info* info);
 
+/* ---- the neuron-sharded step (one system over several devices) ----------
+ * The paper simulates a system on one GPU; its future work names larger
+ * systems.  A system too large for one device is split by neuron range into
+ * shards, one per device.  Each step of the definition needs data of other
+ * neurons at one point only -- the in-flow of phase 2 (Sec. 2: a neuron
+ * receives the spikes its in-neighbours emit) -- so a step of the sharded
+ * system is, on every shard: snp_shard_select (phase 1 for the shard's
+ * neurons: complete / count down / choose a rule and consume, the delay
+ * status; their emissions go into the shard's slice [lo, hi) of its
+ * emission vector), then the caller exchanges the slices so that every
+ * shard's vector holds all q emissions (an allgather, 2 bytes per neuron)
+ * and ORs the shards' `active` flags (the fixed point of Alg. 1: no shard
+ * active means the step is not executed and nothing changed), then
+ * snp_shard_gather (phase 2 for the shard's neurons from the whole vector).
+ * Results equal the unsharded system's, step for step (the Philox counter
+ * keeps the global neuron id).
+ *
+ * snp_shard_create: the shard of neurons lo..hi-1 (0 <= lo < hi <= q) of
+ *   the system desc (validated as by snp_create; the whole desc is read,
+ *   the shard keeps its neurons' rules, state and in-lists with global
+ *   source ids).  E: the emission vector, DEVICE memory of at least q + 1
+ *   uint16 entries owned by the caller (so that a collective library can
+ *   write into it), or NULL to let the shard allocate it.  opts: select,
+ *   seed, stream (form, engine, allocator and flags are not used).  The
+ *   state starts at C_0, no delays, step counter chosen by the caller.
+ * snp_shard_emissions: the device address of the emission vector.
+ * snp_shard_select(k): phase 1 of step k; waits for the device and sets
+ *   *active.  SNP_ERR_OVERFLOW if an earlier phase 2 left int32 range.
+ * snp_shard_gather: phase 2 of the step last selected (queued on the
+ *   stream); marks that step executed.
+ * snp_shard_get_state: C, D, P and the spiking vector of the last executed
+ *   step (global rule ids, -1 none) of the shard's neurons, hi - lo entries
+ *   each (host or device).                                                */
+typedef struct snp_shard snp_shard;
+int snp_shard_create(const snp_desc* desc, int32_t lo, int32_t hi, const snp_options* opts, uint16_t* E,
+                     snp_shard** out);
+int snp_shard_destroy(snp_shard* sh);
+int snp_shard_emissions(snp_shard* sh, uint16_t** E);
+int snp_shard_select(snp_shard* sh, uint64_t k, int32_t* active);
+int snp_shard_gather(snp_shard* sh);
+int snp_shard_get_state(const snp_shard* sh, int32_t* C, int32_t* D, int32_t* P, int32_t* S, int64_t len);
+
 /* ---- paper formats, host only (inspection and memory accounting) -------- */
 /* The paper's matrices for a system, written densely on the host:
  *   snp_export_dense: M_Pi, m x q row-major (Table 1 layout);

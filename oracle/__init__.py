@@ -5,8 +5,8 @@ use this package.  The simulator never imports it.
 """
 from .oracle import (FIRST, PHILOX, FORCED, OracleError, OracleOverflow, build, load,
                      philox4x32_10, step, run, run_trace, is_halted, initial_state, threads,
-                     PullRunner, count_choices)
+                     PullRunner, RangeShard, count_choices)
 
 __all__ = ["FIRST", "PHILOX", "FORCED", "OracleError", "OracleOverflow", "build", "load",
            "philox4x32_10", "step", "run", "run_trace", "is_halted", "initial_state", "threads",
-           "PullRunner", "count_choices"]
+           "PullRunner", "RangeShard", "count_choices"]

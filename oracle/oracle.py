@@ -80,6 +80,13 @@ def load():
                                          ct.c_void_p, ct.c_uint64, ct.c_int64, ct.c_int, ct.c_uint64,
                                          ct.c_void_p, ct.POINTER(ct.c_int64)]
             lib.orc_run_pull.restype = ct.c_int
+            lib.orc_range_select.argtypes = [ct.POINTER(_Sys), ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p,
+                                             ct.c_void_p, ct.c_uint64, ct.c_int, ct.c_uint64, ct.c_void_p,
+                                             ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_int)]
+            lib.orc_range_select.restype = ct.c_int
+            lib.orc_range_receive.argtypes = [ct.POINTER(_Sys), ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p,
+                                              ct.c_void_p, ct.c_void_p, ct.c_void_p]
+            lib.orc_range_receive.restype = ct.c_int
             _lib = lib
     return _lib
 
@@ -208,3 +215,31 @@ def count_choices(desc, state) -> np.ndarray:
     out = np.zeros(desc.q, np.int32)
     load().orc_count_choices(ct.byref(b.s), _ptr(C), _ptr(P), _ptr(out))
     return out
+
+
+class RangeShard:
+    """The definition's step split at its exchange point for the neurons
+    lo..hi-1 (orc_range_select / orc_range_receive): a shard of a system
+    partitioned by neuron range, holding the whole state arrays but changing
+    only its own neurons.  E is the whole emission vector (int32, q); the
+    caller fills the other shards' entries between the two phases."""
+
+    def __init__(self, desc, lo: int, hi: int, state=None):
+        self.desc = desc
+        self.b = _Bound(desc)
+        self.lo, self.hi = int(lo), int(hi)
+        self.C, self.D, self.P = (x.copy() for x in (state or initial_state(desc)))
+        self.S = np.full(desc.q, -1, np.int32)
+        self.E = np.zeros(desc.q, np.int32)
+        self.recv = np.ones(desc.q, np.int8)
+
+    def select(self, k: int, mode: int = FIRST, seed: int = 0) -> bool:
+        act = ct.c_int(0)
+        _check(load().orc_range_select(ct.byref(self.b.s), self.lo, self.hi, _ptr(self.C), _ptr(self.D),
+                                       _ptr(self.P), ct.c_uint64(k), mode, ct.c_uint64(seed), _ptr(self.S),
+                                       _ptr(self.E), _ptr(self.recv), ct.byref(act)))
+        return bool(act.value)
+
+    def receive(self):
+        _check(load().orc_range_receive(ct.byref(self.b.s), self.lo, self.hi, _ptr(self.C), _ptr(self.D),
+                                        _ptr(self.P), _ptr(self.E), _ptr(self.recv)))

@@ -253,6 +253,88 @@ int orc_step(const orc_sys* s, int32_t* C, int32_t* D, int32_t* P, uint64_t step
  * fixed point.  *executed receives the number of steps actually taken and S
  * the spiking vector of the last executed step (left untouched if none).
  */
+/* The definition's step split at its exchange point, for the neurons
+ * lo..hi-1 only (one shard of a system partitioned by neuron range; test
+ * infrastructure for the sharded step).  orc_range_select is phase 1 for
+ * those neurons -- complete a delayed rule / count down / choose an
+ * applicable rule and consume -- writing their emissions into E[lo..hi-1],
+ * their spiking vector into S[lo..hi-1], whether each can receive this step
+ * into recv[lo..hi-1], and *active = 1 when any of them is pending or chose
+ * a rule.  The system is at a fixed point when no shard is active; then no
+ * state changed.  Once E holds every shard's emissions, orc_range_receive is
+ * phase 2 for the same neurons (every emission pushed along the synapses
+ * into the open ones among lo..hi-1) and phase 3 (their delay counters).
+ * Composed over shards covering 0..q-1 this is exactly orc_step.           */
+int orc_range_select(const orc_sys* s, int32_t lo, int32_t hi, int32_t* C, int32_t* D, int32_t* P,
+                     uint64_t step, int mode, uint64_t seed, int32_t* S, int32_t* E, char* recv,
+                     int* active) {
+    *active = 0;
+    for (int32_t i = lo; i < hi; ++i) {
+        const int64_t n = C[i];
+        S[i] = -1;
+        E[i] = 0;
+        recv[i] = 1;
+        if (P[i] != -1 && D[i] == 0) {
+            *active = 1;
+            E[i] = s->rp[P[i]];
+            P[i] = -1;
+        } else if (P[i] != -1) {
+            *active = 1;
+            recv[i] = 0;
+        } else {
+            const int64_t a = orc_count_applicable(s, i, n);
+            if (a == 0) continue;
+            *active = 1;
+            int64_t pick = 0;
+            if (mode == ORC_PHILOX) {
+                uint32_t ctr[4] = {(uint32_t)step, (uint32_t)i, (uint32_t)(step >> 32), 0u};
+                uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+                uint32_t x[4];
+                orc_philox4x32_10(ctr, key, x);
+                pick = (int64_t)(((uint64_t)x[0] * (uint64_t)a) >> 32);
+            } else if (mode != ORC_FIRST) {
+                return ORC_ERR_INVALID;
+            }
+            const int64_t r = orc_nth_applicable(s, i, n, pick);
+            S[i] = (int32_t)r;
+            C[i] = (int32_t)(n - s->rc[r]);
+            if (s->rd[r] == 0) {
+                E[i] = s->rp[r];
+            } else {
+                P[i] = (int32_t)r;
+                D[i] = s->rd[r];
+                recv[i] = 0;
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+int orc_range_receive(const orc_sys* s, int32_t lo, int32_t hi, int32_t* C, int32_t* D, const int32_t* P,
+                      const int32_t* E, const char* recv) {
+    const int32_t q = s->q;
+    int rc = ORC_OK;
+    int64_t* add = (int64_t*)calloc((size_t)(hi > lo ? hi - lo : 1), sizeof(int64_t));
+    if (!add) return ORC_ERR_OOM;
+    /* phase 2: every emission pushed along its synapses into lo..hi-1 */
+    for (int32_t i = 0; i < q; ++i) {
+        if (E[i] == 0) continue;
+        for (int64_t e = s->syn_off[i]; e < s->syn_off[i + 1]; ++e) {
+            const int32_t t = s->syn_tgt[e];
+            if (t >= lo && t < hi && recv[t]) add[t - lo] += E[i];
+        }
+    }
+    for (int32_t t = lo; t < hi; ++t) {
+        const int64_t c = (int64_t)C[t] + add[t - lo];
+        if (c > INT32_MAX || c < INT32_MIN) rc = ORC_ERR_OVERFLOW;
+        C[t] = (int32_t)c;
+        /* phase 3 */
+        if (P[t] != -1) D[t] -= 1;
+    }
+    free(add);
+    return rc;
+}
+
 int orc_run(const orc_sys* s, int32_t* C, int32_t* D, int32_t* P, uint64_t step0,
             int64_t nsteps, int mode, uint64_t seed, int32_t* S, int64_t* executed) {
     int32_t* Stmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->q > 0 ? s->q : 1));

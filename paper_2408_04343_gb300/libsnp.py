@@ -110,6 +110,13 @@ _SIGS = {
     "snp_count_choices": (ct.c_int, [_P, ct.c_void_p, ct.c_int64]),
     "snp_set_choices": (ct.c_int, [_P, ct.c_void_p, ct.c_int64]),
     "snp_branch_step": (ct.c_int, [_P, ct.c_int32] + [ct.c_void_p] * 10),
+    "snp_shard_create": (ct.c_int, [ct.POINTER(snp_desc), ct.c_int32, ct.c_int32, ct.POINTER(snp_options), _P,
+                                     ct.POINTER(ct.c_void_p)]),
+    "snp_shard_destroy": (ct.c_int, [_P]),
+    "snp_shard_emissions": (ct.c_int, [_P, ct.POINTER(ct.c_void_p)]),
+    "snp_shard_select": (ct.c_int, [_P, ct.c_uint64, ct.POINTER(ct.c_int32)]),
+    "snp_shard_gather": (ct.c_int, [_P]),
+    "snp_shard_get_state": (ct.c_int, [_P, _P, _P, _P, _P, ct.c_int64]),
     "snp_strerror": (ct.c_char_p, [ct.c_int]),
     "snp_last_error": (ct.c_char_p, []),
 }
@@ -415,3 +422,52 @@ def snp_step_noalloc(q, m, rule_offsets, rule_k, rule_j, rule_c, rule_p, rule_d,
     check(load().snp_step_noalloc(ct.byref(d), int(select), int(seed) & (2**64 - 1), int(step), int(n),
                                   _stream_handle(stream), ct.byref(done) if wait else None))
     return int(done.value) if wait else None
+
+
+# ---- the neuron-sharded step ------------------------------------------------
+
+class Shard:
+    """snp_shard_*: neurons lo..hi-1 of one system (see shard.py for the step
+    protocol).  E: the emission vector, a device tensor (int16/uint16, at
+    least q + 1 entries) or raw device pointer the caller owns, or None."""
+
+    def __init__(self, desc, lo, hi, *, select=SNP_SELECT_FIRST, seed=None, stream=None, E=None):
+        lib = load()
+        self._lib = lib
+        self.lo, self.hi, self.q = int(lo), int(hi), int(desc.q)
+        h = _DescHolder(desc)
+        seed = getattr(desc, "seed", 0) if seed is None else seed
+        opts = make_options(select=select, seed=int(seed), stream=stream)
+        out = ct.c_void_p()
+        check(lib.snp_shard_create(ct.byref(h.d), self.lo, self.hi, ct.byref(opts), _ptr(E), ct.byref(out)))
+        self.handle = out.value
+
+    def emissions_ptr(self) -> int:
+        p = ct.c_void_p()
+        check(self._lib.snp_shard_emissions(self.handle, ct.byref(p)))
+        return int(p.value)
+
+    def select(self, k: int) -> bool:
+        a = ct.c_int32(0)
+        check(self._lib.snp_shard_select(self.handle, int(k), ct.byref(a)))
+        return bool(a.value)
+
+    def receive(self):
+        check(self._lib.snp_shard_gather(self.handle))
+
+    def get_state(self):
+        n = self.hi - self.lo
+        C, D, P, S = (np.empty(n, np.int32) for _ in range(4))
+        check(self._lib.snp_shard_get_state(self.handle, _ptr(C), _ptr(D), _ptr(P), _ptr(S), n))
+        return C, D, P, S
+
+    def close(self):
+        if getattr(self, "handle", None):
+            check(self._lib.snp_shard_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -70,3 +70,81 @@ def test_reference_arm_under_torchrun_two_ranks():
     j = json.loads(lines[0])
     assert j["impl"] == "reference" and j["n_gpus"] == 2 and j["value"] > 0
     assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["cpu_baseline"]["kind"] == "oracle"
+
+
+def _shard_worker(rank, ws, port, out, mode, seed, nsteps):
+    """One rank of a system split by neuron range: this rank's neurons run the
+    definition's two phases (the oracle's range phases, test infrastructure),
+    the emission slices travel by an in-place all_gather over gloo, the
+    activity by an all_reduce; the protocol is paper_2408_04343_gb300.shard."""
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(ws), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import oracle
+    from paper_2408_04343_gb300 import shard, synth
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    d = _shard_system()
+    ranges, chunk = shard.shard_ranges(d.q, ws)
+    lo, hi = ranges[rank]
+    E = torch.zeros(ws * chunk + 1, dtype=torch.int32)
+    sh = oracle.RangeShard(d, lo, hi)
+    sh.E = E.numpy()[:d.q]           # the shard's emission vector is the exchanged tensor
+
+    class Local:
+        def select(self, k):
+            return sh.select(k, mode, seed)
+
+        def receive(self):
+            sh.receive()
+
+    ex, any_active = shard.collective_exchange(E, rank, ws, chunk)
+    done = shard.run([Local()], nsteps, 0, ex, any_active)
+    # gather every rank's slice of the state
+    parts = []
+    for arr in (sh.C, sh.D, sh.P):
+        mine = torch.zeros(chunk, dtype=torch.int32)
+        mine[:hi - lo] = torch.from_numpy(arr[lo:hi].copy())
+        allp = [torch.zeros(chunk, dtype=torch.int32) for _ in range(ws)]
+        dist.all_gather(allp, mine)
+        parts.append(torch.cat(allp)[:d.q].numpy())
+    out.put((rank, done, [p.tolist() for p in parts]))
+    dist.destroy_process_group()
+
+
+def _shard_system():
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from paper_2408_04343_gb300 import synth
+    return synth.random_system(2500, 77, outdeg=(2, 12), rules=(2, 4), d_range=(0, 3), spikes=(0, 12))
+
+
+@pytest.mark.parametrize("mode_name", ["first", "philox"])
+def test_sharded_step_gloo_world2_matches_the_oracle(mode_name):
+    """A system split by neuron range over two gloo ranks on CPU: phase 1 on
+    each rank, the emission slices all-gathered, the activity all-reduced,
+    phase 2 on each rank (the protocol of shard.py that the CUDA shards
+    follow) gives the whole system's oracle result bit for bit."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    import torch.multiprocessing as mp
+    import oracle
+    oracle.build()
+    mode, seed, nsteps = (oracle.FIRST if mode_name == "first" else oracle.PHILOX), 4242, 40
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q, mode, seed, nsteps)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in range(2)), key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    d = _shard_system()
+    st = oracle.initial_state(d)
+    ex, _ = oracle.run(d, st, nsteps, mode, seed)
+    for rank, done, (C, D, P) in res:
+        assert done == ex
+        assert (np.asarray(C) == st[0]).all() and (np.asarray(D) == st[1]).all() and (np.asarray(P) == st[2]).all()

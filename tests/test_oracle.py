@@ -637,3 +637,33 @@ def test_union_bruteforce_tree(seed):
                         assert S[i] == A[i][combo[i]]
                 nxt.append(s2)
         frontier = nxt[:24]
+
+
+@pytest.mark.parametrize("cuts", [(0, 3000), (0, 1100, 2050, 3000), (0, 1, 2999, 3000)])
+@pytest.mark.parametrize("mode", [oracle.FIRST, oracle.PHILOX])
+def test_range_phases_compose_to_the_step(cuts, mode):
+    """The definition split at its exchange point (phase 1 per neuron range,
+    the emissions of every range collected, then phase 2 and the delay update
+    per range) composes, over ranges covering all neurons, to the whole step:
+    the same states and executed step count as orc_run over 30 steps, and
+    nothing executes once no range is active (the fixed point)."""
+    d = synth.random_system(3000, 5, outdeg=(2, 10), rules=(3, 4), d_range=(0, 3), spikes=(0, 12))
+    full = oracle.initial_state(d)
+    ex, _ = oracle.run(d, full, 30, mode, 7)
+    sh = [oracle.RangeShard(d, a, b) for a, b in zip(cuts[:-1], cuts[1:])]
+    k = 0
+    for _ in range(30):
+        act = [x.select(k, mode, 7) for x in sh]
+        if not any(act):
+            break
+        E = np.zeros(d.q, np.int32)
+        for x in sh:
+            E[x.lo:x.hi] = x.E[x.lo:x.hi]
+        for x in sh:
+            x.E[:] = E
+            x.receive()
+        k += 1
+    assert k == ex
+    for i, arr in enumerate(full):
+        got = np.concatenate([(x.C, x.D, x.P)[i][x.lo:x.hi] for x in sh])
+        assert (got == arr).all()
