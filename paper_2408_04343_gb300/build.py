@@ -15,6 +15,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsnp.so")
+# The bounds-checked debug build (-DSNP_CHECK_BOUNDS): every kernel checks
+# its data-dependent indices and reports an out-of-range one as an error
+# instead of reading outside a buffer.  Built by build(check_bounds=True);
+# the binding loads it when SNP_CHECK_BOUNDS=1 is set in the environment.
+CHECK_DIR = os.path.join(HERE, "_build_check")
+CHECK_LIB = os.path.join(CHECK_DIR, "libsnp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,14 +42,17 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), check_bounds: bool = False) -> str:
+    out_dir, lib = (CHECK_DIR, CHECK_LIB) if check_bounds else (OUT_DIR, LIB)
+    if check_bounds:
+        extra = tuple(extra) + ("-DSNP_CHECK_BOUNDS",)
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(HERE, "..", "include", "*.h"))
     objs, procs = [], []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         objs.append(obj)
         if not force and not _stale(obj, [src] + headers):
             continue
@@ -64,12 +73,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    if force or procs or not os.path.exists(LIB):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or procs or not os.path.exists(lib):
+        tmp = lib + f".{os.getpid()}.tmp"
         subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared",
                                "-Xlinker", "-rpath,$ORIGIN"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 

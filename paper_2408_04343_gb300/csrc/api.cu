@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -381,6 +382,14 @@ int read_flags(snp_system* s, int64_t* exec) {
         cudaMemcpyAsync(s->dev.flags + kFlagOverflow, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream);
         cudaStreamSynchronize(s->stream);
         return fail(SNP_ERR_OVERFLOW, "a spike count left the int32 range");
+    }
+    if (fl[kFlagBounds]) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "bounds check: an index out of range (sites 0x%x)", fl[kFlagBounds]);
+        const uint32_t zero = 0;
+        cudaMemcpyAsync(s->dev.flags + kFlagBounds, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream);
+        cudaStreamSynchronize(s->stream);
+        return fail(SNP_ERR_INVALID, msg);
     }
     if (fl[kFlagTimeout]) return fail(SNP_ERR_TIMEOUT, "a bounded device wait gave up");
     if (fl[kFlagChoice]) {

@@ -286,12 +286,14 @@ static int run_resident_group(snp_batch* b, std::vector<snp_system*>& sys, std::
             if (cand >= 0) b->tune.record(key, cand, work, ms * 1e-3);
         }
     }
-    bool overflow = false;
+    bool overflow = false, bounds = false;
     for (size_t r = 0; r < n; ++r) {
         exec_out[order[r]] = (int64_t)ex[3 * r + 1];
         sys[order[r]]->host_step = ex[3 * r + 0];
-        overflow |= ex[3 * r + 2] != 0ull;
+        overflow |= (ex[3 * r + 2] & 1ull) != 0ull;
+        bounds |= (ex[3 * r + 2] & 2ull) != 0ull;
     }
+    if (bounds) return fail(SNP_ERR_INVALID, "bounds check: an index out of range in a batched system");
     if (overflow) return fail(SNP_ERR_OVERFLOW, "a spike count left the int32 range in a batched system");
     return SNP_OK;
 }

@@ -13,6 +13,27 @@
 
 namespace snp {
 
+// ---- bounds-checked builds -----------------------------------------------
+// Built with SNP_CHECK_BOUNDS, every index passed through SNP_IDX is compared
+// with its limit; an index outside [0, limit) is replaced by 0, so the access
+// stays inside its buffer, and bit `site` is OR-ed into the system's
+// kFlagBounds word, which snp_step reports as SNP_ERR_INVALID.  Built
+// without it SNP_IDX is the index itself.  Sites: 0 an in-list entry's
+// emission index, 1 a packed emission word in shared memory, 2 a shared
+// accumulator, 3 a push target, 4 an ELL (rule, p) pair's rule.
+#ifdef SNP_CHECK_BOUNDS
+__device__ __forceinline__ long long snp_idx(uint32_t* flags, int site, long long i, long long limit) {
+    if (i < 0 || i >= limit) {
+        atomicOr(flags + kFlagBounds, 1u << site);
+        return 0;
+    }
+    return i;
+}
+#define SNP_IDX(flags, site, i, limit) (::snp::snp_idx((flags), (site), (long long)(i), (long long)(limit)))
+#else
+#define SNP_IDX(flags, site, i, limit) (i)
+#endif
+
 // ---- Philox4x32-10 ------------------------------------------------------
 // Counter-based generator of Salmon, Moraes, Dror and Shaw ("Parallel Random
 // Numbers: As Easy as 1, 2, 3", SC'11).  Ten rounds; each round takes the

@@ -68,11 +68,12 @@ __global__ void __launch_bounds__(256) k_ell_pull(DevSys s, EllSys e, int32_t t)
             for (; col + 4 <= w; col += 4) {
                 const int2 a0 = __ldg(p + (col + 0) * kSlice), a1 = __ldg(p + (col + 1) * kSlice);
                 const int2 a2 = __ldg(p + (col + 2) * kSlice), a3 = __ldg(p + (col + 3) * kSlice);
-                sum += (Em[a0.x] ? a0.y : 0) + (Em[a1.x] ? a1.y : 0) + (Em[a2.x] ? a2.y : 0) + (Em[a3.x] ? a3.y : 0);
+                sum += (Em[SNP_IDX(fl, 4, a0.x, e.m + 1)] ? a0.y : 0) + (Em[SNP_IDX(fl, 4, a1.x, e.m + 1)] ? a1.y : 0) +
+                       (Em[SNP_IDX(fl, 4, a2.x, e.m + 1)] ? a2.y : 0) + (Em[SNP_IDX(fl, 4, a3.x, e.m + 1)] ? a3.y : 0);
             }
             for (; col < w; ++col) {
                 const int2 a = __ldg(p + col * kSlice);
-                sum += Em[a.x] ? a.y : 0;
+                sum += Em[SNP_IDX(fl, 4, a.x, e.m + 1)] ? a.y : 0;
             }
             if (valid && (s.st[slot] >> kPendShift) == 0u) {
                 long long nc = (long long)c + sum;
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(256, kEllPushBlocksPerSm) k_ell_push(DevSys s,
     src.Em = SNP_PICK(e.Em, kg);
     src.m = e.m;
     const int32_t nrs = (int32_t)((e.m + kSlice - 1) / kSlice);
-    push_scatter_balanced<8>(src, e.out_ptr, nrs, e.out_ent, s.C, s.st, fl + kFlagOverflow);
+    push_scatter_balanced<8>(src, e.out_ptr, nrs, e.out_ent, s.C, s.st, fl, s.q);
 }
 
 // Dense accumulation of step kg = base + t: CTA (bx, by) covers neurons

@@ -113,9 +113,13 @@ __device__ void run_resident(const DevSys& s, long long n, uint32_t* esm) {
                 const int32_t i1 = __ldg(p + (col + 1) * kSlice);
                 const int32_t i2 = __ldg(p + (col + 2) * kSlice);
                 const int32_t i3 = __ldg(p + (col + 3) * kSlice);
-                sum += (long long)e_get<EB>(Ek, i0) + e_get<EB>(Ek, i1) + e_get<EB>(Ek, i2) + e_get<EB>(Ek, i3);
+                const int32_t lim = s.nslices * 32 + 32;  // the packed vector's entries
+                sum += (long long)e_get<EB>(Ek, SNP_IDX(s.flags, 0, i0, lim)) +
+                       e_get<EB>(Ek, SNP_IDX(s.flags, 0, i1, lim)) + e_get<EB>(Ek, SNP_IDX(s.flags, 0, i2, lim)) +
+                       e_get<EB>(Ek, SNP_IDX(s.flags, 0, i3, lim));
             }
-            for (; col < w; ++col) sum += e_get<EB>(Ek, __ldg(p + col * kSlice));
+            for (; col < w; ++col)
+                sum += e_get<EB>(Ek, SNP_IDX(s.flags, 0, __ldg(p + col * kSlice), s.nslices * 32 + 32));
             if (valid && (st >> kPendShift) == 0u) {
                 long long nc = (long long)c + sum;
                 if (nc > 2147483647ll) {
@@ -174,7 +178,7 @@ __global__ void k_gather_results(const DevSys* __restrict__ systems, int nsys, u
     const DevSys& s = systems[r];
     out[3 * r + 0] = s.step[kStepBase];
     out[3 * r + 1] = s.step[kStepExec];
-    out[3 * r + 2] = s.flags[kFlagOverflow];
+    out[3 * r + 2] = (s.flags[kFlagOverflow] ? 1u : 0u) | (s.flags[kFlagBounds] ? 2u : 0u);
 }
 
 cudaError_t launch_gather_results(const DevSys* d_systems, int nsys, unsigned long long* d_out, cudaStream_t st) {
@@ -237,7 +241,8 @@ __global__ void __launch_bounds__(256) k_branch_step(DevSys s, const int32_t* __
                 const int32_t b0 = __ldg(s.slice_ptr + sl);
                 const int32_t w = __ldg(s.slice_ptr + sl + 1) - b0;
                 const int32_t* __restrict__ p = s.in_idx + (size_t)b0 * kSlice + lane;
-                for (int32_t col = 0; col < w; ++col) in += e_get<EB>(Esm, __ldg(p + col * kSlice));
+                for (int32_t col = 0; col < w; ++col)
+                    in += e_get<EB>(Esm, SNP_IDX(s.flags, 0, __ldg(p + col * kSlice), s.nslices * 32 + 32));
             }
             if (slot < s.q) {
                 const int32_t nid = (int32_t)neuron_id(s, slot);

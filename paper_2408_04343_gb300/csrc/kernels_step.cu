@@ -61,9 +61,10 @@ __global__ void __launch_bounds__(256) k_step_pull(DevSys s, int32_t t) {
                 const int32_t i1 = __ldg(p + (col + 1) * kSlice);
                 const int32_t i2 = __ldg(p + (col + 2) * kSlice);
                 const int32_t i3 = __ldg(p + (col + 3) * kSlice);
-                sum += (long long)E[i0] + E[i1] + E[i2] + E[i3];
+                sum += (long long)E[SNP_IDX(fl, 0, i0, s.q + 1)] + E[SNP_IDX(fl, 0, i1, s.q + 1)] +
+                       E[SNP_IDX(fl, 0, i2, s.q + 1)] + E[SNP_IDX(fl, 0, i3, s.q + 1)];
             }
-            for (; col < w; ++col) sum += E[__ldg(p + col * kSlice)];
+            for (; col < w; ++col) sum += E[SNP_IDX(fl, 0, __ldg(p + col * kSlice), s.q + 1)];
             if (valid && (st >> kPendShift) == 0u) {
                 long long nc = (long long)c + sum;
                 if (nc > 2147483647ll) {
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(256, kPushBlocksPerSm) k_push_scatter(DevSys s
     PushOptSrc src;
     src.E = SNP_PICK(s.E, kg);
     src.q = s.q;
-    push_scatter_balanced<8>(src, s.out_ptr, s.nslices, s.out_idx, s.C, s.st, fl + kFlagOverflow);
+    push_scatter_balanced<8>(src, s.out_ptr, s.nslices, s.out_idx, s.C, s.st, fl, s.q);
 }
 
 // Select-only launch for the push form: step kg = base + t.

@@ -188,18 +188,27 @@ __device__ __forceinline__ void st_shared_u8(uint32_t a, uint32_t v) {
 // d > 0 -- then adds its emission to the run: word b / 32 of Esm, rotated
 // by b mod 32 (the funnel shift takes its count mod 32).  `cur` is the
 // shared address of the current target's accumulator.
+// fl, ewords, abase, alim: the bounds-checked build's flag word, the packed
+// emission words, the accumulators' shared address and byte size.
 template <int EB, bool ACC8 = false>
 __device__ __forceinline__ void rle_vector(const uint32_t* __restrict__ Esm, const uint4& q, int db,
-                                           uint32_t& cur, uint32_t& run) {
+                                           uint32_t& cur, uint32_t& run, uint32_t* fl = nullptr,
+                                           int32_t ewords = 0, uint32_t abase = 0u, int32_t alim = 0) {
     constexpr uint32_t M = 0xFFFFFFu;
     const uint32_t e[5] = {q.x & M, __funnelshift_r(q.x, q.y, 24) & M, __funnelshift_r(q.y, q.z, 16) & M, q.z >> 8,
                            q.w & M};
     const uint32_t dmask = (1u << db) - 1u;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const uint32_t word = Esm[e[i] >> (db + 5)];
+        const uint32_t word = Esm[SNP_IDX(fl, 1, e[i] >> (db + 5), ewords)];
         const uint32_t v = __funnelshift_r(word, word, e[i] >> db) & ((1u << EB) - 1u);
         const uint32_t d = e[i] & dmask;
+#ifdef SNP_CHECK_BOUNDS
+        if (d != 0u && (int32_t)(cur - abase) >= alim) {  // the accumulator a flush would write
+            atomicOr(fl + kFlagBounds, 1u << 2);
+            cur = abase;
+        }
+#endif
         if constexpr (ACC8) {
             run = run_flush8(cur, run, d) + v;
             cur += d;
@@ -409,9 +418,15 @@ __device__ __forceinline__ int tiled_gather_phase(const DevSys& s, const TiledSy
             const uint4 v = x0;
             x0 = x1;
             x1 = ld_stream_v4(col + (size_t)(u + 2) * kTiledThreads);
-            rle_vector<EB, ACC8>(Esm, v, db, cur, run);
+            rle_vector<EB, ACC8>(Esm, v, db, cur, run, s.flags, tl.part_words + 4, acc0, tl.acc_words * 4);
         }
         // the last target of the run (the dummy slot for an empty run)
+#ifdef SNP_CHECK_BOUNDS
+        if ((int32_t)(cur - acc0) >= tl.acc_words * 4) {
+            atomicOr(s.flags + kFlagBounds, 1u << 2);
+            cur = acc0;
+        }
+#endif
         if constexpr (ACC8)
             st_shared_u8(cur, run);
         else
@@ -682,7 +697,8 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
                 // in 16-bit halves (at most 8 x 255 each)
                 const uint8_t* acc8 = reinterpret_cast<const uint8_t*>(acc);
                 const uint8_t* rin8 = reinterpret_cast<const uint8_t*>(rin);
-                const uint32_t ow = *reinterpret_cast<const uint32_t*>(acc8 + (slot0 - lo * kSlice));
+                const uint32_t ow = *reinterpret_cast<const uint32_t*>(
+                    acc8 + SNP_IDX(s.flags, 2, slot0 - lo * kSlice, tl.acc_words * 4 - 3));
                 uint32_t ev = ow & 0x00FF00FFu, od = (ow >> 8) & 0x00FF00FFu;
                 for (int r = 0; r + 1 < tl.P; ++r) {
                     const uint32_t w =
@@ -694,7 +710,7 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
             } else if (live) {
                 c4 = *reinterpret_cast<const int4*>(s.C + slot0);
                 st4 = *reinterpret_cast<const uint4*>(s.st + slot0);
-                const int32_t li = slot0 - lo * kSlice;
+                const int32_t li = (int32_t)SNP_IDX(s.flags, 2, slot0 - lo * kSlice, tl.acc_words - 3);
                 in4 = *reinterpret_cast<const uint4*>(acc + li);
                 uint4 pv = make_uint4(0u, 0u, 0u, 0u);
                 if (push) {

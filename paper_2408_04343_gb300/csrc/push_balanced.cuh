@@ -56,7 +56,8 @@ __device__ __forceinline__ int32_t warp_last_le(const int32_t* __restrict__ ptr,
 template <int U, class Src>
 __device__ __forceinline__ void push_scatter_balanced(const Src& src, const int32_t* __restrict__ ptr, int32_t nslices,
                                                       const typename Src::Ent* __restrict__ ent, int32_t* C,
-                                                      const uint32_t* __restrict__ st, uint32_t* overflow_flag) {
+                                                      const uint32_t* __restrict__ st, uint32_t* flags, int32_t q) {
+    uint32_t* overflow_flag = flags + kFlagOverflow;
     using Ent = typename Src::Ent;
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -80,6 +81,7 @@ __device__ __forceinline__ void push_scatter_balanced(const Src& src, const int3
                 for (int u = 0; u < U; ++u) {
                     const Ent e = v != 0 ? __ldg(p + (size_t)(col + u) * kSlice) : src.pad();
                     tg[u] = src.target(e);
+                    if (tg[u] >= 0) tg[u] = (int32_t)SNP_IDX(flags, 3, tg[u], q);
                     amt[u] = src.amount(e, v);
                 }
 #pragma unroll
@@ -98,6 +100,7 @@ __device__ __forceinline__ void push_scatter_balanced(const Src& src, const int3
             for (; col < stop; ++col) {
                 const Ent e = v != 0 ? __ldg(p + (size_t)col * kSlice) : src.pad();
                 int32_t tg = src.target(e);
+                if (tg >= 0) tg = (int32_t)SNP_IDX(flags, 3, tg, q);
                 if (tg >= 0 && (__ldg(st + tg) >> kPendShift) != 0u) tg = -1;
                 const unsigned grp = __match_any_sync(0xffffffffu, tg);
                 const unsigned add = __reduce_add_sync(grp, tg >= 0 ? (unsigned)src.amount(e, v) : 0u);

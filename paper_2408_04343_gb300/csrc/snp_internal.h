@@ -34,7 +34,8 @@ enum Flag : int {
     kFlagTimeout = 5,  // a bounded wait gave up
     kFlagChoice = 6,   // a forced choice index was out of range (snp_set_choices)
     kFlagImport = 7,   // smallest neuron whose imported state is invalid (snp_set_state)
-    kNumFlags = 8
+    kFlagBounds = 8,   // bounds-checked builds: bit per site of an out-of-range index (SNP_IDX)
+    kNumFlags = 9
 };
 // Device step counters of one system (uint64).
 enum StepWord : int {

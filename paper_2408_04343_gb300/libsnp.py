@@ -126,7 +126,9 @@ _lock = threading.Lock()
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the bounds-checked debug build when
+    SNP_CHECK_BOUNDS=1 is set, else the release build."""
+    return _build.CHECK_LIB if os.environ.get("SNP_CHECK_BOUNDS") == "1" else _build.LIB
 
 
 def load():
