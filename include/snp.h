@@ -45,7 +45,7 @@ extern "C" {
 #define SNP_ERR_UNSUPPORTED 7 /* option combination not available          */
 
 /* ---- options ----------------------------------------------------------- */
-/* Representation of the transition matrix (Sec. 3):
+/* Representation of the transition matrix (Sec. 4):
  *   SNP_FORM_OPT   -- the "Compressed"/"optimized" form: rule vector with
  *                     (c, p) per rule plus per-neuron synapse lists;
  *   SNP_FORM_ELL   -- the ELL form: per-rule columns of (neuron, value);
@@ -218,7 +218,7 @@ int snp_step(snp_system* sys, int64_t n, int64_t* steps_done);
 /* C_k: spikes per neuron, out[q].                                          */
 int snp_get_config(const snp_system* sys, int32_t* out, int64_t len);
 /* S_k of the last executed step: per neuron the global id of the rule it
- * selected at that step, or -1 (Sec. 3, the Compressed spiking vector of
+ * selected at that step, or -1 (Sec. 4, the Compressed spiking vector of
  * length q with 0-based rule ids).  All -1 before the first step.         */
 int snp_get_spiking(const snp_system* sys, int32_t* out, int64_t len);
 /* D_k: per neuron the number of steps before it reopens, 0 = open (Sec. 2,

@@ -6,7 +6,7 @@
 // its delay ran out), stored as bytes, double-buffered by step parity.
 //
 //  * ELL pull: each target neuron sums Em_k[r] * p over the (rule, p) pairs
-//    of its in-ELL column (the transpose of M^s_Pi's +p rows, Sec. 3);
+//    of its in-ELL column (the transpose of M^s_Pi's +p rows, Sec. 4);
 //  * ELL push: each emitting rule walks its column of M^s_Pi and adds p into
 //    every open target with warp-aggregated atomics (Alg. 4's direction),
 //    the columns dealt to warps in equal runs (push_balanced.cuh);

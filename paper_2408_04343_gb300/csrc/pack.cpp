@@ -11,7 +11,7 @@
 //  * in-lists (pull): sliced ELL.  Slots are grouped by 32 (one warp); a slice
 //    stores its in-neighbour columns column-major, padded to the widest list
 //    in the slice with the dummy slot q (whose emission is always 0).  This is
-//    the transpose of the paper's synapse matrix Sy_Pi (Sec. 3) cut into
+//    the transpose of the paper's synapse matrix Sy_Pi (Sec. 4) cut into
 //    warp-sized slices;
 //  * out-lists (push): the paper's Sy_Pi in the same sliced layout, padded
 //    with -1 (the null entry that ends a column in Alg. 5).

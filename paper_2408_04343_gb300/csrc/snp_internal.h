@@ -191,7 +191,7 @@ struct TiledPack {
     std::vector<int32_t> cta_lo;  // [G/P + 1] first slice of each range
 };
 
-// Layouts of the ELL form (Sec. 3, M^s_Pi: a column per rule of (neuron,
+// Layouts of the ELL form (Sec. 4, M^s_Pi: a column per rule of (neuron,
 // value) pairs) and of the uncompressed "Sparse" form (Table 1, M_Pi).
 // Rule ids are slot-order ids (rule_off[slot] + local index).  The
 // consumption pair (-c, own neuron) of M^s_Pi's row 0 is not stored: with
