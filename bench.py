@@ -265,6 +265,13 @@ def main():
     stream.synchronize()
     t_pack = (time.perf_counter() - t_pack) / max(1, args.replicas)
     foot = sum(s.info().device_bytes for s in systems)
+    inf0 = systems[0].info()
+    shape = ({"clusters": inf0.tiled_ctas // max(1, inf0.tiled_partitions),
+              "ctas_per_cluster": inf0.tiled_partitions, "threads_per_cta": 1024,
+              "entry_layout": ["target words", "paired target words", "run-length"][inf0.tiled_layout],
+              "accumulator_bits": inf0.tiled_acc_bits, "smem_bytes_per_cta": inf0.tiled_smem_bytes,
+              "emission_bits": inf0.e_bits, "entry_bytes": inf0.in_entries * 4}
+             if inf0.engine == libsnp.SNP_ENGINE_TILED else None)
     for i in range(args.warmup):
         systems[i % len(systems)].step(T, wait=False)
     stream.synchronize()
@@ -291,7 +298,7 @@ def main():
     value = work / t_max
     # launches of this library per call on this workload: begin, select,
     # T-1 fused steps (plus one advance per captured chunk of 48), gather,
-    # finish -- the tiled engine's one-launch step (two source partitions)
+    # finish -- the tiled engine's one-launch step (clusters of P <= 8 CTAs)
     per_call = 4 + (T - 1) + (T - 1) // 48
     launches = per_call * args.steps
 
@@ -348,7 +355,7 @@ def main():
                              f"stepped round-robin", "parallelism": f"replicas x{ws}",
                        "q": desc.q, "num_syn": desc.num_syn, "snp_steps_timed": int(executed),
                        "snp_steps_per_s": work / desc.num_syn / t_max if t_max > 0 else None,
-                       "create_seconds_per_system": round(t_pack, 3)},
+                       "create_seconds_per_system": round(t_pack, 3), "launch_shape": shape},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": {"tiled": "k_tiled_step (one launch per SNP step: gather, then select in thread-block clusters; achieved = a step's algorithmic bytes / its live device time)",

@@ -210,9 +210,15 @@ def skewed(args, libsnp, synth):
         t0 = time.perf_counter()
         done = g.step(nsteps)
         dt = time.perf_counter() - t0
+        inf = g.info()
         res[name] = {"syn_updates_per_s": d.num_syn * done / dt, "us_per_step": dt / max(done, 1) * 1e6,
-                     "device_mb": g.info().device_bytes / 1e6,
-                     "engine": {1: "l2_gather", 2: "resident", 3: "tiled"}.get(g.info().engine, "?")}
+                     "device_mb": inf.device_bytes / 1e6,
+                     "engine": {1: "l2_gather", 2: "resident", 3: "tiled"}.get(inf.engine, "?")}
+        if inf.engine == libsnp.SNP_ENGINE_TILED:
+            res[name]["launch_shape"] = {"clusters": inf.tiled_ctas // max(1, inf.tiled_partitions),
+                                         "ctas_per_cluster": inf.tiled_partitions,
+                                         "accumulator_bits": inf.tiled_acc_bits,
+                                         "smem_bytes_per_cta": inf.tiled_smem_bytes}
         g.close()
     dd, _, _ = synth.skewed_dense_copy()
     g = libsnp.System(dd, form=libsnp.SNP_FORM_DENSE, select=libsnp.SNP_SELECT_PHILOX, seed=dd.seed)

@@ -190,6 +190,13 @@ typedef struct snp_info {
                              /* applicability record per neuron instead    */
                              /* of testing each rule (Compressed form with */
                              /* at most 4 small rules per neuron)          */
+    /* The tiled engine's launch shape (all 0 when the system has none):   */
+    int32_t tiled_partitions; /* source partitions P = CTAs per cluster    */
+    int32_t tiled_ctas;       /* CTAs of one step launch (ranges x P)      */
+    int32_t tiled_layout;     /* in-edge entries: 0 target words, 1 paired */
+                              /* target words, 2 run-length entries        */
+    int32_t tiled_acc_bits;   /* width of the in-flow accumulators: 8, 32  */
+    int64_t tiled_smem_bytes; /* dynamic shared memory per CTA            */
 } snp_info;
 
 typedef struct snp_system snp_system;

@@ -548,6 +548,10 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
         s->tiled_smem = tiled_smem_bytes(im.tp);
         s->tiled_entries = (int64_t)im.tp.ent.size();
         s->tiled_threads = kTiledThreads;  // fixed: the entry layout is dealt to this many threads
+        s->tiled_P = im.tp.P;
+        s->tiled_G = im.tp.G;
+        s->tiled_layout = im.tp.rle ? 2 : (im.tp.pairs ? 1 : 0);
+        s->tiled_acc_bits = im.tp.acc8 ? 8 : 32;
     }
     {
         std::vector<Piece> plan;
@@ -886,6 +890,13 @@ int snp_get_info(const snp_system* s, snp_info* info) {
     info->e_bits = info->engine == SNP_ENGINE_TILED ? s->tiled.e_bits : resident_e_bits(s->max_p);
     info->step = s->host_step;
     info->compiled_rules = s->compiled ? 1 : 0;
+    if (s->has_tiled) {
+        info->tiled_partitions = s->tiled_P;
+        info->tiled_ctas = s->tiled_G;
+        info->tiled_layout = s->tiled_layout;
+        info->tiled_acc_bits = s->tiled_acc_bits;
+        info->tiled_smem_bytes = (int64_t)s->tiled_smem;
+    }
     return SNP_OK;
 }
 

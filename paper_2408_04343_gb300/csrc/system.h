@@ -74,6 +74,7 @@ struct snp_system {
     size_t tiled_smem = 0;
     int64_t tiled_entries = 0;
     int32_t tiled_threads = 1024;
+    int32_t tiled_P = 0, tiled_G = 0, tiled_layout = 0, tiled_acc_bits = 0;  // launch shape (snp_get_info)
     // ELL and dense forms
     snp::EllSys ell{};
     // deferred upload

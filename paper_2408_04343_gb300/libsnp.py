@@ -57,7 +57,8 @@ class snp_info(ct.Structure):
                 ("in_entries", ct.c_int64), ("out_entries", ct.c_int64), ("rule_words", ct.c_int64),
                 ("device_bytes", ct.c_int64), ("max_rules", ct.c_int32), ("max_p", ct.c_int32),
                 ("compact_rules", ct.c_int32), ("e_bits", ct.c_int32), ("step", ct.c_uint64),
-                ("compiled_rules", ct.c_int32)]
+                ("compiled_rules", ct.c_int32), ("tiled_partitions", ct.c_int32), ("tiled_ctas", ct.c_int32),
+                ("tiled_layout", ct.c_int32), ("tiled_acc_bits", ct.c_int32), ("tiled_smem_bytes", ct.c_int64)]
 
 
 class snp_device_system(ct.Structure):
