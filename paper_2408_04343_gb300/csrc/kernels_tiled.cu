@@ -27,6 +27,8 @@
 // Same status word, fixed-point test and activity words as k_step_pull.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -584,6 +586,87 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t a, const uint4& v) {
 //    before its remote stores.
 //  * Otherwise the select phase reads the other CTAs' accumulators through
 //    distributed shared memory between two cluster barriers.
+// ---- the select phase of four consecutive slots of one lane -------------
+// Same results as select_compiled, slot by slot, for systems with compiled
+// rule records: finishes step k for the four slots (an open neuron receives
+// its in-flow; a count above INT32_MAX is clamped and reported in ovf) and
+// selects step k+1.  Written for instruction count, since the select phase
+// issues most of the fused step's instructions outside the gather:
+//  * the applicability mask is one table lookup: entry e of the record's
+//    fourteen 4-bit masks sits in word x (e < 8) or y (e >= 8) at bit
+//    4e mod 32, so one rotate of the right word finds it;
+//  * the chosen rule's 16-bit (c, p, d) field is taken with one byte
+//    permute of words z and w;
+//  * Philox runs only for slots with two or more applicable rules, one such
+//    slot per lane per round, as many rounds as the warp's busiest lane
+//    needs (all 32 lanes call this together: the loop is warp-uniform).
+// Slots past the system's end arrive as c = 0, st = 0, in = 0 and a zero
+// record: an open neuron with no applicable rule, which changes nothing.
+// The lane's 4 x EB emission bits are returned in packed (slot j at EB * j).
+template <int SEL, int EB, typename PT>
+__device__ __forceinline__ void select_quad(const uint4 (&rec)[4], int4& c4, uint4& st4, const uint4& in4,
+                                            const uint4& nid4, const PhiloxHead& ph, const uint32_t* rk,
+                                            const uint2* __restrict__ tab, const uint8_t* __restrict__ pick,
+                                            int4& s4, PT& packed, bool& active, bool& dirty, bool& ovf) {
+    uint32_t mask[4], need = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t st = (&st4.x)[j];
+        const bool closed = (st >> kPendShift) != 0u;
+        const uint32_t nc = (uint32_t)(&c4.x)[j] + (&in4.x)[j];
+        ovf |= !closed && nc > 2147483647u;
+        const uint32_t n = closed ? (uint32_t)(&c4.x)[j] : min(nc, 2147483647u);
+        (&c4.x)[j] = (int32_t)n;
+        const uint32_t y = rec[j].y, K = (y >> 24) & 15u, L = y >> 28;
+        const uint32_t x = n - K;
+        const uint2 mg = tab[L];
+        const uint32_t r = x - (__umulhi(x, mg.x) >> mg.y) * L;  // x mod L when n >= K and L >= 2
+        const uint32_t e = n < K ? n : K + (L > 1u ? r : 0u);
+        const uint32_t w = e < 8u ? rec[j].x : y;
+        mask[j] = closed ? 0u : __funnelshift_r(w, w, 4u * e) & 15u;
+        if (SEL == SNP_SELECT_PHILOX) need |= ((mask[j] & (mask[j] - 1u)) != 0u ? 1u : 0u) << j;
+    }
+    uint32_t x0[4] = {0u, 0u, 0u, 0u};
+    if (SEL == SNP_SELECT_PHILOX) {
+        while (__any_sync(0xffffffffu, need != 0u)) {
+            const uint32_t j = need ? (uint32_t)__ffs(need) - 1u : 0u;
+            const uint32_t nid = j == 0u ? nid4.x : j == 1u ? nid4.y : j == 2u ? nid4.z : nid4.w;
+            const uint32_t v = philox_x0(ph, nid, rk);
+            x0[0] = (need & 1u) ? v : x0[0];
+            x0[1] = (need & 3u) == 2u ? v : x0[1];
+            x0[2] = (need & 7u) == 4u ? v : x0[2];
+            x0[3] = need == 8u ? v : x0[3];
+            need &= need - 1u;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t st = (&st4.x)[j];
+        const uint32_t pend = st >> kPendShift;
+        const bool closed = pend != 0u;
+        const bool completing = closed && (st & kDMask) == 0u;
+        const uint32_t m = mask[j];
+        const bool selected = m != 0u;
+        const uint32_t idx = SEL == SNP_SELECT_PHILOX && (m & (m - 1u)) != 0u
+                                 ? (uint32_t)(((unsigned long long)x0[j] * (uint32_t)__popc(m)) >> 32)
+                                 : 0u;  // < popc <= 4
+        const uint32_t t = pick[m | (idx << 4)];
+        const uint32_t fi = completing ? pend - 1u : t;
+        const uint32_t f = __byte_perm(rec[j].z, rec[j].w, fi * 0x22u + 0x10u);  // bytes 2fi, 2fi+1
+        const uint32_t c = f & 63u, p = (f >> 6) & 31u, d = (f >> 11) & 31u;
+        const int32_t n = (&c4.x)[j];
+        (&s4.x)[j] = selected ? (int32_t)t : -1;
+        (&c4.x)[j] = selected ? n - (int32_t)c : n;
+        const uint32_t emit = (completing || (selected && d == 0u)) ? p : 0u;
+        const uint32_t nst = closed ? (completing ? 0u : st - 1u)
+                                    : ((selected && d > 0u) ? ((t + 1u) << kPendShift) | (d - 1u) : 0u);
+        active |= closed || selected;
+        dirty |= nst != st;
+        (&st4.x)[j] = nst;
+        packed |= (PT)emit << (EB * j);
+    }
+}
+
 template <int EB, int LAYOUT, int SEL>
 __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, int32_t t, int select, int compact) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -732,40 +815,66 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
                 in4.z += pv.z;
                 in4.w += pv.w;
             }
-            unsigned long long packed = 0ull;
+            using PT = typename std::conditional<EB == 16, unsigned long long, uint32_t>::type;
+            PT packed = 0u;
             int4 s4 = make_int4(-1, -1, -1, -1);
             bool dirty = false, ovf = false;
+            if (has_rec && select) {  // warp-uniform
+                const int32_t nv = qend - slot0;  // the lane's slots inside the system (<= 0: none)
+                uint4 rq[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int32_t slot = slot0 + j;
-                const bool v = slot < qend;
-                int32_t c = (&c4.x)[j];
-                const uint32_t st = (&st4.x)[j];
-                // an open neuron receives; a count above INT32_MAX is clamped
-                // and reported
-                const uint32_t nc = (uint32_t)c + (&in4.x)[j];
-                const bool open = v && (st >> kPendShift) == 0u;
-                ovf |= open && nc > 2147483647u;
-                c = open ? (int32_t)min(nc, 2147483647u) : c;
-                if (select && v) {
-                    const uint32_t nid = neuron_id(s, slot);
-                    SelOut o;
-                    if (has_rec)
-                        o = select_rec_flat<SEL>(__ldg(rp + j), c, st, nid, phx, s.philox_rk, s_mod, s_pick);
-                    else if (compact)
-                        o = select_neuron<true, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks, nid,
-                                                     s.seed);
-                    else
-                        o = select_neuron<false, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks, nid,
-                                                      s.seed);
-                    c = o.c_after;
-                    active |= o.active;
-                    packed |= (unsigned long long)(uint32_t)o.emit << (EB * j);
-                    (&s4.x)[j] = o.s;
-                    dirty |= o.st != st;
-                    (&st4.x)[j] = o.st;
+                for (int j = 0; j < 4; ++j) rq[j] = j < nv ? __ldg(rp + j) : make_uint4(0u, 0u, 0u, 0u);
+                if (nv < 4) {  // the system's last quad, or past its end
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (j >= nv) {
+                            (&c4.x)[j] = 0;
+                            (&st4.x)[j] = 0u;
+                            (&in4.x)[j] = 0u;
+                        }
+                    }
                 }
-                (&c4.x)[j] = c;
+                uint4 nid4 = make_uint4((uint32_t)slot0, (uint32_t)slot0 + 1u, (uint32_t)slot0 + 2u,
+                                        (uint32_t)slot0 + 3u);
+                if (!s.identity) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) (&nid4.x)[j] = j < nv ? (uint32_t)__ldg(s.orig + slot0 + j) : 0u;
+                }
+                select_quad<SEL, EB, PT>(rq, c4, st4, in4, nid4, phx, s.philox_rk, s_mod, s_pick, s4, packed,
+                                         active, dirty, ovf);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int32_t slot = slot0 + j;
+                    const bool v = slot < qend;
+                    int32_t c = (&c4.x)[j];
+                    const uint32_t st = (&st4.x)[j];
+                    // an open neuron receives; a count above INT32_MAX is clamped
+                    // and reported
+                    const uint32_t nc = (uint32_t)c + (&in4.x)[j];
+                    const bool open = v && (st >> kPendShift) == 0u;
+                    ovf |= open && nc > 2147483647u;
+                    c = open ? (int32_t)min(nc, 2147483647u) : c;
+                    if (select && v) {
+                        const uint32_t nid = neuron_id(s, slot);
+                        SelOut o;
+                        if (has_rec)
+                            o = select_rec_flat<SEL>(__ldg(rp + j), c, st, nid, phx, s.philox_rk, s_mod, s_pick);
+                        else if (compact)
+                            o = select_neuron<true, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks, nid,
+                                                         s.seed);
+                        else
+                            o = select_neuron<false, SEL>(s.rules, rule_lo(s, slot), rule_hi(s, slot), c, st, ks, nid,
+                                                          s.seed);
+                        c = o.c_after;
+                        active |= o.active;
+                        packed |= (PT)(uint32_t)o.emit << (EB * j);
+                        (&s4.x)[j] = o.s;
+                        dirty |= o.st != st;
+                        (&st4.x)[j] = o.st;
+                    }
+                    (&c4.x)[j] = c;
+                }
             }
             if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(s.flags + kFlagOverflow, 1u);
             if (live) {
