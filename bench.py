@@ -235,6 +235,8 @@ def main():
                          "launch vs the plain per-system loop; serve: Poisson request loop; skewed: the "
                          "2M-neuron power-law system and its 16,384-neuron dense copy")
     ap.add_argument("--batch-count", type=int, default=8192)
+    ap.add_argument("--skewed-engines", default="all",
+                    help="skewed workload: comma list of auto,tiled,l2_gather,push,ell_pull,ell_push,dense")
     ap.add_argument("--rates", default="10,30,100,300,1000,3000,10000")
     ap.add_argument("--requests", type=int, default=1000)
     args = ap.parse_args()

@@ -194,12 +194,15 @@ def skewed(args, libsnp, synth):
     import torch
     d, nsteps, mode = synth.skewed_2m()
     res = {}
+    chosen = None if args.skewed_engines in (None, "all") else set(args.skewed_engines.split(","))
     for name, kw in [("auto", dict(engine=libsnp.SNP_ENGINE_AUTO)),
                      ("tiled", dict(engine=libsnp.SNP_ENGINE_TILED)),
                      ("l2_gather", dict(engine=libsnp.SNP_ENGINE_LAUNCH)),
                      ("push", dict(prop=libsnp.SNP_PROP_PUSH)),
                      ("ell_pull", dict(form=libsnp.SNP_FORM_ELL)),
                      ("ell_push", dict(form=libsnp.SNP_FORM_ELL, prop=libsnp.SNP_PROP_PUSH))]:
+        if chosen is not None and name not in chosen:
+            continue
         try:
             g = libsnp.System(d, select=libsnp.SNP_SELECT_PHILOX, seed=d.seed, **kw)
         except libsnp.SnpError as e:
@@ -220,6 +223,11 @@ def skewed(args, libsnp, synth):
                                          "accumulator_bits": inf.tiled_acc_bits,
                                          "smem_bytes_per_cta": inf.tiled_smem_bytes}
         g.close()
+    if chosen is not None and "dense" not in chosen:
+        return {"metric": "synaptic updates/s", "workload": "skewed", "value": next(
+                    (r.get("syn_updates_per_s") for r in res.values() if "syn_updates_per_s" in r), None),
+                "unit": "synaptic updates/s", "engines": res,
+                "config": {"q": d.q, "num_syn": d.num_syn, "steps": nsteps, "engines_run": sorted(chosen)}}
     dd, _, _ = synth.skewed_dense_copy()
     g = libsnp.System(dd, form=libsnp.SNP_FORM_DENSE, select=libsnp.SNP_SELECT_PHILOX, seed=dd.seed)
     g.step(2)

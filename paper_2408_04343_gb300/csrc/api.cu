@@ -410,6 +410,51 @@ int run_steps(snp_system* s, int64_t n) {
     return eng == SNP_ENGINE_RESIDENT ? step_resident(s, n) : step_launch_engine(s, n);
 }
 
+// The launches of a pull call of n steps on a grid-wide engine, as
+// step_launch_engine issues them but without its chunk graph (so without
+// the base step's advances, which only bound the step index of the chunk
+// graph's launches): begin, the first select, n - 1 fused steps, the last
+// gather, finish.  Every parameter is a constant of the call, so the
+// sequence can be captured once and replayed.
+static cudaError_t enqueue_pull_call(snp_system* s, int64_t n, cudaStream_t st) {
+    cudaError_t e = launch_begin(s->dev, st);
+    if (e == cudaSuccess) e = launch_pull_any(s, kPullSelectOnly, 0, st);
+    for (int64_t t = 0; t < n - 1 && e == cudaSuccess; ++t) e = launch_pull_any(s, kPullFused, (int32_t)t, st);
+    if (e == cudaSuccess) e = launch_pull_any(s, kPullGatherOnly, (int32_t)(n - 1), st);
+    if (e == cudaSuccess) e = launch_finish(s->dev, (int32_t)n, st);
+    return e;
+}
+
+int run_steps_graphed(snp_system* s, int64_t n) {
+    const int eng = s->opt.form == SNP_FORM_OPT ? effective_engine(s) : SNP_ENGINE_LAUNCH;
+    if (n < 2 || n > kMaxGraphedCall || s->opt.form != SNP_FORM_OPT || s->opt.prop != SNP_PROP_PULL ||
+        eng == SNP_ENGINE_RESIDENT || (eng == SNP_ENGINE_LAUNCH && !s->has_in_lists))
+        return run_steps(s, n);
+    if (!s->call_exec || s->call_n != n) {
+        if (s->call_exec) cudaGraphExecDestroy(s->call_exec);
+        s->call_exec = nullptr;
+        if (!s->cap_stream && cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_fail("stream create");
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return cuda_fail("begin capture");
+        const cudaError_t le = enqueue_pull_call(s, n, s->cap_stream);
+        if (cudaStreamEndCapture(s->cap_stream, &g) != cudaSuccess || le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail("call capture");
+        }
+        const cudaError_t e = cudaGraphInstantiate(&s->call_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            s->call_exec = nullptr;
+            return cuda_fail("graph instantiate");
+        }
+        s->call_n = n;
+    }
+    if (cudaGraphLaunch(s->call_exec, s->stream) != cudaSuccess) return cuda_fail("graph launch");
+    return SNP_OK;
+}
+
 }  // namespace snp
 
 using namespace snp;
@@ -466,8 +511,24 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     HostPack& hp = im.hp;
     bool want_tiled = false, want_in = false;
     plan_layouts(o, desc->q, desc->rule_offsets[desc->q], &want_tiled, &want_in);
-    // the tiled layout needs no in-degree order; without it slots are the caller's neurons
-    const int window = (o.form == SNP_FORM_OPT && o.engine == SNP_ENGINE_TILED) ? 0 : kSortWindow;
+    int dev = 0, sms = 0, optin = 0;
+    if (want_tiled) {
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+            delete s;
+            return cuda_fail("device query");
+        }
+    }
+    // The tiled layout needs no in-degree order; without it slots are the
+    // caller's neurons, and the select reads no slot-to-neuron map.  Under
+    // AUTO the caller's order is kept as well when the system is too large
+    // for one CTA (so no resident in-lists): if no tiled layout fits after
+    // all, the system is packed again in the in-degree order that the
+    // L2-gather engine's in-lists want.
+    const bool auto_large = o.engine == SNP_ENGINE_AUTO && want_tiled &&
+                            resident_smem_bytes(desc->q, 2) + 1024 > (size_t)optin;
+    int window = (o.form == SNP_FORM_OPT && (o.engine == SNP_ENGINE_TILED || auto_large)) ? 0 : kSortWindow;
     st = pack_system(desc, o.form == SNP_FORM_OPT && o.prop == SNP_PROP_PUSH, false, window, &hp);
     if (!st && o.form == SNP_FORM_ELL) st = pack_ell(desc, hp, o.prop == SNP_PROP_PULL, o.prop == SNP_PROP_PUSH, &im.ep);
     if (!st && o.form == SNP_FORM_DENSE) st = pack_dense(desc, hp, &im.dense);
@@ -480,13 +541,6 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
     s->unions = desc->rule_term_offsets != nullptr;
 
     if (want_tiled) {
-        int dev = 0, sms = 0, optin = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
-            delete s;
-            return cuda_fail("device query");
-        }
         // the gather sums a partition's in-flow in 32-bit shared accumulators,
         // read back as int32: a target must not be able to receive more than
         // INT32_MAX spikes from one partition in one step (the int64 sums of
@@ -521,6 +575,15 @@ int snp_create(const snp_desc* desc, const snp_options* opts, snp_system** out) 
             return st;
         } else {
             want_in = true;  // AUTO falls back to the L2-gather engine
+            if (window != kSortWindow) {
+                hp = HostPack();
+                window = kSortWindow;
+                st = pack_system(desc, false, false, window, &hp);
+                if (st) {
+                    delete s;
+                    return st;
+                }
+            }
         }
     }
     if (want_in) pack_in_lists(desc, &hp);
@@ -576,6 +639,7 @@ int snp_destroy(snp_system* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
     if (s->chunk_exec) cudaGraphExecDestroy(s->chunk_exec);
+    if (s->call_exec) cudaGraphExecDestroy(s->call_exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     batch_release(s);
     sys_free_all(s);

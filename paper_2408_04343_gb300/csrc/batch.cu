@@ -328,7 +328,7 @@ static int run_round(snp_batch* b, std::vector<Item*>& items, RoundTimes& tm) {
     std::vector<int64_t> large_n(large.size());
     for (size_t i = 0; i < large.size() && !rc; ++i) {
         large_n[i] = std::min(large[i]->remaining, b->round);
-        rc = run_steps(large[i]->sys, large_n[i]);
+        rc = run_steps_graphed(large[i]->sys, large_n[i]);
     }
     const double t1 = now_s();
     for (auto& g : groups) {

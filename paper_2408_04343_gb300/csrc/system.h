@@ -14,6 +14,7 @@
 namespace snp {
 
 constexpr int kChunk = 48;                 // steps per captured CUDA graph
+constexpr int kMaxGraphedCall = 256;       // longest call run_steps_graphed captures whole
 constexpr int kSortWindow = 8192;          // in-degree sort window (slots)
 constexpr int kAutoResidentMaxQ = 8192;    // AUTO picks the resident engine up to here
 constexpr int64_t kAutoResidentMaxRules = 65536;  // ... and up to this many rules (one CTA does all the work)
@@ -44,6 +45,8 @@ struct snp_system {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t chunk_exec = nullptr;
+    cudaGraphExec_t call_exec = nullptr;  // a whole call of call_n steps (run_steps_graphed)
+    int64_t call_n = 0;
     snp::DevSys dev{};
     snp::DevSys* d_self = nullptr;     // device copy of dev (resident engine)
     long long* d_nsteps = nullptr;
@@ -96,4 +99,8 @@ bool resident_fits(const snp_system* s, ResidentPlan* plan);
 int effective_engine(const snp_system* s);
 int read_flags(snp_system* s, int64_t* exec);
 int run_steps(snp_system* s, int64_t n);
+// The same as run_steps, for callers that run calls of one length again and
+// again (the batch's rounds): a pull call on a grid-wide engine is captured
+// once as one graph and replayed, one launch instead of one per step.
+int run_steps_graphed(snp_system* s, int64_t n);
 }  // namespace snp
