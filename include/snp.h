@@ -64,10 +64,12 @@ extern "C" {
  *   SNP_SELECT_FIRST  -- the lowest-index applicable rule (the paper's
  *                        deterministic choice);
  *   SNP_SELECT_PHILOX -- uniform over the applicable rules, drawn from
- *                        Philox4x32-10 (Salmon et al., SC'11) at counter
- *                        (k mod 2^32, i, k >> 32, 0) and key (seed mod 2^32,
- *                        seed >> 32) for step k and neuron i: the index into
- *                        the applicable list is floor(x0 * |A| / 2^32).    */
+ *                        Philox4x32-10 (Salmon et al., SC'11): the four
+ *                        words of the block at counter (k mod 2^32, i / 4,
+ *                        k >> 32, 0) and key (seed mod 2^32, seed >> 32)
+ *                        serve neurons 4(i / 4) .. 4(i / 4) + 3 at step k,
+ *                        neuron i taking word x = word i mod 4; the index
+ *                        into the applicable list is floor(x |A| / 2^32). */
 #define SNP_SELECT_FIRST 0
 #define SNP_SELECT_PHILOX 1
 /* How snp_step runs its steps:

@@ -101,6 +101,20 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
+/* The uniform choice of SAMPLE_ONE (Sec. 5: one of the a applicable rules,
+ * each equally likely).  The paper does not fix the generator; this library's
+ * reading: the four 32-bit words of the Philox4x32-10 block at counter
+ * (step mod 2^32, i / 4, step >> 32, 0) and key (seed mod 2^32, seed >> 32)
+ * belong to the four neurons 4(i / 4) .. 4(i / 4) + 3, neuron i taking word
+ * i mod 4, and the pick is floor(word * a / 2^32) (an index 0 .. a-1). */
+static int64_t orc_philox_pick(uint64_t step, int64_t i, uint64_t seed, int64_t a) {
+    uint32_t ctr[4] = {(uint32_t)step, (uint32_t)(i / 4), (uint32_t)(step >> 32), 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    return (int64_t)(((uint64_t)x[i % 4] * (uint64_t)a) >> 32);
+}
+
 /* The system as the user describes it (Sec. 5, "Initialization"). */
 typedef struct {
     int32_t q;
@@ -203,11 +217,7 @@ int orc_step(const orc_sys* s, int32_t* C, int32_t* D, int32_t* P, uint64_t step
             if (a == 0) continue;
             int64_t pick = 0;
             if (mode == ORC_PHILOX) {
-                uint32_t ctr[4] = {(uint32_t)step, (uint32_t)i, (uint32_t)(step >> 32), 0u};
-                uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-                uint32_t x[4];
-                orc_philox4x32_10(ctr, key, x);
-                pick = (int64_t)(((uint64_t)x[0] * (uint64_t)a) >> 32);
+                pick = orc_philox_pick(step, i, seed, a);
             } else if (mode == ORC_FORCED) {
                 pick = forced[i];
                 if (pick < 0 || pick >= a) {
@@ -287,11 +297,7 @@ int orc_range_select(const orc_sys* s, int32_t lo, int32_t hi, int32_t* C, int32
             *active = 1;
             int64_t pick = 0;
             if (mode == ORC_PHILOX) {
-                uint32_t ctr[4] = {(uint32_t)step, (uint32_t)i, (uint32_t)(step >> 32), 0u};
-                uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-                uint32_t x[4];
-                orc_philox4x32_10(ctr, key, x);
-                pick = (int64_t)(((uint64_t)x[0] * (uint64_t)a) >> 32);
+                pick = orc_philox_pick(step, i, seed, a);
             } else if (mode != ORC_FIRST) {
                 return ORC_ERR_INVALID;
             }
@@ -429,11 +435,7 @@ int orc_run_pull(const orc_sys* s, const int64_t* in_off, const int32_t* in_src,
                 if (a == 0) continue;
                 int64_t pick = 0;
                 if (mode == ORC_PHILOX) {
-                    uint32_t ctr[4] = {(uint32_t)step, (uint32_t)i, (uint32_t)(step >> 32), 0u};
-                    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-                    uint32_t x[4];
-                    orc_philox4x32_10(ctr, key, x);
-                    pick = (int64_t)(((uint64_t)x[0] * (uint64_t)a) >> 32);
+                    pick = orc_philox_pick(step, i, seed, a);
                 }
                 const int64_t r = orc_nth_applicable(s, i, n, pick);
                 Sk[i] = (int32_t)r;

@@ -96,6 +96,25 @@ __device__ __forceinline__ Philox4 philox4x32_10_rk(uint32_t c0, uint32_t c1, ui
     return out;
 }
 
+// The uniform 32-bit word a neuron draws its choice from (SAMPLE_ONE of
+// Sec. 5 picks uniformly among the applicable rules; the generator is this
+// library's choice): the four words of one Philox4x32-10 block at counter
+// (k mod 2^32, nid / 4, k >> 32, 0) go to the four neurons 4(nid / 4) ..
+// 4(nid / 4) + 3, neuron nid taking word nid mod 4 -- so four consecutive
+// neurons can share one evaluation.
+__device__ __forceinline__ uint32_t philox_word_of(const Philox4& x, uint32_t nid) {
+    const uint32_t j = nid & 3u;
+    return j == 0u ? x.v[0] : j == 1u ? x.v[1] : j == 2u ? x.v[2] : x.v[3];
+}
+__device__ __forceinline__ uint32_t philox_draw(unsigned long long k, uint32_t nid, uint64_t seed) {
+    return philox_word_of(philox4x32_10((uint32_t)k, nid >> 2, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
+                                        (uint32_t)(seed >> 32)),
+                          nid);
+}
+__device__ __forceinline__ uint32_t philox_draw_rk(unsigned long long k, uint32_t nid, const uint32_t* rk) {
+    return philox_word_of(philox4x32_10_rk((uint32_t)k, nid >> 2, (uint32_t)(k >> 32), 0u, rk), nid);
+}
+
 // ---- rules ----------------------------------------------------------------
 struct RuleF {
     int32_t k, j, c, p, d;
@@ -258,9 +277,8 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
         if (mask == 0u) return o;
         if (SEL == SNP_SELECT_PHILOX && (mask & (mask - 1u)) != 0u) {
             const int32_t cnt = __popc(mask);
-            const Philox4 x = philox4x32_10((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
-                                            (uint32_t)(seed >> 32));
-            int32_t idx = (int32_t)(((unsigned long long)x.v[0] * (unsigned long long)cnt) >> 32);
+            const uint32_t x = philox_draw(k, nid, seed);
+            int32_t idx = (int32_t)(((unsigned long long)x * (unsigned long long)cnt) >> 32);
             for (; idx > 0; --idx) mask &= mask - 1u;
         }
         const int32_t t = __ffs(mask) - 1;  // FIRST: the lowest applicable rule
@@ -292,9 +310,8 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
         if (cnt == 1) {
             pick = r0 + __ffs(mask) - 1;
         } else if (cnt > 1) {
-            const Philox4 x = philox4x32_10((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
-                                            (uint32_t)(seed >> 32));
-            int32_t idx = (int32_t)(((unsigned long long)x.v[0] * (unsigned long long)cnt) >> 32);
+            const uint32_t x = philox_draw(k, nid, seed);
+            int32_t idx = (int32_t)(((unsigned long long)x * (unsigned long long)cnt) >> 32);
             for (; idx > 0; --idx) mask &= mask - 1u;  // drop the lowest set bits
             pick = r0 + __ffs(mask) - 1;
         }
@@ -309,9 +326,8 @@ __device__ __forceinline__ SelOut select_neuron(const uint32_t* __restrict__ rul
         if (cnt == 1) {
             pick = first;
         } else if (cnt > 1) {
-            const Philox4 x = philox4x32_10((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
-                                            (uint32_t)(seed >> 32));
-            int32_t idx = (int32_t)(((unsigned long long)x.v[0] * (unsigned long long)cnt) >> 32);
+            const uint32_t x = philox_draw(k, nid, seed);
+            int32_t idx = (int32_t)(((unsigned long long)x * (unsigned long long)cnt) >> 32);
             for (int32_t r = first; r < r1; ++r) {
                 if (rule_applies_at<COMPACT>(rules, r, n)) {
                     if (idx == 0) {
@@ -426,10 +442,8 @@ __device__ __forceinline__ SelOut select_compiled(const uint4 rec, int32_t n, ui
     if (mask == 0u) return o;
     if (SEL == SNP_SELECT_PHILOX && (mask & (mask - 1u)) != 0u) {
         const uint32_t cnt = (uint32_t)__popc(mask);
-        const Philox4 x = RK ? philox4x32_10_rk((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, rk)
-                             : philox4x32_10((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, (uint32_t)seed,
-                                             (uint32_t)(seed >> 32));
-        const uint32_t idx = (uint32_t)(((unsigned long long)x.v[0] * cnt) >> 32);  // < cnt <= 4
+        const uint32_t x = RK ? philox_draw_rk(k, nid, rk) : philox_draw(k, nid, seed);
+        const uint32_t idx = (uint32_t)(((unsigned long long)x * cnt) >> 32);  // < cnt <= 4
         // drop the idx lowest set bits, without a loop
         mask = idx > 0u ? mask & (mask - 1u) : mask;
         mask = idx > 1u ? mask & (mask - 1u) : mask;
@@ -464,8 +478,8 @@ __device__ __forceinline__ SelOut select_compiled_flat(const uint4 rec, int32_t 
         const bool draw = (mask & (mask - 1u)) != 0u;
         if (__any_sync(__activemask(), draw)) {
             const uint32_t cnt = (uint32_t)__popc(mask);
-            const Philox4 x = philox4x32_10_rk((uint32_t)k, nid, (uint32_t)(k >> 32), 0u, rk);
-            uint32_t idx = draw ? (uint32_t)(((unsigned long long)x.v[0] * cnt) >> 32) : 0u;  // < cnt <= 4
+            const uint32_t x = philox_draw_rk(k, nid, rk);
+            uint32_t idx = draw ? (uint32_t)(((unsigned long long)x * cnt) >> 32) : 0u;  // < cnt <= 4
             mask = idx > 0u ? mask & (mask - 1u) : mask;
             mask = idx > 1u ? mask & (mask - 1u) : mask;
             mask = idx > 2u ? mask & (mask - 1u) : mask;
@@ -486,14 +500,15 @@ __device__ __forceinline__ SelOut select_compiled_flat(const uint4 rec, int32_t 
 }
 
 // ---- the select of one slot from its compiled record, for the fused step --
-// Philox4x32-10 at counter (k mod 2^32, nid, k >> 32, 0): only word 1 of the
-// counter (the neuron) differs between the neurons of one step, so in rounds
-// 1 to 3 most products and XORs are the same for every neuron.  PhiloxHead
-// holds those parts (computed once per step), philox_x0 finishes the ten
-// rounds from them and returns output word 0 -- the same value as
-// philox4x32_10_rk(k, nid, k >> 32, 0, rk).v[0].
+// Philox4x32-10 at counter (k mod 2^32, g, k >> 32, 0), g = nid / 4: only
+// word 1 of the counter (the block) differs between the blocks of one step,
+// so in rounds 1 to 3 most products and XORs are the same for every block.
+// PhiloxHead holds those parts (computed once per step), philox_block
+// finishes the ten rounds from them -- the same words as
+// philox4x32_10_rk(k, g, k >> 32, 0, rk) -- and philox_word takes neuron
+// nid's word of its block (philox_draw_rk's value).
 struct PhiloxHead {
-    uint32_t u1;    // round 1: c0 = u1 ^ nid
+    uint32_t u1;    // round 1: c0 = u1 ^ g
     uint32_t u4k;   // round 2: c2 = hi(A c0) ^ u4k
     uint32_t u6k;   // round 3: c0 = hi(B c2) ^ u6k
     uint32_t w;     // round 3: c2 = w ^ lo(A c0 of round 2)
@@ -503,17 +518,17 @@ struct PhiloxHead {
 __device__ __forceinline__ PhiloxHead philox_head(unsigned long long k, const uint32_t* rk) {
     constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
     const uint32_t k0 = (uint32_t)k, k1 = (uint32_t)(k >> 32);
-    // round 1 on (k0, nid, k1, 0)
+    // round 1 on (k0, g, k1, 0)
     const unsigned long long pA1 = (unsigned long long)kMulA * k0, pB1 = (unsigned long long)kMulB * k1;
-    const uint32_t u1 = (uint32_t)(pB1 >> 32) ^ rk[0];  // c0 = u1 ^ nid
+    const uint32_t u1 = (uint32_t)(pB1 >> 32) ^ rk[0];  // c0 = u1 ^ g
     const uint32_t u2 = (uint32_t)pB1;                   // c1
     const uint32_t u3 = (uint32_t)(pA1 >> 32) ^ rk[1];   // c2
     const uint32_t u4 = (uint32_t)pA1;                   // c3
-    // round 2: B c2 does not depend on nid
+    // round 2: B c2 does not depend on g
     const unsigned long long pB2 = (unsigned long long)kMulB * u3;
     const uint32_t u5 = (uint32_t)(pB2 >> 32) ^ u2 ^ rk[2];  // c0
     const uint32_t u6 = (uint32_t)pB2;                        // c1
-    // round 3: A c0 does not depend on nid
+    // round 3: A c0 does not depend on g
     const unsigned long long pA3 = (unsigned long long)kMulA * u5;
     PhiloxHead h;
     h.u1 = u1;
@@ -524,10 +539,10 @@ __device__ __forceinline__ PhiloxHead philox_head(unsigned long long k, const ui
     return h;
 }
 
-__device__ __forceinline__ uint32_t philox_x0(const PhiloxHead& h, uint32_t nid, const uint32_t* rk) {
+__device__ __forceinline__ Philox4 philox_block(const PhiloxHead& h, uint32_t g, const uint32_t* rk) {
     constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
-    // rounds 2 and 3: the parts that depend on nid
-    const unsigned long long pA2 = (unsigned long long)kMulA * (h.u1 ^ nid);
+    // rounds 2 and 3: the parts that depend on g
+    const unsigned long long pA2 = (unsigned long long)kMulA * (h.u1 ^ g);
     const uint32_t c2r2 = (uint32_t)(pA2 >> 32) ^ h.u4k, c3r2 = (uint32_t)pA2;
     const unsigned long long pB3 = (unsigned long long)kMulB * c2r2;
     uint32_t c0 = (uint32_t)(pB3 >> 32) ^ h.u6k, c1 = (uint32_t)pB3, c2 = h.w ^ c3r2, c3 = h.loA3;
@@ -542,7 +557,16 @@ __device__ __forceinline__ uint32_t philox_x0(const PhiloxHead& h, uint32_t nid,
         c2 = n2;
         c3 = (uint32_t)pA;
     }
-    return c0;
+    Philox4 out;
+    out.v[0] = c0;
+    out.v[1] = c1;
+    out.v[2] = c2;
+    out.v[3] = c3;
+    return out;
+}
+
+__device__ __forceinline__ uint32_t philox_word(const PhiloxHead& h, uint32_t nid, const uint32_t* rk) {
+    return philox_word_of(philox_block(h, nid >> 2, rk), nid);
 }
 
 // The compiled applicability mask without branches: the period's remainder
@@ -592,7 +616,7 @@ __device__ __forceinline__ SelOut select_rec_flat(const uint4 rec, int32_t n, ui
     if (SEL == SNP_SELECT_PHILOX) {
         const bool draw = (mask & (mask - 1u)) != 0u;
         if (__any_sync(__activemask(), draw)) {
-            const uint32_t x0 = philox_x0(ph, nid, rk);
+            const uint32_t x0 = philox_word(ph, nid, rk);
             idx = draw ? (uint32_t)(((unsigned long long)x0 * (uint32_t)__popc(mask)) >> 32) : 0u;  // < popc <= 4
         }
     }

@@ -597,15 +597,20 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t a, const uint4& v) {
 //    4e mod 32, so one rotate of the right word finds it;
 //  * the chosen rule's 16-bit (c, p, d) field is taken with one byte
 //    permute of words z and w;
-//  * Philox runs only for slots with two or more applicable rules, one such
-//    slot per lane per round, as many rounds as the warp's busiest lane
-//    needs (all 32 lanes call this together: the loop is warp-uniform).
+//  * Philox runs only when a slot has two or more applicable rules.  When
+//    the four slots are the neurons 4g .. 4g+3 (quad_block: the system keeps
+//    the caller's neuron order), one block at counter g serves all four
+//    (philox_draw's word assignment), computed once per lane when any lane
+//    of the warp draws; otherwise one drawing slot per lane per round, as
+//    many rounds as the warp's busiest lane needs.  All 32 lanes call this
+//    together: both branches are warp-uniform.
 // Slots past the system's end arrive as c = 0, st = 0, in = 0 and a zero
 // record: an open neuron with no applicable rule, which changes nothing.
 // The lane's 4 x EB emission bits are returned in packed (slot j at EB * j).
 template <int SEL, int EB, typename PT>
 __device__ __forceinline__ void select_quad(const uint4 (&rec)[4], int4& c4, uint4& st4, const uint4& in4,
-                                            const uint4& nid4, const PhiloxHead& ph, const uint32_t* rk,
+                                            const uint4& nid4, bool quad_block, const PhiloxHead& ph,
+                                            const uint32_t* rk,
                                             const uint2* __restrict__ tab, const uint8_t* __restrict__ pick,
                                             int4& s4, PT& packed, bool& active, bool& dirty, bool& ovf) {
     uint32_t mask[4], need = 0u;
@@ -627,11 +632,19 @@ __device__ __forceinline__ void select_quad(const uint4 (&rec)[4], int4& c4, uin
         if (SEL == SNP_SELECT_PHILOX) need |= ((mask[j] & (mask[j] - 1u)) != 0u ? 1u : 0u) << j;
     }
     uint32_t x0[4] = {0u, 0u, 0u, 0u};
-    if (SEL == SNP_SELECT_PHILOX) {
+    if (SEL == SNP_SELECT_PHILOX && quad_block) {
+        if (__any_sync(0xffffffffu, need != 0u)) {
+            const Philox4 w = philox_block(ph, nid4.x >> 2, rk);
+            x0[0] = w.v[0];
+            x0[1] = w.v[1];
+            x0[2] = w.v[2];
+            x0[3] = w.v[3];
+        }
+    } else if (SEL == SNP_SELECT_PHILOX) {
         while (__any_sync(0xffffffffu, need != 0u)) {
             const uint32_t j = need ? (uint32_t)__ffs(need) - 1u : 0u;
             const uint32_t nid = j == 0u ? nid4.x : j == 1u ? nid4.y : j == 2u ? nid4.z : nid4.w;
-            const uint32_t v = philox_x0(ph, nid, rk);
+            const uint32_t v = philox_word(ph, nid, rk);
             x0[0] = (need & 1u) ? v : x0[0];
             x0[1] = (need & 3u) == 2u ? v : x0[1];
             x0[2] = (need & 7u) == 4u ? v : x0[2];
@@ -840,8 +853,8 @@ __global__ void __launch_bounds__(1024, 1) k_tiled_step(DevSys s, TiledSys tl, i
 #pragma unroll
                     for (int j = 0; j < 4; ++j) (&nid4.x)[j] = j < nv ? (uint32_t)__ldg(s.orig + slot0 + j) : 0u;
                 }
-                select_quad<SEL, EB, PT>(rq, c4, st4, in4, nid4, phx, s.philox_rk, s_mod, s_pick, s4, packed,
-                                         active, dirty, ovf);
+                select_quad<SEL, EB, PT>(rq, c4, st4, in4, nid4, s.identity, phx, s.philox_rk, s_mod, s_pick, s4,
+                                         packed, active, dirty, ovf);
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {

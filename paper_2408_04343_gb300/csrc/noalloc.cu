@@ -127,9 +127,8 @@ __device__ __forceinline__ SelOut na_select(const NaSys& s, int32_t j, int32_t r
     if (cnt == 1 || (SEL == SNP_SELECT_FIRST && cnt > 0)) {
         pick = first;
     } else if (cnt > 1) {
-        const Philox4 x = philox4x32_10((uint32_t)k, (uint32_t)j, (uint32_t)(k >> 32), 0u, (uint32_t)s.seed,
-                                        (uint32_t)(s.seed >> 32));
-        int32_t idx = (int32_t)(((unsigned long long)x.v[0] * (unsigned long long)cnt) >> 32);
+        const uint32_t x = philox_draw(k, (uint32_t)j, s.seed);
+        int32_t idx = (int32_t)(((unsigned long long)x * (unsigned long long)cnt) >> 32);
         for (int32_t r = first; r < r1; ++r) {
             if (rule_applies(n, na_rule(s, r))) {
                 if (idx == 0) {

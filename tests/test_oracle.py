@@ -136,6 +136,42 @@ def test_philox_choice_is_uniform():
     assert chi2 < 13.8  # p = 0.001 for 2 dof
 
 
+def test_philox_choice_every_word_position_is_uniform():
+    """Neurons 0..7 draw words 0..3 of two Philox blocks (i mod 4 of the
+    block at counter i / 4): each neuron's pick over |A| = 3 always
+    applicable rules is uniform (chi-square, 2 dof, p = 0.001 each)."""
+    q = 8
+    d = make_desc(q, [[(1, 1, 1, 0, 0), (1, 1, 1, 0, 0), (1, 1, 1, 0, 0)] for _ in range(q)], [], [10**6] * q)
+    counts = np.zeros((q, 3))
+    st = oracle.initial_state(d)
+    for k in range(6000):
+        S, _, _ = oracle.step(d, st, k, oracle.PHILOX, seed=777)
+        for i in range(q):
+            counts[i, S[i] - 3 * i] += 1
+    exp = 6000 / 3
+    chi2 = ((counts - exp) ** 2 / exp).sum(axis=1)
+    assert (chi2 < 13.8).all(), chi2
+
+
+@pytest.mark.parametrize("pair", [(0, 1), (3, 4)])
+def test_philox_choices_of_neighbours_are_independent(pair):
+    """Two neurons sharing one Philox block (0, 1: words 0 and 1) or in
+    adjacent blocks (3, 4) choose independently: their joint picks over 3 x 3
+    cells are uniform (chi-square, 8 dof, p = 0.001).  Giving two neurons of
+    a block the same word would put every draw on the diagonal."""
+    q = 8
+    d = make_desc(q, [[(1, 1, 1, 0, 0), (1, 1, 1, 0, 0), (1, 1, 1, 0, 0)] for _ in range(q)], [], [10**6] * q)
+    a, b = pair
+    joint = np.zeros((3, 3))
+    st = oracle.initial_state(d)
+    for k in range(9000):
+        S, _, _ = oracle.step(d, st, k, oracle.PHILOX, seed=31337)
+        joint[S[a] - 3 * a, S[b] - 3 * b] += 1
+    exp = 9000 / 9
+    chi2 = ((joint - exp) ** 2 / exp).sum()
+    assert chi2 < 26.1, (chi2, joint)
+
+
 # ---------------------------------------------------------------- worked example
 
 def test_sort_system_reproduces_table1():
