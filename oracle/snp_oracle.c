@@ -40,10 +40,10 @@
  *   phase 3: every pending neuron's counter drops by one (UPDATE_DELAYS).
  *
  *   choice : FIRST  -- the lowest-index applicable rule (Sec. 5, SV_CALC);
- *            PHILOX -- A_i[floor(x0 * |A_i| / 2^32)], x0 the first word of
- *                      Philox4x32-10 (Salmon et al., SC'11) at counter
- *                      (k mod 2^32, i, k >> 32, 0) and key (seed mod 2^32,
- *                      seed >> 32);
+ *            PHILOX -- A_i[floor(x * |A_i| / 2^32)], x word i mod 4 of the
+ *                      Philox4x32-10 block (Salmon et al., SC'11) at counter
+ *                      (k mod 2^32, i / 4, k >> 32, 0) and key
+ *                      (seed mod 2^32, seed >> 32) (orc_philox_pick);
  *            FORCED -- A_i[forced[i]] (used to enumerate branches).
  *
  * Pins (tests/test_oracle.py): Tables 1-3 and the sorting system of Sec. 6,
