@@ -230,7 +230,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--engine", default="tiled", choices=["tiled", "launch"],
                     help="tiled: emissions in shared memory (default); launch: emissions gathered from L2")
-    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "skewed", "families", "tree", "engines"],
+    ap.add_argument("--workload", default="large", choices=["large", "batch", "serve", "skewed", "families", "tree", "engines", "shards"],
                     help="large: the 1M-neuron headline (default); batch: 8,192 systems in one persistent "
                          "launch vs the plain per-system loop; serve: Poisson request loop; skewed: the "
                          "2M-neuron power-law system and its 16,384-neuron dense copy")

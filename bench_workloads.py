@@ -26,6 +26,11 @@ engines -- the 1,048,576-neuron workload of the headline bench on every
           engine and form (tiled, L2 gather, push, ELL pull, ELL push): one
           system each, 8 untimed steps, then one timed snp_step(192) call;
           the final configurations must agree.
+shards -- the 1,048,576-neuron workload split by neuron range into 1, 2
+          and 4 shards on one GPU (snp_shard_*, the step protocol of
+          paper_2408_04343_gb300/shard.py with the emission slices exchanged
+          by device copies): 64 timed steps after 4 untimed; the final
+          configuration must equal the unsharded system's.
 tree   -- computation-tree exploration of the subset-sum-shaped stand-in
           (n = 14: 2^14 branches when the choice neurons fire): branches per
           second explored breadth first with the batched branch step (one
@@ -50,7 +55,7 @@ def run(args, ws, rank, local):
         B.build()
     torch.cuda.set_device(local)
     fn = {"batch": batch, "serve": serve, "skewed": skewed, "families": families, "tree": tree_workload,
-          "engines": engines}[args.workload]
+          "engines": engines, "shards": shards}[args.workload]
     line = fn(args, libsnp, synth)
     line.update({"n_gpus": ws, "data": "synthetic", "dtype": "int32", "higher_is_better": True})
     if rank == 0:
@@ -275,6 +280,49 @@ def engines(args, libsnp, synth):
     return {"metric": "synaptic updates/s", "workload": "engines", "value": res["tiled"]["syn_updates_per_s"],
             "unit": "synaptic updates/s", "engines": res, "same_final_configuration": len(digests) == 1,
             "config": {"q": d.q, "num_syn": d.num_syn, "timed_steps": 192}}
+
+
+def shards(args, libsnp, synth):
+    """The sharded step of one system (one shard per device in a multi-GPU
+    run) with all shards on this GPU: per step every shard's phase 1 (its
+    activity read back to the host), the slices copied into every shard's
+    emission vector, every shard's phase 2.  Timed on the host around a
+    device synchronize; checked against the unsharded system."""
+    import torch
+    from paper_2408_04343_gb300 import shard as SH
+    d, _, _ = synth.large_1m()
+    warm, n = 4, 64
+    sel = libsnp.SNP_SELECT_PHILOX
+    ref = libsnp.System(d, select=sel, seed=d.seed, engine=libsnp.SNP_ENGINE_TILED)
+    ref.step(warm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done_ref = ref.step(n)
+    torch.cuda.synchronize()
+    ref_dt = time.perf_counter() - t0
+    C_ref = ref.config().copy()
+    ref.close()
+    res = {"unsharded_tiled": {"us_per_step": ref_dt / max(done_ref, 1) * 1e6,
+                               "syn_updates_per_s": d.num_syn * done_ref / ref_dt}}
+    for world in (1, 2, 4):
+        ranges, chunk = SH.shard_ranges(d.q, world)
+        Es = [torch.zeros(world * chunk + 1, dtype=torch.int16, device="cuda") for _ in range(world)]
+        shs = [libsnp.Shard(d, lo, hi, select=sel, seed=d.seed, E=Es[r]) for r, (lo, hi) in enumerate(ranges)]
+        ex = SH.local_exchange([(Es[r], lo, hi) for r, (lo, hi) in enumerate(ranges)])
+        k = SH.run(shs, warm, 0, ex, lambda a: a)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = SH.run(shs, n, k, ex, lambda a: a)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        C = np.concatenate([sh.get_state()[0] for sh in shs])
+        res[f"shards_{world}"] = {"us_per_step": dt / max(done, 1) * 1e6, "syn_updates_per_s": d.num_syn * done / dt,
+                                  "identical_to_unsharded": bool(done == done_ref and (C == C_ref).all())}
+        for sh in shs:
+            sh.close()
+    return {"metric": "synaptic updates/s", "workload": "shards", "value": res["shards_2"]["syn_updates_per_s"],
+            "unit": "synaptic updates/s", "shards": res,
+            "config": {"q": d.q, "num_syn": d.num_syn, "timed_steps": n, "exchange": "device copies, one GPU"}}
 
 
 def families(args, libsnp, synth):
